@@ -1,0 +1,265 @@
+/*
+ * elas_gb300 -- C-ABI of the GB300 (sm_103a) implementation of the ELAS
+ * data-parallel stereo path (Rahnama, Frost, Miksik, Torr, "Real-Time Dense
+ * Stereo Matching with ELAS on FPGA Accelerated Embedded Devices",
+ * arXiv 1802.07210, Sec. III.A).
+ *
+ * Pipeline per rectified 8-bit stereo pair (Sec. III.A, Fig. 1):
+ *   elas_descriptors      gradient (Sobel) images -> 16-byte descriptors
+ *   elas_support_points   sparse matches with ratio test (Eq. 1-2), texture
+ *                         and left-right checks, consistency + redundancy
+ *                         filters, grid vectors (Fig. 2), raster-order list
+ *   elas_triangulate      Delaunay mesh of the support points (host)
+ *   elas_plane_prior      per-triangle slanted plane -> image-sized prior
+ *                         matrix (Sec. VI.D)
+ *   elas_dense_argmin     per-pixel argmin of SAD + tabulated prior over the
+ *   elas_dense_match      grid-vector and plane-neighbourhood candidates
+ *   elas_lr_check         left-right consistency (occlusion invalidation)
+ *   elas_postprocess      gap interpolation + adaptive mean (smoothing)
+ *
+ * Conventions shared by every call
+ *   - All device pointers are owned by the caller.  Calls never allocate
+ *     device memory: scratch comes from a caller-provided workspace whose
+ *     size the matching *_workspace_bytes() call returns.  Only the pipeline
+ *     handle (elas_pipeline_*) owns memory, created in elas_pipeline_create.
+ *   - Device calls are asynchronous on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  Argument errors are detected on the host and
+ *     returned synchronously; a launch failure returns ELAS_ERR_CUDA;
+ *     execution errors surface on the caller's next synchronisation.
+ *   - No call aborts, traps or prints.  elas_last_error() returns a
+ *     thread-local text for the last non-OK status of the calling thread.
+ *   - Layouts: image uint8 [h][pitch]; descriptors uint8 [h][w][16] (16-byte
+ *     aligned); candidate grid int16 [h/step][w/step] with candidate (jc,ic)
+ *     at pixel (jc*step, ic*step), -1 = none; support list int16 triples
+ *     (u, v, d) in raster order of the candidate grid; grid vectors uint32
+ *     [ceil(h/G)][ceil(w/G)][ceil((disp_max+1)/32)], bit d set = candidate d;
+ *     triangles int32 triples of support-list indices; disparity maps int16
+ *     [h][w] with -1 = invalid; post-processed map float [h][w], -1 = invalid.
+ *   - Integer outputs are bit-exact functions of the inputs (independent of
+ *     launch shape and scheduling).  Float outputs use single IEEE-754 ops
+ *     in a fixed order without contraction.
+ */
+#ifndef ELAS_GB300_H
+#define ELAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ELAS_OK = 0,
+    ELAS_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or parameter    */
+    ELAS_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed         */
+    ELAS_ERR_CAPACITY = 3,    /* an output buffer is smaller than required    */
+    ELAS_ERR_TIMEOUT = 4,     /* a bounded wait ran out                       */
+    ELAS_ERR_NO_MEMORY = 5,   /* host or device allocation refused (handles)  */
+    ELAS_ERR_INTERNAL = 6     /* internal invariant broken                    */
+} elas_status;
+
+/* Test-only switches in elas_params.test_flags. */
+#define ELAS_FLAG_PRIOR_OFF      1u /* dense: prior term forced to 0                  */
+#define ELAS_FLAG_FULL_RANGE     2u /* dense: every in-range d is a candidate and no
+                                       plane is required                             */
+#define ELAS_FLAG_REDUNDANCY_OFF 4u /* support: skip the redundancy filter           */
+
+/* Method parameters.  Names follow the libelas "robotics" setting used to
+ * quote the workloads; elas_params_default() fills disp_max = 255 and
+ * support_threshold 0.85, support_texture 10, candidate_stepsize 5,
+ * incon_window_size 5, incon_threshold 5, incon_min_support 5,
+ * redun_max_dist 5, grid_size 20, beta 0.02, gamma 3, sigma 1, sradius 2,
+ * match_texture 1, lr_threshold 2, ipol_gap_width 3, filter_adaptive_mean 1.
+ * Limits: 0 <= disp_min <= disp_max <= 1023, candidate_stepsize >= 1,
+ * grid_size >= 1, 0 <= sradius <= 15, 0 < support_threshold. */
+typedef struct {
+    int32_t disp_min, disp_max;
+    float support_threshold;     /* Eq. 2: accept iff m1 <= t * m2                  */
+    int32_t support_texture;     /* min 64-byte window texture (sum |b-128|)        */
+    int32_t candidate_stepsize;  /* support candidate lattice spacing (pixels)      */
+    int32_t incon_window_size;   /* consistency window, candidate units             */
+    int32_t incon_threshold;     /* |dd| <= threshold counts as agreement           */
+    int32_t incon_min_support;   /* agreeing neighbours needed to keep a point      */
+    int32_t redun_max_dist;      /* redundancy search distance, candidate units     */
+    int32_t grid_size;           /* grid-vector cell size G (pixels)                */
+    float beta, gamma, sigma;    /* prior P[delta] parameters                       */
+    int32_t sradius;             /* plane neighbourhood radius                      */
+    int32_t match_texture;       /* min 16-byte descriptor texture for dense        */
+    int32_t lr_threshold;        /* left-right tolerance (support and dense)        */
+    int32_t ipol_gap_width;      /* max gap length filled by interpolation (0=off)  */
+    int32_t filter_adaptive_mean;/* 1 = adaptive mean after interpolation           */
+    uint32_t test_flags;         /* ELAS_FLAG_* (tests only)                        */
+} elas_params;
+
+/* A cudaStream_t passed through the C ABI. */
+typedef void *elas_stream;
+
+/* Fills `p` with the default parameter set listed above.  Host only. */
+elas_status elas_params_default(elas_params *p);
+
+/* Text of the calling thread's last error (never NULL). */
+const char *elas_last_error(void);
+
+/* Library version string. */
+const char *elas_version(void);
+
+/*
+ * Descriptors (Sec. III.A: matching runs on the horizontal and vertical
+ * gradient images, Fig. 1(b-d); Sec. VI.A: 16-byte descriptors).
+ * du/dv: 3x3 Sobel responses (du weights -1 0 1 / -2 0 2 / -1 0 1 with +1 on
+ * the right column; dv its transpose), 0 on the one-pixel frame;
+ * q(s) = clamp(128 + trunc(s/4), 1, 255).  Byte k of pixel (u,v): q(du) at
+ * offsets (-2,-2),(2,-2),(-1,0),(1,0),(-2,2),(2,2),(0,-1),(0,1) for k<8,
+ * q(dv) at (0,-2),(0,2),(-2,0),(2,0),(-1,-1),(1,-1),(-1,1),(1,1) for k>=8;
+ * samples outside the image read 128.
+ * imgL/imgR: device uint8 [h][pitch] (pitch >= w); descL/descR: device
+ * uint8 [h][w][16], 16-byte aligned.  imgR/descR may both be NULL.
+ * Errors: ELAS_ERR_INVALID_ARG for w,h < 1, pitch < w, NULL or misaligned.
+ */
+elas_status elas_descriptors(const uint8_t *imgL, const uint8_t *imgR, int32_t w, int32_t h,
+                             int32_t pitch, uint8_t *descL, uint8_t *descR, elas_stream stream);
+
+/*
+ * Support points (Sec. III.A; Eq. 1-2).  For every lattice candidate
+ * (u,v) = (jc*step, ic*step) with 4 <= u <= w-5, 4 <= v <= h-5: the 64-byte
+ * window = descriptors at (u+-2, v+-2); cost(d) = window SAD against the
+ * right window at u-d (searched for d in [disp_min, disp_max] with
+ * u-d >= 4).  d1 = smallest d of the minimum m1, m2 = minimum over d != d1;
+ * accepted iff >= 2 disparities were searched, m2 > 0 and
+ * (float)m1 <= support_threshold * (float)m2, the left window texture and
+ * the right window texture at u-d1 are >= support_texture, and the
+ * right-to-left re-match from u-d1 (searching u-d1+d <= w-5, same test)
+ * returns d_rl with |d1 - d_rl| <= lr_threshold.  Then the consistency
+ * filter (keep iff >= incon_min_support other valid points in the
+ * +-incon_window_size candidate window differ by <= incon_threshold) and
+ * the redundancy filter (drop iff the identical disparity occurs within
+ * redun_max_dist candidates in each of the four axis directions) run, each
+ * reading the previous grid as a whole.  Grid vectors: bits {d-1,d,d+1}
+ * (clipped to the range) of every point are OR-ed into the 3x3 cells around
+ * cell(u,v) (grid_L) and cell(u-d,v) (grid_R).
+ * Outputs (device): d_can int16 [h/step][w/step]; list int16 [cap][3];
+ * count int32 (true number of points); grid_L/grid_R (may be NULL).
+ * cap must be >= (w/step)*(h/step), so the list can never overflow.
+ * workspace: device, >= elas_support_workspace_bytes(w,h,p), 256-byte
+ * aligned.
+ */
+size_t elas_support_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
+elas_status elas_support_points(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
+                                const elas_params *p, int16_t *d_can, int16_t *list, int32_t cap,
+                                int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
+                                void *workspace, size_t workspace_bytes, elas_stream stream);
+
+/*
+ * Delaunay triangulation of the support list (Sec. III.A), on the host,
+ * synchronous.  right = 0: points (u, v); right = 1: points (u - d, v), where
+ * coincident points keep only the lowest list index.  Cocircular ties are
+ * broken by the symbolic perturbation |p_i|^2 + eps_i of the lifted heights
+ * with eps_0 >> eps_1 >> ... (lower list index dominates), so the result is
+ * unique.  tri: host int32 [cap][3], counter-clockwise in (u, v) with v
+ * pointing down as the y axis; *ntri = triangle count (also on
+ * ELAS_ERR_CAPACITY, when it exceeds cap).  cap >= 2n always suffices.
+ */
+elas_status elas_triangulate(const int16_t *list, int32_t n, int32_t right, int32_t *tri,
+                             int32_t cap, int32_t *ntri);
+
+/*
+ * Slanted-plane prior (Sec. III.A; image-sized prior matrix, Sec. VI.D).
+ * For each triangle, with its vertices taken in ascending list index:
+ * det = du1*dv2 - du2*dv1, a = (float)(dd1*dv2 - dd2*dv1) / (float)det,
+ * b = (float)(du1*dd2 - du2*dd1) / (float)det, c = (d0 - a*u0) - b*v0 (FP32,
+ * left to right, no fused multiply-add).  Pixels owned by the triangle under
+ * integer edge functions with the top-left rule get
+ * d_plane = clamp(floor((a*u + b*v) + c + 0.5), disp_min, disp_max); all
+ * other pixels get -1.  list/tri/d_plane: device; d_plane int16 [h][w].
+ */
+elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,
+                             int32_t right, int32_t w, int32_t h, const elas_params *p,
+                             int16_t *d_plane, elas_stream stream);
+
+/*
+ * Dense argmin for one reference image (Sec. III.A, Fig. 1(h)).
+ * right = 0: reference = left, other position u-d; right = 1: reference =
+ * right, other position u+d.  Pixel (u,v) with 2 <= u <= w-3, 2 <= v <= h-3,
+ * reference texture >= match_texture and d_plane >= 0 searches
+ * S = ({d : |d - d_plane| <= sradius} U grid(cell(u,v))) within
+ * [disp_min, disp_max] and 2 <= other position <= w-3, with
+ * cost(d) = SAD16 + (|d - d_plane| <= sradius ? P[|d - d_plane|] : 0),
+ * P[k] = trunc((ln gamma - ln(gamma + exp(-k^2/(2 sigma^2)))) / beta)
+ * (computed on the host in double).  Output = smallest d of the minimum
+ * cost, -1 if S is empty or the pixel is not matched.  d_plane and grid may
+ * be NULL only with ELAS_FLAG_FULL_RANGE.
+ */
+elas_status elas_dense_argmin(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
+                              const elas_params *p, const int16_t *d_plane, const uint32_t *grid,
+                              int32_t right, int16_t *out, elas_stream stream);
+
+/*
+ * Plane prior + dense argmin for both reference images.  list (device) is
+ * the support list of n points, triL/triR (device) the triangulations in
+ * left and right coordinates, grid_L/grid_R the grid vectors.  Outputs dL,
+ * dR int16 [h][w].  workspace: device, >= elas_dense_workspace_bytes().
+ */
+size_t elas_dense_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
+elas_status elas_dense_match(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
+                             const elas_params *p, const int16_t *list, int32_t n,
+                             const int32_t *triL, int32_t ntriL, const int32_t *triR,
+                             int32_t ntriR, const uint32_t *grid_L, const uint32_t *grid_R,
+                             int16_t *dL, int16_t *dR, void *workspace, size_t workspace_bytes,
+                             elas_stream stream);
+
+/*
+ * Left-right consistency check (Sec. III.A, Fig. 1(i)), in place.  Decisions
+ * read the unmodified maps: dL(u) is kept iff d >= 0, u-d >= 0,
+ * dR(u-d) >= 0 and |d - dR(u-d)| <= lr_threshold; dR(u) symmetrically with
+ * u+d <= w-1 and dL(u+d).  Rejected pixels become -1; maskL/maskR (uint8,
+ * may be NULL) get 1 = kept, 0 = invalid.  Requires w <= 16384.
+ */
+elas_status elas_lr_check(int16_t *dL, int16_t *dR, int32_t w, int32_t h, int32_t lr_threshold,
+                          uint8_t *maskL, uint8_t *maskR, elas_stream stream);
+
+/*
+ * Post-processing (Sec. III.A, Fig. 1(i)).  If ipol_gap_width > 0: each
+ * maximal run of invalid pixels in a row no longer than ipol_gap_width and
+ * bounded by valid d1, d2 is filled with (d1+d2)/2 if |d1-d2| < 3 else
+ * min(d1,d2); then the same along columns.  If filter_adaptive_mean: for
+ * valid pixels, horizontal then vertical weighted mean over offsets -3..3
+ * (ascending) of valid neighbours with weight max(0, 4 - |d_i - d_0|).
+ * d: device int16 [h][w]; out: device float [h][w], -1 = invalid.
+ * workspace >= elas_postprocess_workspace_bytes(w, h).
+ */
+size_t elas_postprocess_workspace_bytes(int32_t w, int32_t h);
+elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, const elas_params *p,
+                             float *out, void *workspace, size_t workspace_bytes,
+                             elas_stream stream);
+
+/*
+ * Pipeline handle: owns device buffers, pinned staging and host worker
+ * threads for one image size, and runs the whole path per pair.
+ * elas_pipeline_run: device images in, device maps out (dR, post may be
+ * NULL); the stream is synchronised once in the middle (support list to the
+ * host for triangulation) and the call returns with the rest enqueued.
+ * elas_pipeline_run_host: host buffers in and out, copies included; returns
+ * when the outputs are on the host.
+ */
+typedef struct elas_pipeline elas_pipeline;
+typedef struct {
+    int32_t n_support;     /* support points of the last pair           */
+    int32_t n_tri_left;    /* triangles, left coordinates                */
+    int32_t n_tri_right;   /* triangles, right coordinates               */
+    double  triangulate_ms;/* host wall time of both triangulations      */
+} elas_pipeline_stats;
+
+elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_params *p, elas_pipeline **out);
+elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR,
+                              int32_t pitch, int16_t *dL, int16_t *dR, float *post,
+                              elas_stream stream);
+elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR,
+                                   int16_t *dL, int16_t *dR, float *post, elas_stream stream);
+elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st);
+void elas_pipeline_destroy(elas_pipeline *pl);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELAS_GB300_H */

@@ -1,0 +1,208 @@
+"""Torch-facing binding of the C-ABI: one function per entry point, same
+names.  PyTorch supplies device memory and the current stream only; every
+output tensor is allocated here and filled by the library.
+
+Layouts follow include/elas_gb300.h: images uint8 [h, w]; descriptors uint8
+[h, w, 16]; candidate grid int16 [h//step, w//step]; support list int16
+[cap, 3]; grid vectors int32 [gh, gw, nw] (uint32 bit patterns); triangles
+int32 [ntri, 3]; disparity maps int16 [h, w]; post-processed map float32.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import ElasError, Params, PipelineStats, as_params, check, lib, np_ptr, params  # noqa: F401
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return C.c_void_p(t.data_ptr())
+
+
+def _opt(t, dtype, name, shape=None):
+    return None if t is None else _dev(t, dtype, name, shape)
+
+
+def grid_shape(w, h, prm):
+    G = prm.grid_size
+    return ((h + G - 1) // G, (w + G - 1) // G, (prm.disp_max + 1 + 31) // 32)
+
+
+def _workspace(nbytes, device):
+    # 256-byte aligned device scratch (torch's allocator aligns to >= 512)
+    return torch.empty(max(1, int(nbytes)), dtype=torch.uint8, device=device)
+
+
+def elas_descriptors(imgL, imgR=None, stream=None):
+    h, w = imgL.shape
+    pL = _dev(imgL, torch.uint8, "imgL")
+    descL = torch.empty((h, w, 16), dtype=torch.uint8, device=imgL.device)
+    descR = None
+    pR = None
+    if imgR is not None:
+        pR = _dev(imgR, torch.uint8, "imgR", (h, w))
+        descR = torch.empty_like(descL)
+    check(lib().elas_descriptors(pL, pR, w, h, w, C.c_void_p(descL.data_ptr()),
+                                 None if descR is None else C.c_void_p(descR.data_ptr()), _stream(stream)))
+    return (descL, descR) if imgR is not None else descL
+
+
+def elas_support_points(descL, descR, prm=None, grids=True, stream=None):
+    prm = as_params(prm)
+    h, w = descL.shape[:2]
+    dev = descL.device
+    step = prm.candidate_stepsize
+    hc, wc = h // step, w // step
+    cap = max(1, hc * wc)
+    d_can = torch.empty((hc, wc), dtype=torch.int16, device=dev)
+    lst = torch.empty((cap, 3), dtype=torch.int16, device=dev)
+    count = torch.empty((1,), dtype=torch.int32, device=dev)
+    gL = gR = None
+    if grids:
+        gL = torch.empty(grid_shape(w, h, prm), dtype=torch.int32, device=dev)
+        gR = torch.empty_like(gL)
+    nb = lib().elas_support_workspace_bytes(w, h, C.byref(prm))
+    ws = _workspace(nb, dev)
+    check(lib().elas_support_points(
+        _dev(descL, torch.uint8, "descL", (h, w, 16)), _dev(descR, torch.uint8, "descR", (h, w, 16)), w, h,
+        C.byref(prm), C.c_void_p(d_can.data_ptr()), C.c_void_p(lst.data_ptr()), cap,
+        C.c_void_p(count.data_ptr()), _opt(gL, torch.int32, "grid_L"), _opt(gR, torch.int32, "grid_R"),
+        C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+    return dict(d_can=d_can, list=lst, count=count, grid_L=gL, grid_R=gR)
+
+
+def elas_triangulate(lst, right=False):
+    """Host call: lst is a numpy int16 [n, 3] support list."""
+    lst = np.ascontiguousarray(lst, dtype=np.int16).reshape(-1, 3)
+    n = len(lst)
+    cap = max(1, 2 * n)
+    tri = np.empty((cap, 3), np.int32)
+    nt = C.c_int32(0)
+    check(lib().elas_triangulate(np_ptr(lst), n, int(bool(right)), np_ptr(tri), cap, C.byref(nt)))
+    return tri[:nt.value].copy()
+
+
+def elas_plane_prior(lst, tri, w, h, prm=None, right=False, stream=None):
+    prm = as_params(prm)
+    dev = lst.device
+    out = torch.empty((h, w), dtype=torch.int16, device=dev)
+    n = lst.shape[0]
+    ntri = tri.shape[0]
+    check(lib().elas_plane_prior(_dev(lst, torch.int16, "list"), n, _dev(tri, torch.int32, "tri"), ntri,
+                                 int(bool(right)), w, h, C.byref(prm), C.c_void_p(out.data_ptr()),
+                                 _stream(stream)))
+    return out
+
+
+def elas_dense_argmin(descL, descR, prm=None, d_plane=None, grid=None, right=False, stream=None):
+    prm = as_params(prm)
+    h, w = descL.shape[:2]
+    out = torch.empty((h, w), dtype=torch.int16, device=descL.device)
+    check(lib().elas_dense_argmin(
+        _dev(descL, torch.uint8, "descL", (h, w, 16)), _dev(descR, torch.uint8, "descR", (h, w, 16)), w, h,
+        C.byref(prm), _opt(d_plane, torch.int16, "d_plane", (h, w)),
+        _opt(grid, torch.int32, "grid", grid_shape(w, h, prm)), int(bool(right)),
+        C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def elas_dense_match(descL, descR, prm, lst, n, triL, triR, grid_L, grid_R, stream=None):
+    prm = as_params(prm)
+    h, w = descL.shape[:2]
+    dev = descL.device
+    dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+    dR = torch.empty_like(dL)
+    nb = lib().elas_dense_workspace_bytes(w, h, C.byref(prm))
+    ws = _workspace(nb, dev)
+    gs = grid_shape(w, h, prm)
+    check(lib().elas_dense_match(
+        _dev(descL, torch.uint8, "descL", (h, w, 16)), _dev(descR, torch.uint8, "descR", (h, w, 16)), w, h,
+        C.byref(prm), _dev(lst, torch.int16, "list"), int(n), _dev(triL, torch.int32, "triL"), triL.shape[0],
+        _dev(triR, torch.int32, "triR"), triR.shape[0], _dev(grid_L, torch.int32, "grid_L", gs),
+        _dev(grid_R, torch.int32, "grid_R", gs), C.c_void_p(dL.data_ptr()), C.c_void_p(dR.data_ptr()),
+        C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+    return dL, dR
+
+
+def elas_lr_check(dL, dR, lr_threshold, masks=True, stream=None):
+    """In place on dL and dR; returns (maskL, maskR) or None."""
+    h, w = dL.shape
+    mL = mR = None
+    if masks:
+        mL = torch.empty((h, w), dtype=torch.uint8, device=dL.device)
+        mR = torch.empty_like(mL)
+    check(lib().elas_lr_check(_dev(dL, torch.int16, "dL"), _dev(dR, torch.int16, "dR", (h, w)), w, h,
+                              int(lr_threshold), _opt(mL, torch.uint8, "maskL"), _opt(mR, torch.uint8, "maskR"),
+                              _stream(stream)))
+    return (mL, mR) if masks else None
+
+
+def elas_postprocess(d, prm=None, stream=None):
+    prm = as_params(prm)
+    h, w = d.shape
+    out = torch.empty((h, w), dtype=torch.float32, device=d.device)
+    nb = lib().elas_postprocess_workspace_bytes(w, h)
+    ws = _workspace(nb, d.device)
+    check(lib().elas_postprocess(_dev(d, torch.int16, "d"), w, h, C.byref(prm), C.c_void_p(out.data_ptr()),
+                                 C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+    return out
+
+
+class Pipeline:
+    """Owner of an ``elas_pipeline`` handle for one image size."""
+
+    def __init__(self, w, h, prm=None):
+        self.w, self.h = w, h
+        self.prm = as_params(prm)
+        self._h = C.c_void_p()
+        check(lib().elas_pipeline_create(w, h, C.byref(self.prm), C.byref(self._h)))
+
+    def run(self, imgL, imgR, dL, dR=None, post=None, stream=None):
+        """Device tensors in and out (dL/dR int16 [h, w], post float32)."""
+        check(lib().elas_pipeline_run(
+            self._h, _dev(imgL, torch.uint8, "imgL", (self.h, self.w)),
+            _dev(imgR, torch.uint8, "imgR", (self.h, self.w)), self.w,
+            _dev(dL, torch.int16, "dL", (self.h, self.w)), _opt(dR, torch.int16, "dR", (self.h, self.w)),
+            _opt(post, torch.float32, "post", (self.h, self.w)), _stream(stream)))
+
+    def run_host(self, imgL, imgR, dL, dR=None, post=None, stream=None):
+        """Host (ideally pinned) CPU tensors in and out; returns when done."""
+        def hp(t, dtype, name):
+            if t is None:
+                return None
+            if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+                raise TypeError("%s must be a contiguous host %s tensor" % (name, dtype))
+            return C.c_void_p(t.data_ptr())
+        check(lib().elas_pipeline_run_host(self._h, hp(imgL, torch.uint8, "imgL"), hp(imgR, torch.uint8, "imgR"),
+                                           hp(dL, torch.int16, "dL"), hp(dR, torch.int16, "dR"),
+                                           hp(post, torch.float32, "post"), _stream(stream)))
+
+    def stats(self):
+        st = PipelineStats()
+        check(lib().elas_pipeline_stats_get(self._h, C.byref(st)))
+        return dict(n_support=st.n_support, n_tri_left=st.n_tri_left, n_tri_right=st.n_tri_right,
+                    triangulate_ms=st.triangulate_ms)
+
+    def close(self):
+        if self._h:
+            lib().elas_pipeline_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

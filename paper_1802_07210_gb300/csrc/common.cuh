@@ -1,0 +1,66 @@
+// Internal helpers shared by the CUDA translation units of libelas_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "elas_gb300.h"
+
+namespace elas {
+
+// Thread-local error text behind elas_last_error().
+void set_error(const char *fmt, ...);
+elas_status fail(elas_status st, const char *fmt, ...);
+// Converts a pending launch error into ELAS_ERR_CUDA.
+elas_status launch_status(const char *what);
+// Validates the parameter block against the image size.
+elas_status check_params(const elas_params *p, int32_t w, int32_t h);
+
+inline cudaStream_t to_stream(elas_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+constexpr int kMaxSradius = 15;
+constexpr int kMaxDisp = 1023;
+
+// Grid-vector geometry.
+struct GridGeom {
+    int gw, gh, nw;  // cells across, cells down, 32-bit words per cell
+};
+inline GridGeom grid_geom(int w, int h, const elas_params *p) {
+    GridGeom g;
+    g.gw = (w + p->grid_size - 1) / p->grid_size;
+    g.gh = (h + p->grid_size - 1) / p->grid_size;
+    g.nw = (p->disp_max + 1 + 31) / 32;
+    return g;
+}
+
+// Prior table P[0..sradius] from the parameters (host, double precision).
+void prior_table(const elas_params *p, int32_t *P);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Sum of |a_i - b_i| over the 4 bytes of a and b, added to acc.
+__device__ __forceinline__ uint32_t sad4_acc(uint32_t a, uint32_t b, uint32_t acc) {
+    return __dp4a(__vabsdiffu4(a, b), 0x01010101u, acc);
+}
+
+__device__ __forceinline__ uint32_t sad16(const uint4 &a, const uint4 &b) {
+    uint32_t s = sad4_acc(a.x, b.x, 0u);
+    s = sad4_acc(a.y, b.y, s);
+    s = sad4_acc(a.z, b.z, s);
+    return sad4_acc(a.w, b.w, s);
+}
+
+// Texture of a descriptor: sum of |b - 128| over its 16 bytes.
+__device__ __forceinline__ uint32_t texture16(const uint4 &a) {
+    const uint32_t m = 0x80808080u;
+    uint32_t s = sad4_acc(a.x, m, 0u);
+    s = sad4_acc(a.y, m, s);
+    s = sad4_acc(a.z, m, s);
+    return sad4_acc(a.w, m, s);
+}
+
+}  // namespace elas

@@ -1,0 +1,267 @@
+// Pipeline handle: the per-pair runtime around the kernels.
+//
+// Owns, for one image size: device buffers for every intermediate, the
+// workspaces, a pinned staging area for the support list (device -> host)
+// and the triangles (host -> device), and one helper thread so that the
+// left- and right-coordinate triangulations run concurrently.
+//
+// Per pair: descriptors -> support (GPU) | count+list to host | two
+// triangulations (host, in parallel) | triangles to device | plane prior ->
+// dense -> LR check -> post-processing (GPU).
+#include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "launch.cuh"
+
+namespace {
+
+// One persistent helper thread running one job at a time.
+class Helper {
+  public:
+    Helper() : th_([this] { loop(); }) {}
+    ~Helper() {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        th_.join();
+    }
+    template <class F> void submit(F &&f) {
+        std::lock_guard<std::mutex> g(m_);
+        job_ = std::forward<F>(f);
+        has_job_ = true;
+        done_ = false;
+        cv_.notify_all();
+    }
+    void wait() {
+        std::unique_lock<std::mutex> g(m_);
+        cv_.wait(g, [this] { return done_; });
+    }
+
+  private:
+    void loop() {
+        for (;;) {
+            std::function<void()> job;
+            {
+                std::unique_lock<std::mutex> g(m_);
+                cv_.wait(g, [this] { return stop_ || has_job_; });
+                if (stop_) return;
+                job = std::move(job_);
+                has_job_ = false;
+            }
+            job();
+            {
+                std::lock_guard<std::mutex> g(m_);
+                done_ = true;
+            }
+            cv_.notify_all();
+        }
+    }
+    std::mutex m_;
+    std::condition_variable cv_;
+    std::function<void()> job_;
+    bool has_job_ = false, done_ = true, stop_ = false;
+    std::thread th_;
+};
+
+}  // namespace
+
+struct elas_pipeline {
+    int w = 0, h = 0, wc = 0, hc = 0, nc = 0;
+    elas_params p{};
+    elas::GridGeom g{};
+    // device
+    uint8_t *img = nullptr;  // L then R (host-input path)
+    uint8_t *descL = nullptr, *descR = nullptr;
+    int16_t *dcan = nullptr;
+    char *countlist = nullptr;  // int32 count at offset 0, int16 list at offset 16
+    uint32_t *gridL = nullptr, *gridR = nullptr;
+    int32_t *tri = nullptr;  // left triangles then right triangles
+    void *ws_support = nullptr, *ws_dense = nullptr, *ws_post = nullptr;
+    int16_t *dL = nullptr, *dR = nullptr;  // host-output path
+    float *post = nullptr;
+    size_t ws_support_bytes = 0, ws_dense_bytes = 0, ws_post_bytes = 0;
+    // pinned host
+    char *h_countlist = nullptr;
+    int32_t *h_tri = nullptr;
+    size_t countlist_bytes = 0;
+    int tri_cap = 0;  // per side
+    // last run
+    elas_pipeline_stats stats{};
+    std::vector<int32_t> triL_v, triR_v;
+    Helper *helper = nullptr;
+};
+
+namespace {
+
+template <class T> cudaError_t dalloc(T **p, size_t bytes) {
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+void release(elas_pipeline *pl) {
+    if (!pl) return;
+    delete pl->helper;
+    void *dev[] = {pl->img, pl->descL, pl->descR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
+                   pl->ws_support, pl->ws_dense, pl->ws_post, pl->dL, pl->dR, pl->post};
+    for (void *d : dev)
+        if (d) cudaFree(d);
+    if (pl->h_countlist) cudaFreeHost(pl->h_countlist);
+    if (pl->h_tri) cudaFreeHost(pl->h_tri);
+    delete pl;
+}
+
+// Host part of one pair: triangulations in left and right coordinates.
+elas_status triangulate_both(elas_pipeline *pl, int n, const int16_t *list, int *ntL, int *ntR) {
+    std::vector<int32_t> &tl = pl->triL_v, &tr = pl->triR_v;
+    int32_t cntL = 0, cntR = 0;
+    elas_status sR = ELAS_OK;
+    tr.resize((size_t)3 * pl->tri_cap);
+    tl.resize((size_t)3 * pl->tri_cap);
+    pl->helper->submit([&] { sR = elas_triangulate(list, n, 1, tr.data(), pl->tri_cap, &cntR); });
+    elas_status sL = elas_triangulate(list, n, 0, tl.data(), pl->tri_cap, &cntL);
+    pl->helper->wait();
+    if (sL != ELAS_OK) return sL;
+    if (sR != ELAS_OK) return sR;
+    *ntL = cntL;
+    *ntR = cntR;
+    std::memcpy(pl->h_tri, tl.data(), sizeof(int32_t) * 3 * (size_t)cntL);
+    std::memcpy(pl->h_tri + 3 * (size_t)cntL, tr.data(), sizeof(int32_t) * 3 * (size_t)cntR);
+    return ELAS_OK;
+}
+
+}  // namespace
+
+extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_params *p, elas_pipeline **out) {
+    using namespace elas;
+    if (!out) return fail(ELAS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    elas_status s = check_params(p, w, h);
+    if (s != ELAS_OK) return s;
+    elas_pipeline *pl = new (std::nothrow) elas_pipeline();
+    if (!pl) return fail(ELAS_ERR_NO_MEMORY, "host allocation");
+    pl->w = w;
+    pl->h = h;
+    pl->p = *p;
+    pl->wc = w / p->candidate_stepsize;
+    pl->hc = h / p->candidate_stepsize;
+    pl->nc = pl->wc * pl->hc;
+    pl->g = grid_geom(w, h, p);
+    const size_t npx = (size_t)w * h;
+    const size_t gbytes = (size_t)pl->g.gw * pl->g.gh * pl->g.nw * sizeof(uint32_t);
+    pl->tri_cap = 2 * pl->nc + 8;
+    pl->countlist_bytes = 16 + align_up((size_t)pl->nc * 3 * sizeof(int16_t) + 16, 16);
+    pl->ws_support_bytes = support_workspace(w, h, p);
+    pl->ws_dense_bytes = dense_workspace(w, h);
+    pl->ws_post_bytes = post_workspace(w, h);
+    bool ok = dalloc(&pl->img, 2 * align_up(npx, 256)) == cudaSuccess &&
+              dalloc(&pl->descL, npx * 16) == cudaSuccess && dalloc(&pl->descR, npx * 16) == cudaSuccess &&
+              dalloc(&pl->dcan, (size_t)pl->nc * 2 + 16) == cudaSuccess &&
+              dalloc(&pl->countlist, pl->countlist_bytes) == cudaSuccess &&
+              dalloc(&pl->gridL, gbytes) == cudaSuccess && dalloc(&pl->gridR, gbytes) == cudaSuccess &&
+              dalloc(&pl->tri, sizeof(int32_t) * 3 * 2 * (size_t)pl->tri_cap) == cudaSuccess &&
+              dalloc(&pl->ws_support, pl->ws_support_bytes) == cudaSuccess &&
+              dalloc(&pl->ws_dense, pl->ws_dense_bytes) == cudaSuccess &&
+              dalloc(&pl->ws_post, pl->ws_post_bytes) == cudaSuccess &&
+              dalloc(&pl->dL, npx * 2) == cudaSuccess && dalloc(&pl->dR, npx * 2) == cudaSuccess &&
+              dalloc(&pl->post, npx * 4) == cudaSuccess &&
+              cudaMallocHost(reinterpret_cast<void **>(&pl->h_countlist), pl->countlist_bytes) == cudaSuccess &&
+              cudaMallocHost(reinterpret_cast<void **>(&pl->h_tri), sizeof(int32_t) * 3 * 2 * (size_t)pl->tri_cap) ==
+                  cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(pl);
+        return fail(ELAS_ERR_NO_MEMORY, "pipeline allocation for %dx%d failed", w, h);
+    }
+    pl->helper = new (std::nothrow) Helper();
+    if (!pl->helper) {
+        release(pl);
+        return fail(ELAS_ERR_NO_MEMORY, "helper thread");
+    }
+    *out = pl;
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR, int32_t pitch,
+                                         int16_t *dL, int16_t *dR, float *post, elas_stream stream) {
+    using namespace elas;
+    if (!pl || !imgL || !imgR || !dL) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
+    if (pitch < pl->w) return fail(ELAS_ERR_INVALID_ARG, "pitch %d < width %d", pitch, pl->w);
+    cudaStream_t st = to_stream(stream);
+    const int w = pl->w, h = pl->h;
+    const elas_params *p = &pl->p;
+    int16_t *list = reinterpret_cast<int16_t *>(pl->countlist + 16);
+    int32_t *count = reinterpret_cast<int32_t *>(pl->countlist);
+    elas_status s;
+    if ((s = launch_descriptors(imgL, imgR, w, h, pitch, pl->descL, pl->descR, st)) != ELAS_OK) return s;
+    if ((s = launch_support(pl->descL, pl->descR, w, h, p, pl->dcan, list, count, pl->gridL, pl->gridR,
+                            pl->ws_support, st)) != ELAS_OK)
+        return s;
+    if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, pl->countlist_bytes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return launch_status("support list to host");
+    const int n = *reinterpret_cast<const int32_t *>(pl->h_countlist);
+    if (n < 0 || n > pl->nc) return fail(ELAS_ERR_INTERNAL, "support count %d out of range", n);
+    const auto t0 = std::chrono::steady_clock::now();
+    int ntL = 0, ntR = 0;
+    if ((s = triangulate_both(pl, n, reinterpret_cast<const int16_t *>(pl->h_countlist + 16), &ntL, &ntR)) !=
+        ELAS_OK)
+        return s;
+    const auto t1 = std::chrono::steady_clock::now();
+    pl->stats.n_support = n;
+    pl->stats.n_tri_left = ntL;
+    pl->stats.n_tri_right = ntR;
+    pl->stats.triangulate_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (ntL + ntR > 0 &&
+        cudaMemcpyAsync(pl->tri, pl->h_tri, sizeof(int32_t) * 3 * (size_t)(ntL + ntR), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return launch_status("triangles to device");
+    int16_t *dpL = reinterpret_cast<int16_t *>(pl->ws_dense);
+    int16_t *dpR = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(pl->ws_dense) +
+                                               align_up((size_t)w * h * sizeof(int16_t), 256));
+    int16_t *outR = dR ? dR : pl->dR;
+    if ((s = launch_plane_prior(list, pl->tri, ntL, 0, w, h, p, dpL, st)) != ELAS_OK) return s;
+    if ((s = launch_plane_prior(list, pl->tri + 3 * (size_t)ntL, ntR, 1, w, h, p, dpR, st)) != ELAS_OK) return s;
+    if ((s = launch_dense(pl->descL, pl->descR, w, h, p, dpL, pl->gridL, 0, dL, st)) != ELAS_OK) return s;
+    if ((s = launch_dense(pl->descL, pl->descR, w, h, p, dpR, pl->gridR, 1, outR, st)) != ELAS_OK) return s;
+    if ((s = launch_lr_check(dL, outR, w, h, p->lr_threshold, nullptr, nullptr, st)) != ELAS_OK) return s;
+    if (post) return launch_post(dL, w, h, p, post, pl->ws_post, st);
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR,
+                                              int16_t *dL, int16_t *dR, float *post, elas_stream stream) {
+    using namespace elas;
+    if (!pl || !imgL || !imgR || !dL) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = to_stream(stream);
+    const size_t npx = (size_t)pl->w * pl->h;
+    uint8_t *iL = pl->img, *iR = pl->img + align_up(npx, 256);
+    if (cudaMemcpyAsync(iL, imgL, npx, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(iR, imgR, npx, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return launch_status("images to device");
+    elas_status s = elas_pipeline_run(pl, iL, iR, pl->w, pl->dL, pl->dR, post ? pl->post : nullptr, stream);
+    if (s != ELAS_OK) return s;
+    if (cudaMemcpyAsync(dL, pl->dL, npx * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return launch_status("left map to host");
+    if (dR && cudaMemcpyAsync(dR, pl->dR, npx * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return launch_status("right map to host");
+    if (post && cudaMemcpyAsync(post, pl->post, npx * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return launch_status("post map to host");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return launch_status("pipeline sync");
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st) {
+    if (!pl || !st) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL argument");
+    *st = pl->stats;
+    return ELAS_OK;
+}
+
+extern "C" void elas_pipeline_destroy(elas_pipeline *pl) { release(pl); }

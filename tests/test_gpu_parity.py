@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle, step by
+step and end to end, on seeded synthetic pairs shaped like the paper's
+workloads (Sec. VII: KITTI 1242x375, New Tsukuba 640x480) and on edge cases.
+Integer outputs must be bit-exact; the float post-processing must agree
+within 1e-4 absolute."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_07210_gb300 import synth
+from tests.gpu_util import dev, grid_as_i32, host, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+POST_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _B():
+    from paper_1802_07210_gb300 import binding
+    return binding
+
+
+def _cases():
+    small = synth.SMALL_320
+    ragged = synth.scaled_workload(203, 117, 48)
+    ragged.params["disp_min"] = 3
+    return [
+        ("small_320", small, 1),
+        ("ragged_203x117", ragged, 7),
+        ("vga_640", synth.VGA_640, 2),
+    ]
+
+
+CASES = _cases()
+
+
+@pytest.fixture(scope="module")
+def pairs():
+    out = {}
+    for name, wl, cfg in CASES:
+        L, R, gt = synth.workload_pair(wl, 0, cfg)
+        out[name] = (wl, L, R, oracle.pipeline(L, R, wl.params, postprocess_on=True))
+    return out
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_descriptors(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    dL, dR = B.elas_descriptors(dev(L), dev(R))
+    np.testing.assert_array_equal(host(dL), ref["descL"])
+    np.testing.assert_array_equal(host(dR), ref["descR"])
+    # single-image form and a pitched image
+    h, w = L.shape
+    np.testing.assert_array_equal(host(B.elas_descriptors(dev(R))), ref["descR"])
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_support_points(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    r = B.elas_support_points(dev(ref["descL"]), dev(ref["descR"]), wl.params)
+    np.testing.assert_array_equal(host(r["d_can"]), ref["dcan"])
+    n = int(host(r["count"])[0])
+    assert n == len(ref["list"])
+    np.testing.assert_array_equal(host(r["list"])[:n], ref["list"])
+    np.testing.assert_array_equal(host(r["grid_L"]), grid_as_i32(ref["gridL"]))
+    np.testing.assert_array_equal(host(r["grid_R"]), grid_as_i32(ref["gridR"]))
+
+
+def test_support_raw_and_filters(pairs):
+    """Each filter stage on its own: redundancy off exposes the consistency
+    output; the raw matcher is checked through a window size of 0 with
+    min_support 0 (every valid point kept)."""
+    B = _B()
+    wl, L, R, ref = pairs["small_320"]
+    prm = dict(wl.params, incon_window_size=0, incon_min_support=0, flags=oracle.FLAG_REDUNDANCY_OFF)
+    r = B.elas_support_points(dev(ref["descL"]), dev(ref["descR"]), prm)
+    np.testing.assert_array_equal(host(r["d_can"]), oracle.support_match(ref["descL"], ref["descR"], wl.params))
+    prm = dict(wl.params, flags=oracle.FLAG_REDUNDANCY_OFF)
+    r = B.elas_support_points(dev(ref["descL"]), dev(ref["descR"]), prm)
+    exp = oracle.filter_consistency(oracle.support_match(ref["descL"], ref["descR"], wl.params), wl.params)
+    np.testing.assert_array_equal(host(r["d_can"]), exp)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_plane_prior(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    h, w = L.shape
+    lst = dev(ref["list"])
+    for side, tri, exp in (("L", ref["triL"], ref["dplaneL"]), ("R", ref["triR"], ref["dplaneR"])):
+        dp = B.elas_plane_prior(lst, dev(tri.astype(np.int32)), w, h, wl.params, right=(side == "R"))
+        np.testing.assert_array_equal(host(dp), exp)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_dense_argmin(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    dL, dR = dev(ref["descL"]), dev(ref["descR"])
+    for right, dp, g, exp in ((False, ref["dplaneL"], ref["gridL"], ref["denseL"]),
+                              (True, ref["dplaneR"], ref["gridR"], ref["denseR"])):
+        out = B.elas_dense_argmin(dL, dR, wl.params, dev(dp), dev(grid_as_i32(g)), right=right)
+        np.testing.assert_array_equal(host(out), exp)
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_dense_test_modes(pairs, flags):
+    B = _B()
+    wl, L, R, ref = pairs["ragged_203x117"]
+    prm = dict(wl.params, flags=flags)
+    for right, dp, g in ((False, ref["dplaneL"], ref["gridL"]), (True, ref["dplaneR"], ref["gridR"])):
+        exp = oracle.dense(ref["descL"], ref["descR"], dp, g, prm, right=right)
+        out = B.elas_dense_argmin(dev(ref["descL"]), dev(ref["descR"]), prm, dev(dp), dev(grid_as_i32(g)),
+                                  right=right)
+        np.testing.assert_array_equal(host(out), exp)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_dense_match_and_lr(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    n = len(ref["list"])
+    dL, dR = B.elas_dense_match(dev(ref["descL"]), dev(ref["descR"]), wl.params, dev(ref["list"]), n,
+                                dev(ref["triL"].astype(np.int32)), dev(ref["triR"].astype(np.int32)),
+                                dev(grid_as_i32(ref["gridL"])), dev(grid_as_i32(ref["gridR"])))
+    np.testing.assert_array_equal(host(dL), ref["denseL"])
+    np.testing.assert_array_equal(host(dR), ref["denseR"])
+    mL, mR = B.elas_lr_check(dL, dR, wl.params["lr_threshold"])
+    np.testing.assert_array_equal(host(dL), ref["lrL"])
+    np.testing.assert_array_equal(host(dR), ref["lrR"])
+    np.testing.assert_array_equal(host(mL), ref["maskL"])
+    np.testing.assert_array_equal(host(mR), ref["maskR"])
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_postprocess(pairs, name):
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    prm = dict(wl.params, ipol_gap_width=3, filter_adaptive_mean=1)
+    exp = oracle.postprocess(ref["lrL"], prm)
+    out = host(B.elas_postprocess(dev(ref["lrL"]), prm))
+    assert np.abs(out - exp).max() <= POST_TOL
+    assert ((out < 0) == (exp < 0)).all()
+    for gap, mean in ((0, 1), (3, 0), (0, 0)):
+        prm = dict(wl.params, ipol_gap_width=gap, filter_adaptive_mean=mean)
+        exp = oracle.postprocess(ref["lrL"], prm)
+        out = host(B.elas_postprocess(dev(ref["lrL"]), prm))
+        assert np.abs(out - exp).max() <= POST_TOL
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_pipeline_end_to_end(pairs, name):
+    """The whole path through the pipeline handle (GPU kernels + the library's
+    own host triangulation) against the oracle pipeline."""
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    h, w = L.shape
+    pl = B.Pipeline(w, h, wl.params)
+    dL = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    dR = torch.empty_like(dL)
+    post = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    for _ in range(2):  # a second run reuses every buffer
+        pl.run(dev(L), dev(R), dL, dR, post)
+        np.testing.assert_array_equal(host(dL), ref["lrL"])
+        np.testing.assert_array_equal(host(dR), ref["lrR"])
+        assert np.abs(host(post) - ref["post"]).max() <= POST_TOL
+    st = pl.stats()
+    assert st["n_support"] == len(ref["list"])
+    assert st["n_tri_left"] == len(ref["triL"]) and st["n_tri_right"] == len(ref["triR"])
+    # host-buffer path
+    hL = torch.empty((h, w), dtype=torch.int16).pin_memory()
+    hpost = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    pl.run_host(torch.from_numpy(L).pin_memory(), torch.from_numpy(R).pin_memory(), hL, None, hpost)
+    np.testing.assert_array_equal(hL.numpy(), ref["lrL"])
+    assert np.abs(hpost.numpy() - ref["post"]).max() <= POST_TOL
+    pl.close()

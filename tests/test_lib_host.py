@@ -1,0 +1,93 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point include/elas_gb300.h declares, rejects bad arguments
+synchronously, and its host Delaunay step (Sec. III.A) reproduces the
+oracle's triangulation exactly."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1802_07210_gb300 import _lib, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "elas_gb300.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(elas_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(_lib.SIGNATURES), "binding table must mirror the header"
+
+
+def test_params_default_matches_oracle_defaults(orc):
+    p = _lib.params()
+    o = orc.params()
+    for name, _ in _lib.Params._fields_:
+        oname = "flags" if name == "test_flags" else name
+        assert getattr(p, name) == pytest.approx(getattr(o, oname)), name
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    L = _lib.lib()
+    st = L.elas_descriptors(None, None, 0, 10, 10, None, None, None)
+    assert st == 1 and b"image size" in L.elas_last_error()
+    p = _lib.params(disp_max=2000)
+    assert L.elas_support_workspace_bytes(64, 64, C.byref(p)) == 0
+    nt = C.c_int32(-5)
+    assert L.elas_triangulate(None, -1, 0, None, 0, C.byref(nt)) == 1
+
+
+def _canon(t):
+    return sorted(tuple(int(v) for v in np.roll(r, -int(np.argmin(r)))) for r in np.asarray(t).reshape(-1, 3))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_triangulation_matches_oracle_on_lattice_subsets(orc, seed):
+    rng = np.random.default_rng(seed)
+    gx, gy = int(rng.integers(2, 30)), int(rng.integers(2, 20))
+    pts = [(5 * i + 5, 5 * j + 5, int(rng.integers(0, 40)))
+           for j in range(gy) for i in range(gx) if rng.random() < rng.uniform(0.2, 1.0)]
+    lst = np.array(pts, np.int16).reshape(-1, 3)
+    for right in (0, 1):
+        cap = max(1, 2 * len(lst))
+        tri = np.empty((cap, 3), np.int32)
+        nt = C.c_int32(0)
+        _lib.check(_lib.lib().elas_triangulate(_lib.np_ptr(lst), len(lst), right, _lib.np_ptr(tri), cap,
+                                               C.byref(nt)))
+        got = tri[:nt.value]
+        exp = orc.triangulate(lst, right=bool(right))
+        # identical triangles with identical (counter-clockwise) orientation
+        assert _canon(got) == _canon(exp)
+
+
+def test_triangulation_matches_oracle_on_real_support(orc):
+    wl = synth.SMALL_320
+    L, R, _ = synth.workload_pair(wl, 3, 1)
+    dL, dR = orc.descriptors(L), orc.descriptors(R)
+    lst = orc.support_list(orc.support_points(dL, dR, wl.params), wl.params)
+    assert len(lst) > 300
+    for right in (0, 1):
+        cap = 2 * len(lst)
+        tri = np.empty((cap, 3), np.int32)
+        nt = C.c_int32(0)
+        _lib.check(_lib.lib().elas_triangulate(_lib.np_ptr(lst), len(lst), right, _lib.np_ptr(tri), cap,
+                                               C.byref(nt)))
+        assert _canon(tri[:nt.value]) == _canon(orc.triangulate(lst, right=bool(right)))
+
+
+def test_triangulation_capacity_error():
+    lst = np.array([[5, 5, 0], [10, 5, 0], [5, 10, 0], [10, 10, 0]], np.int16)
+    tri = np.empty((1, 3), np.int32)
+    nt = C.c_int32(0)
+    st = _lib.lib().elas_triangulate(_lib.np_ptr(lst), 4, 0, _lib.np_ptr(tri), 1, C.byref(nt))
+    assert st == 3 and nt.value == 2
