@@ -151,6 +151,37 @@ elas_status elas_support_points(const uint8_t *descL, const uint8_t *descR, int3
                                 void *workspace, size_t workspace_bytes, elas_stream stream);
 
 /*
+ * Support points with no allocation at all.  The paper has no counterpart:
+ * this is a deployment variant of elas_support_points for callers that are
+ * not allowed to allocate device memory -- for example a robot's real-time
+ * stereo loop that reserves all its memory at start-up and must not call
+ * cudaMalloc per frame (an allocation can block and synchronise the device),
+ * or a plug-in whose host application owns every device buffer.  The caller
+ * still passes the descriptors and all outputs; the scratch that
+ * elas_support_points takes as `workspace` comes instead from one static
+ * device array of ELAS_STATIC_SUPPORT_SCRATCH_BYTES, which every GPU that
+ * loads the library keeps until the process exits.
+ *   - Same arguments, semantics and results as elas_support_points, minus
+ *     the workspace.
+ *   - Limit: elas_support_workspace_bytes(w, h, p) must not exceed
+ *     ELAS_STATIC_SUPPORT_SCRATCH_BYTES (512 KiB: e.g. 1920x1080 or
+ *     2048x1536 with candidate_stepsize 5); larger sizes return
+ *     ELAS_ERR_CAPACITY with a message and launch nothing.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  No call allocates or frees memory.
+ *   - All calls share the one array, and it keeps the previous call's
+ *     contents.  Every scratch byte a call reads was written earlier in the
+ *     same call, so nothing has to be cleared, but calls that overlap on the
+ *     GPU (other streams, other threads) race on it: serialise them.
+ */
+#define ELAS_STATIC_SUPPORT_SCRATCH_BYTES (512u * 1024u)
+elas_status elas_support_points_static(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
+                                       const elas_params *p, int16_t *d_can, int16_t *list, int32_t cap,
+                                       int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
+                                       elas_stream stream);
+
+/*
  * Delaunay triangulation of the support list (Sec. III.A), on the host,
  * synchronous.  right = 0: points (u, v); right = 1: points (u - d, v), where
  * coincident points keep only the lowest list index.  Cocircular ties are

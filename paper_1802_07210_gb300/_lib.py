@@ -60,6 +60,7 @@ SIGNATURES = {
     "elas_descriptors": (C.c_int, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "elas_support_workspace_bytes": (_Z, [_I, _I, _P]),
     "elas_support_points": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P, _Z, _P]),
+    "elas_support_points_static": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_triangulate": (C.c_int, [_P, _I, _I, _P, _I, _P]),
     "elas_plane_prior": (C.c_int, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P]),
     "elas_dense_argmin": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P]),

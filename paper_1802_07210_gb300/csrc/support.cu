@@ -297,3 +297,66 @@ extern "C" elas_status elas_support_points(const uint8_t *descL, const uint8_t *
         return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, support_workspace(w, h, p));
     return launch_support(descL, descR, w, h, p, d_can, list, count, grid_L, grid_R, workspace, to_stream(stream));
 }
+
+// ---------------------------------------------------------------------------
+// Support points without any allocation by the caller or the library.
+//
+// The scratch (the unfiltered and the consistency-filtered candidate grids)
+// lives in one file-scope device array instead of a caller workspace.  Every
+// GPU that loads this library holds the array until the process exits.  Host
+// code cannot use the array's name as a device address, so its address is
+// looked up with cudaGetSymbolAddress, once per device, on the first call
+// made while that device is current.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace elas {
+
+static __device__ __align__(256) unsigned char g_support_scratch[ELAS_STATIC_SUPPORT_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+static elas_status static_support_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(ELAS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(ELAS_ERR_INTERNAL, "device ordinal %d above %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_support_scratch);
+        if (e != cudaSuccess)
+            return fail(ELAS_ERR_CUDA, "cudaGetSymbolAddress(support scratch): %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return ELAS_OK;
+}
+
+}  // namespace elas
+
+extern "C" elas_status elas_support_points_static(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
+                                                  const elas_params *p, int16_t *d_can, int16_t *list, int32_t cap,
+                                                  int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
+                                                  elas_stream stream) {
+    using namespace elas;
+    elas_status s = check_params(p, w, h);
+    if (s != ELAS_OK) return s;
+    if (!descL || !descR || !d_can || !list || !count) return fail(ELAS_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned(descL, 16) || !aligned(descR, 16)) return fail(ELAS_ERR_INVALID_ARG, "descriptors not 16-byte aligned");
+    const int64_t nc = (int64_t)(w / p->candidate_stepsize) * (h / p->candidate_stepsize);
+    if (cap < nc) return fail(ELAS_ERR_CAPACITY, "list capacity %d < %lld candidates", cap, (long long)nc);
+    const size_t need = support_workspace(w, h, p);
+    if (need > (size_t)ELAS_STATIC_SUPPORT_SCRATCH_BYTES)
+        return fail(ELAS_ERR_CAPACITY,
+                    "%dx%d with candidate step %d needs %zu scratch bytes; the static scratch holds %u "
+                    "(use elas_support_points with a workspace)",
+                    w, h, p->candidate_stepsize, need, (unsigned)ELAS_STATIC_SUPPORT_SCRATCH_BYTES);
+    void *scratch = nullptr;
+    if ((s = static_support_scratch(&scratch)) != ELAS_OK) return s;
+    return launch_support(descL, descR, w, h, p, d_can, list, count, grid_L, grid_R, scratch, to_stream(stream));
+}
