@@ -27,7 +27,7 @@ from paper_1802_07210_gb300 import synth  # noqa: E402
 METRIC = "Mpix/s & pairs/s at 640x480 D=256; p50/p99 served latency vs per-pair path"
 WORKLOADS = {"vga_640": (synth.VGA_640, 2), "small_320": (synth.SMALL_320, 1),
              "kitti_1242": (synth.KITTI_1242, 3)}
-KERNELS_PER_STEP = 15  # descriptor 1, support 5, plane prior 2, dense 2, LR 1, post 4
+KERNELS_PER_STEP = 11  # descriptor 1, support 4, prior binning 1, dense 1, LR 1, post 4
 
 
 def _peaks():
@@ -180,7 +180,18 @@ def main():
     dL = torch.empty((h, w), dtype=torch.int16, device=dev)
     dR = torch.empty_like(dL)
     post = torch.empty((h, w), dtype=torch.float32, device=dev) if wl.postprocess else None
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    clean_buf = torch.zeros(256 << 20, dtype=torch.uint8, device=dev)
+
+    class _Flush:
+        """Writes 256 MB (evicting everything), then reads another 256 MB so
+        that the dirty lines are written back before the timed region."""
+
+        def fill_(self, v):
+            flush_buf.fill_(v)
+            clean_buf.max()
+
+    flush = _Flush()
     stream = torch.cuda.current_stream()
 
     def step(i):
@@ -241,15 +252,25 @@ def main():
            "ms_per_step": e2e_ms / args.steps}
 
     # ---- per-stage kernel times (C-ABI calls bracketed by events) -------
-    stages = stage_times(B, torch, wl, pool[0], dev, stream, flush, reps=max(5, min(args.steps, 20)))
+    stages, work = stage_times(B, torch, wl, pool[0], dev, stream, flush, reps=max(5, min(args.steps, 20)))
     hbm_gbs, peak_kind = _peaks()
-    dense_bytes = 36 * px  # per map: 16 B reference + 16 B other descriptor + 2 B d_plane + 2 B output
-    t_dense = stages["dense_L_ms"]
-    roof = {"kernel": "dense_kernel (left reference)", "bound": "hbm", "achieved": dense_bytes / (t_dense * 1e-3) / 1e9,
-            "peak": hbm_gbs, "unit": "GB/s", "traffic": None,
-            "peak_source": "%s copy bandwidth, MEASURED_PEAKS.json" % peak_kind if peak_kind == "measured"
-            else "fallback 6.8 TB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    prm = B.as_params(wl.params)
+    evals = dense_work(work, prm, w, h)
+    probe = alu_peak(B, torch, dev, stream)
+    t_dense = stages["dense_match_ms"]
+    achieved = evals / (t_dense * 1e-3) / 1e9
+    peak = probe[0] / 1e9
+    # algorithmic HBM bytes of the same launch: both descriptor images read
+    # once (32 B/px), grid vectors and meshes (small), two int16 maps written
+    dense_bytes = 2 * (16 + 16 + 2) * px
+    roof = {"kernel": "cell_kernel<kDenseFused> (prior + dense argmin, both reference images)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SAD16/s", "frac": achieved / peak,
+            "traffic": None, "algorithmic_evals": evals,
+            "peak_source": "measured: probe kernel running the same SAD16 sequence on registers over all SMs",
+            "probe_variants_gsad16": {str(k): v / 1e9 for k, v in probe.items()},
+            "hbm": {"achieved_gbs": dense_bytes / (t_dense * 1e-3) / 1e9, "peak_gbs": hbm_gbs,
+                    "frac": dense_bytes / (t_dense * 1e-3) / 1e9 / hbm_gbs,
+                    "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_kind}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
@@ -257,7 +278,7 @@ def main():
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": {"workload": wl.name, "w": w, "h": h, "disp_max": wl.disp_max,
                            "pairs_per_step": 1, "pool": args.pool, "path": "plain one-pair path",
-                           "l2": "flushed (256 MB write) before every timed step"},
+                           "l2": "flushed before every timed step (256 MB write, then 256 MB read so no dirty lines remain)"},
                 "pairs_per_s": ws * args.steps / (total_ms / 1e3),
                 "triangulate_ms_median": float(np.median(tri_ms)),
                 "support_points": st["n_support"], "triangles": [st["n_tri_left"], st["n_tri_right"]],
@@ -271,7 +292,8 @@ def main():
 
 
 def stage_times(B, torch, wl, pair, dev, stream, flush, reps=10):
-    """Median device time of each stage's C-ABI call on one pair."""
+    """Median device time of each stage's C-ABI call on one pair, plus the
+    inputs needed to count the dense matcher's algorithmic work."""
     L, R, _ = pair
     prm = B.as_params(wl.params)
     tL, tR = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
@@ -286,15 +308,16 @@ def stage_times(B, torch, wl, pair, dev, stream, flush, reps=10):
     h, w = L.shape
     dpL = B.elas_plane_prior(lst, triL, w, h, prm, False)
     dpR = B.elas_plane_prior(lst, triR, w, h, prm, True)
-    dl = B.elas_dense_argmin(descL, descR, prm, dpL, sp["grid_L"], False)
-    dr = B.elas_dense_argmin(descL, descR, prm, dpR, sp["grid_R"], True)
+    dl, dr = B.elas_dense_match(descL, descR, prm, lst, n, triL, triR, sp["grid_L"], sp["grid_R"])
+    dl2, dr2 = dl.clone(), dr.clone()
     calls = {
         "descriptors_ms": lambda: B.elas_descriptors(tL, tR),
         "support_ms": lambda: B.elas_support_points(descL, descR, prm),
+        "dense_match_ms": lambda: B.elas_dense_match(descL, descR, prm, lst, n, triL, triR, sp["grid_L"],
+                                                     sp["grid_R"]),
         "plane_prior_L_ms": lambda: B.elas_plane_prior(lst, triL, w, h, prm, False),
-        "dense_L_ms": lambda: B.elas_dense_argmin(descL, descR, prm, dpL, sp["grid_L"], False),
-        "dense_R_ms": lambda: B.elas_dense_argmin(descL, descR, prm, dpR, sp["grid_R"], True),
-        "lr_check_ms": lambda: B.elas_lr_check(dl.clone(), dr.clone(), prm.lr_threshold, masks=False),
+        "dense_argmin_L_ms": lambda: B.elas_dense_argmin(descL, descR, prm, dpL, sp["grid_L"], False),
+        "lr_check_ms": lambda: B.elas_lr_check(dl2, dr2, prm.lr_threshold, masks=False),
         "postprocess_ms": lambda: B.elas_postprocess(dl, prm),
     }
     out = {}
@@ -310,7 +333,70 @@ def stage_times(B, torch, wl, pair, dev, stream, flush, reps=10):
             b.synchronize()
             ts.append(a.elapsed_time(b))
         out[name] = float(np.median(ts))
-    return out
+    work = dict(descL=descL.cpu().numpy(), descR=descR.cpu().numpy(), dpL=dpL.cpu().numpy(),
+                dpR=dpR.cpu().numpy(), gridL=sp["grid_L"].cpu().numpy(), gridR=sp["grid_R"].cpu().numpy())
+    return out, work
+
+
+def dense_work(work, prm, w, h):
+    """Candidate evaluations of the dense step, both reference images:
+    |S(p)| = |(grid(cell) U plane window) within the admissible range| per
+    matched pixel (each a 16-byte SAD)."""
+    G = prm.grid_size
+    sr = prm.sradius
+    total = 0
+    vv, uu = np.mgrid[0:h, 0:w]
+    for side in (0, 1):
+        ref = work["descR"] if side else work["descL"]
+        dp = (work["dpR"] if side else work["dpL"]).astype(np.int64)
+        grid = (work["gridR"] if side else work["gridL"]).view(np.uint32)
+        tex = np.abs(ref.astype(np.int32) - 128).sum(-1)
+        ok = (uu >= 2) & (uu <= w - 3) & (vv >= 2) & (vv <= h - 3) & (tex >= prm.match_texture) & (dp >= 0)
+        dlim = np.minimum(prm.disp_max, (w - 3 - uu) if side else (uu - 2))
+        gh, gw = grid.shape[:2]
+        for cy in range(gh):
+            for cx in range(gw):
+                bits = np.unpackbits(grid[cy, cx].view(np.uint8), bitorder="little")
+                cand = np.nonzero(bits)[0]
+                cand = cand[(cand >= prm.disp_min) & (cand <= prm.disp_max)]
+                ys, xs = slice(cy * G, min(h, cy * G + G)), slice(cx * G, min(w, cx * G + G))
+                m = ok[ys, xs]
+                if not m.any():
+                    continue
+                dl = dlim[ys, xs][m]
+                d0 = dp[ys, xs][m]
+                cnt = np.searchsorted(cand, dl, side="right")
+                inmask = np.zeros(prm.disp_max + 2, bool)
+                inmask[cand] = True
+                for k in range(-sr, sr + 1):
+                    d = d0 + k
+                    valid = (d >= prm.disp_min) & (d <= dl)
+                    cnt = cnt + (valid & ~inmask[np.clip(d, 0, prm.disp_max + 1)])
+                total += int(cnt.sum())
+    return total
+
+
+def alu_peak(B, torch, dev, stream):
+    """SAD16/s of the probe kernel (the SAD sequence alone, registers only,
+    every SM): the ALU ceiling of the matchers."""
+    import ctypes as C
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sm * 8, 256, 2048
+    scratch = torch.empty(blocks * threads, dtype=torch.int32, device=dev)
+    res = {}
+    for variant in (0, 1, 2):
+        args = (variant, blocks, threads, iters, C.c_void_p(scratch.data_ptr()), C.c_void_p(stream.cuda_stream))
+        B.check(B.lib().elas_probe_sad16(*args))
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.check(B.lib().elas_probe_sad16(*args))
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res[variant] = blocks * threads * iters * 8 / (min(ts) * 1e-3)
+    return res
 
 
 if __name__ == "__main__":

@@ -195,6 +195,25 @@ elas_status elas_triangulate(const int16_t *list, int32_t n, int32_t right, int3
                              int32_t cap, int32_t *ntri);
 
 /*
+ * Delaunay triangulation of the support list on the GPU (Sec. III.A), the
+ * same unique triangulation as elas_triangulate (symbolic tie-break on list
+ * indices, coincident right-image points keep the lowest index).  Each point
+ * builds its own star by exact gift-wrapping among its neighbours, certified
+ * by the circumdisc test; uncertified stars are redone with a larger radius.
+ * list: device int16 [cap][3]; count: device int32, number of points (<= cap);
+ * right: 0 = (u, v), 1 = (u - d, v).  Outputs on the device: tri int32
+ * [cap_tri][3] (counter-clockwise, each triangle once, deterministic order),
+ * *ntri = triangle count, or -1 if the triangulation failed.  cap_tri must be
+ * >= 2*cap + 8.  workspace: device, 256-byte aligned,
+ * >= elas_triangulate_device_workspace_bytes(cap, w, h).  Asynchronous.
+ */
+size_t elas_triangulate_device_workspace_bytes(int32_t cap, int32_t w, int32_t h);
+elas_status elas_triangulate_device(const int16_t *list, const int32_t *count, int32_t cap, int32_t w,
+                                    int32_t h, int32_t right, int32_t *tri, int32_t cap_tri,
+                                    int32_t *ntri, void *workspace, size_t workspace_bytes,
+                                    elas_stream stream);
+
+/*
  * Slanted-plane prior (Sec. III.A; image-sized prior matrix, Sec. VI.D).
  * For each triangle, with its vertices taken in ascending list index:
  * det = du1*dv2 - du2*dv1, a = (float)(dd1*dv2 - dd2*dv1) / (float)det,
@@ -202,11 +221,15 @@ elas_status elas_triangulate(const int16_t *list, int32_t n, int32_t right, int3
  * left to right, no fused multiply-add).  Pixels owned by the triangle under
  * integer edge functions with the top-left rule get
  * d_plane = clamp(floor((a*u + b*v) + c + 0.5), disp_min, disp_max); all
- * other pixels get -1.  list/tri/d_plane: device; d_plane int16 [h][w].
+ * other pixels get -1.  right = 1: vertices at (u - d, v).
+ * list/tri/d_plane: device; d_plane int16 [h][w].  workspace: device,
+ * 256-byte aligned, >= elas_plane_prior_workspace_bytes(ntri).
  */
+size_t elas_plane_prior_workspace_bytes(int32_t ntri);
 elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,
                              int32_t right, int32_t w, int32_t h, const elas_params *p,
-                             int16_t *d_plane, elas_stream stream);
+                             int16_t *d_plane, void *workspace, size_t workspace_bytes,
+                             elas_stream stream);
 
 /*
  * Dense argmin for one reference image (Sec. III.A, Fig. 1(h)).
@@ -226,10 +249,13 @@ elas_status elas_dense_argmin(const uint8_t *descL, const uint8_t *descR, int32_
                               int32_t right, int16_t *out, elas_stream stream);
 
 /*
- * Plane prior + dense argmin for both reference images.  list (device) is
+ * Plane prior + dense argmin for both reference images (elas_plane_prior
+ * then elas_dense_argmin on each side, in two launches).  list (device) is
  * the support list of n points, triL/triR (device) the triangulations in
  * left and right coordinates, grid_L/grid_R the grid vectors.  Outputs dL,
- * dR int16 [h][w].  workspace: device, >= elas_dense_workspace_bytes().
+ * dR int16 [h][w]; each mesh has at most 2*(w/step)*(h/step)+8 triangles.
+ * workspace: device, 256-byte aligned, >= elas_dense_workspace_bytes() (it
+ * holds the two prior maps).
  */
 size_t elas_dense_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
 elas_status elas_dense_match(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
@@ -278,7 +304,8 @@ typedef struct {
     int32_t n_support;     /* support points of the last pair           */
     int32_t n_tri_left;    /* triangles, left coordinates                */
     int32_t n_tri_right;   /* triangles, right coordinates               */
-    double  triangulate_ms;/* host wall time of both triangulations      */
+    double  triangulate_ms;/* host wall time of both triangulations (host
+                              triangulation only, else 0)               */
 } elas_pipeline_stats;
 
 elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_params *p, elas_pipeline **out);
@@ -287,6 +314,12 @@ elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL, const uint
                               elas_stream stream);
 elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR,
                                    int16_t *dL, int16_t *dR, float *post, elas_stream stream);
+/* Where the pipeline triangulates: on_gpu = 1 (default) runs
+ * elas_triangulate_device inside the step, with no host synchronisation;
+ * on_gpu = 0 copies the support list to the host and runs elas_triangulate
+ * (left and right meshes on two threads).  Both give identical meshes. */
+elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu);
+/* Counts of the last pair; waits for the pipeline's last stream. */
 elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st);
 void elas_pipeline_destroy(elas_pipeline *pl);
 

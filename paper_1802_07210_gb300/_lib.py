@@ -52,7 +52,7 @@ class PipelineStats(C.Structure):
 
 _P, _I, _Z = C.c_void_p, C.c_int32, C.c_size_t
 
-# name -> (restype, argtypes), exactly the declarations of include/elas_gb300.h
+# name -> (restype, argtypes), exactly the declarations of include/*.h
 SIGNATURES = {
     "elas_params_default": (C.c_int, [_P]),
     "elas_last_error": (C.c_char_p, []),
@@ -62,7 +62,10 @@ SIGNATURES = {
     "elas_support_points": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P, _Z, _P]),
     "elas_support_points_static": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_triangulate": (C.c_int, [_P, _I, _I, _P, _I, _P]),
-    "elas_plane_prior": (C.c_int, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P]),
+    "elas_triangulate_device_workspace_bytes": (_Z, [_I, _I, _I]),
+    "elas_triangulate_device": (C.c_int, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _Z, _P]),
+    "elas_plane_prior_workspace_bytes": (_Z, [_I]),
+    "elas_plane_prior": (C.c_int, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _Z, _P]),
     "elas_dense_argmin": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P]),
     "elas_dense_workspace_bytes": (_Z, [_I, _I, _P]),
     "elas_dense_match": (C.c_int, [_P, _P, _I, _I, _P, _P, _I, _P, _I, _P, _I, _P, _P, _P, _P,
@@ -73,8 +76,10 @@ SIGNATURES = {
     "elas_pipeline_create": (C.c_int, [_I, _I, _P, _P]),
     "elas_pipeline_run": (C.c_int, [_P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_pipeline_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "elas_pipeline_set_triangulation": (C.c_int, [_P, _I]),
     "elas_pipeline_stats_get": (C.c_int, [_P, _P]),
     "elas_pipeline_destroy": (None, [_P]),
+    "elas_probe_sad16": (C.c_int, [_I, _I, _I, _I, _P, _P]),
 }
 
 _lib = None

@@ -95,15 +95,32 @@ def elas_triangulate(lst, right=False):
     return tri[:nt.value].copy()
 
 
+def elas_triangulate_device(lst, count, w, h, right=False, stream=None):
+    """lst: device int16 [cap, 3]; count: device int32 [1].  Returns the
+    device triangle buffer [2*cap+8, 3] and the device count tensor [1]."""
+    cap = lst.shape[0]
+    cap_tri = 2 * cap + 8
+    tri = torch.empty((cap_tri, 3), dtype=torch.int32, device=lst.device)
+    nt = torch.empty((1,), dtype=torch.int32, device=lst.device)
+    nb = lib().elas_triangulate_device_workspace_bytes(cap, w, h)
+    ws = _workspace(nb, lst.device)
+    check(lib().elas_triangulate_device(_dev(lst, torch.int16, "list"), _dev(count, torch.int32, "count"), cap, w,
+                                        h, int(bool(right)), C.c_void_p(tri.data_ptr()), cap_tri,
+                                        C.c_void_p(nt.data_ptr()), C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+    return tri, nt
+
+
 def elas_plane_prior(lst, tri, w, h, prm=None, right=False, stream=None):
     prm = as_params(prm)
     dev = lst.device
     out = torch.empty((h, w), dtype=torch.int16, device=dev)
     n = lst.shape[0]
     ntri = tri.shape[0]
+    nb = lib().elas_plane_prior_workspace_bytes(ntri)
+    ws = _workspace(nb, dev)
     check(lib().elas_plane_prior(_dev(lst, torch.int16, "list"), n, _dev(tri, torch.int32, "tri"), ntri,
                                  int(bool(right)), w, h, C.byref(prm), C.c_void_p(out.data_ptr()),
-                                 _stream(stream)))
+                                 C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
     return out
 
 
@@ -164,11 +181,12 @@ def elas_postprocess(d, prm=None, stream=None):
 class Pipeline:
     """Owner of an ``elas_pipeline`` handle for one image size."""
 
-    def __init__(self, w, h, prm=None):
+    def __init__(self, w, h, prm=None, gpu_triangulation=True):
         self.w, self.h = w, h
         self.prm = as_params(prm)
         self._h = C.c_void_p()
         check(lib().elas_pipeline_create(w, h, C.byref(self.prm), C.byref(self._h)))
+        check(lib().elas_pipeline_set_triangulation(self._h, int(bool(gpu_triangulation))))
 
     def run(self, imgL, imgR, dL, dR=None, post=None, stream=None):
         """Device tensors in and out (dL/dR int16 [h, w], post float32)."""

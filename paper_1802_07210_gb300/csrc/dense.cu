@@ -2,203 +2,445 @@
 // dense per-pixel argmin of descriptor SAD plus tabulated prior over the
 // grid-vector and plane-neighbourhood candidates (Sec. III.A, Fig. 1(h)).
 //
-// plane_prior_kernel  one warp per triangle (grid-stride over triangles):
-//                     every lane evaluates the FP32 plane in the fixed order,
-//                     lanes stride the bounding box and write the pixels the
-//                     triangle owns under the top-left rule.  Ownership is
-//                     unique, so no two writes ever race.
-// dense_kernel        one thread per pixel in 32x8 tiles; the reference
-//                     descriptor stays in registers, the other image's
-//                     descriptors are 16-byte read-only loads; the cell's
-//                     grid vector is walked bit by bit, then the plane
-//                     neighbourhood not already covered by the mask.
+// plane_raster_kernel  one warp per triangle (grid-stride), both meshes in one
+//                      launch.  Every lane evaluates the FP32 plane in the
+//                      fixed order.  For each row of the bounding box the
+//                      owned x-range follows from the three integer edge
+//                      functions (E >= 0 on owned edges, E >= 1 otherwise);
+//                      each pixel of that range (widened by one) is
+//                      confirmed with the edge functions themselves before
+//                      it is written, so ownership is exactly the top-left
+//                      rule.  One row per lane; triangles whose bounding
+//                      box exceeds kBigArea pixels are listed instead and
+//                      drawn by plane_raster_big_kernel, one CTA each (rows
+//                      over warps, lanes across x), so they leave no tail.
+// cell_kernel          one CTA per grid-vector cell (G x G pixels, which share
+//                      one candidate mask) and per reference image.  It
+//                      expands the cell's mask into an ascending candidate
+//                      list in shared memory, then per pixel takes the
+//                      minimum of the packed key (cost, d) over the list (no
+//                      prior) and over the plane neighbourhood (with prior).
+//                      A d in both sets is evaluated twice, without and with
+//                      the prior; as P <= 0 the second never loses, so the
+//                      result is the argmin over the union.  The list is
+//                      uniform across the CTA: no divergence, broadcast
+//                      shared loads.
 #include "launch.cuh"
 
 namespace elas {
 
-struct PriorArgs {
-    int w, h, dmin, dmax, right;
-};
+constexpr int kKeyBias = 65536;  // keeps (cost + bias) positive; |P| <= 65535
 
 __device__ __forceinline__ bool edge_owned(int px, int py, int qx, int qy) {
     return (qy == py && qx > px) || (qy < py);
 }
 
-__global__ void __launch_bounds__(256)
-plane_prior_kernel(const int16_t *__restrict__ list, const int32_t *__restrict__ tri, int ntri, PriorArgs a,
-                   int16_t *__restrict__ dplane) {
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntri; t += gridDim.x * wpb) {
-        int i0 = __ldg(tri + 3 * t), i1 = __ldg(tri + 3 * t + 1), i2 = __ldg(tri + 3 * t + 2);
-        // canonical vertex order: ascending list index
-        if (i1 < i0) { int s = i0; i0 = i1; i1 = s; }
-        if (i2 < i1) { int s = i1; i1 = i2; i2 = s; }
-        if (i1 < i0) { int s = i0; i0 = i1; i1 = s; }
-        int X[3], Y[3], Z[3];
-        const int id[3] = {i0, i1, i2};
+__device__ __forceinline__ int floor_div(int n, int d) {  // d > 0
+    const int q = n / d;
+    return (n % d != 0 && n < 0) ? q - 1 : q;
+}
+__device__ __forceinline__ int ceil_div(int n, int d) {  // d > 0
+    const int q = n / d;
+    return (n % d != 0 && n > 0) ? q + 1 : q;
+}
+
+// Narrows [lo, hi] to the x where edge (px,py)->(qx,qy) admits row y.
+__device__ __forceinline__ void edge_span(int px, int py, int qx, int qy, int own, int y, int &lo, int &hi) {
+    const int A = py - qy;
+    const int B = (qx - px) * (y - py) + (qy - py) * px;
+    const int t = own ? 0 : 1;
+    if (A > 0)
+        lo = max(lo, ceil_div(t - B, A));
+    else if (A < 0)
+        hi = min(hi, floor_div(B - t, -A));
+    else if (B < t)
+        hi = lo - 1;
+}
+
+struct RasterSide {
+    const int32_t *tri;
+    int ntri, right;            // ntri: used when ntri_dev is NULL
+    int16_t *dplane;
+    const int32_t *ntri_dev;    // device triangle count (negative = none)
+};
+
+__device__ __forceinline__ int side_ntri(const RasterSide &S) {
+    return S.ntri_dev ? max(0, *S.ntri_dev) : S.ntri;
+}
+
+struct RasterArgs {
+    const int16_t *list;
+    RasterSide s[2];
+    int32_t *big;     // (side << 30) | triangle, for triangles left to plane_raster_big_kernel
+    int32_t *nbig;    // count of big (zeroed before the launch)
+    int w, h, dmin, dmax;
+};
+
+constexpr int kBigArea = 1024;  // bounding-box pixels above which a triangle is "big"
+
+// Plane and positively oriented integer edges of one triangle.
+struct TriGeom {
+    float fa, fb, fc;
+    int ex0, ey0, ex1, ey1, ex2, ey2, o0, o1, o2;
+    int xmin, xmax, ymin, ymax;
+    bool empty;
+};
+
+__device__ __forceinline__ TriGeom tri_geom(const int16_t *__restrict__ list, const int32_t *__restrict__ tri, int t,
+                                            int right, int w, int h) {
+    TriGeom g;
+    int i0 = __ldg(tri + 3 * t), i1 = __ldg(tri + 3 * t + 1), i2 = __ldg(tri + 3 * t + 2);
+    // canonical vertex order: ascending list index
+    if (i1 < i0) { const int q = i0; i0 = i1; i1 = q; }
+    if (i2 < i1) { const int q = i1; i1 = i2; i2 = q; }
+    if (i1 < i0) { const int q = i0; i0 = i1; i1 = q; }
+    int X[3], Y[3], Z[3];
+    const int id[3] = {i0, i1, i2};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int u = __ldg(list + 3 * id[k]), v = __ldg(list + 3 * id[k] + 1), d = __ldg(list + 3 * id[k] + 2);
-            X[k] = a.right ? u - d : u;
-            Y[k] = v;
-            Z[k] = d;
-        }
-        const int det = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
-        if (det == 0) continue;
-        const int na = (Z[1] - Z[0]) * (Y[2] - Y[0]) - (Z[2] - Z[0]) * (Y[1] - Y[0]);
-        const int nb = (X[1] - X[0]) * (Z[2] - Z[0]) - (X[2] - X[0]) * (Z[1] - Z[0]);
-        const float fa = __fdiv_rn(__int2float_rn(na), __int2float_rn(det));
-        const float fb = __fdiv_rn(__int2float_rn(nb), __int2float_rn(det));
-        float fc = __fsub_rn(__int2float_rn(Z[0]), __fmul_rn(fa, __int2float_rn(X[0])));
-        fc = __fsub_rn(fc, __fmul_rn(fb, __int2float_rn(Y[0])));
-        // positively oriented order for the edge functions
-        int ex[3], ey[3];
-        ex[0] = X[0];
-        ey[0] = Y[0];
-        if (det > 0) {
-            ex[1] = X[1]; ey[1] = Y[1]; ex[2] = X[2]; ey[2] = Y[2];
-        } else {
-            ex[1] = X[2]; ey[1] = Y[2]; ex[2] = X[1]; ey[2] = Y[1];
-        }
-        const int xmin = max(0, min(X[0], min(X[1], X[2]))), xmax = min(a.w - 1, max(X[0], max(X[1], X[2])));
-        const int ymin = max(0, min(Y[0], min(Y[1], Y[2]))), ymax = min(a.h - 1, max(Y[0], max(Y[1], Y[2])));
-        if (xmax < xmin || ymax < ymin) continue;
-        const int bw = xmax - xmin + 1;
-        const int npx = bw * (ymax - ymin + 1);
-        const bool own0 = edge_owned(ex[0], ey[0], ex[1], ey[1]);
-        const bool own1 = edge_owned(ex[1], ey[1], ex[2], ey[2]);
-        const bool own2 = edge_owned(ex[2], ey[2], ex[0], ey[0]);
-        for (int k = lane; k < npx; k += 32) {
-            const int yy = ymin + k / bw, xx = xmin + k % bw;
-            const int e0 = (ex[1] - ex[0]) * (yy - ey[0]) - (ey[1] - ey[0]) * (xx - ex[0]);
-            const int e1 = (ex[2] - ex[1]) * (yy - ey[1]) - (ey[2] - ey[1]) * (xx - ex[1]);
-            const int e2 = (ex[0] - ex[2]) * (yy - ey[2]) - (ey[0] - ey[2]) * (xx - ex[2]);
-            const bool in = (e0 > 0 || (e0 == 0 && own0)) && (e1 > 0 || (e1 == 0 && own1)) &&
-                            (e2 > 0 || (e2 == 0 && own2));
-            if (!in) continue;
-            const float t1 = __fmul_rn(fa, __int2float_rn(xx));
-            const float t2 = __fmul_rn(fb, __int2float_rn(yy));
-            const float mu = __fadd_rn(__fadd_rn(t1, t2), fc);
-            int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
-            dp = min(max(dp, a.dmin), a.dmax);
-            dplane[(size_t)yy * a.w + xx] = (int16_t)dp;
-        }
+    for (int k = 0; k < 3; ++k) {
+        const int u = __ldg(list + 3 * id[k]), v = __ldg(list + 3 * id[k] + 1);
+        const int d = __ldg(list + 3 * id[k] + 2);
+        X[k] = right ? u - d : u;
+        Y[k] = v;
+        Z[k] = d;
+    }
+    const int det = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
+    const int na = (Z[1] - Z[0]) * (Y[2] - Y[0]) - (Z[2] - Z[0]) * (Y[1] - Y[0]);
+    const int nb = (X[1] - X[0]) * (Z[2] - Z[0]) - (X[2] - X[0]) * (Z[1] - Z[0]);
+    g.empty = det == 0;
+    const float fdet = __int2float_rn(det == 0 ? 1 : det);
+    g.fa = __fdiv_rn(__int2float_rn(na), fdet);
+    g.fb = __fdiv_rn(__int2float_rn(nb), fdet);
+    const float c = __fsub_rn(__int2float_rn(Z[0]), __fmul_rn(g.fa, __int2float_rn(X[0])));
+    g.fc = __fsub_rn(c, __fmul_rn(g.fb, __int2float_rn(Y[0])));
+    g.ex0 = X[0];
+    g.ey0 = Y[0];
+    g.ex1 = det > 0 ? X[1] : X[2];
+    g.ey1 = det > 0 ? Y[1] : Y[2];
+    g.ex2 = det > 0 ? X[2] : X[1];
+    g.ey2 = det > 0 ? Y[2] : Y[1];
+    g.o0 = edge_owned(g.ex0, g.ey0, g.ex1, g.ey1);
+    g.o1 = edge_owned(g.ex1, g.ey1, g.ex2, g.ey2);
+    g.o2 = edge_owned(g.ex2, g.ey2, g.ex0, g.ey0);
+    g.xmin = max(0, min(X[0], min(X[1], X[2])));
+    g.xmax = min(w - 1, max(X[0], max(X[1], X[2])));
+    g.ymin = max(0, min(Y[0], min(Y[1], Y[2])));
+    g.ymax = min(h - 1, max(Y[0], max(Y[1], Y[2])));
+    if (g.xmax < g.xmin || g.ymax < g.ymin) g.empty = true;
+    return g;
+}
+
+// Writes the owned pixels of row y of a triangle, x from `first` in steps of
+// `stride` (lanes of a warp stride 32, a single thread strides 1).
+__device__ __forceinline__ void raster_row(const TriGeom &g, int y, int first, int stride, int w, int dmin, int dmax,
+                                           int16_t *__restrict__ dplane) {
+    int lo = g.xmin, hi = g.xmax;
+    edge_span(g.ex0, g.ey0, g.ex1, g.ey1, g.o0, y, lo, hi);
+    edge_span(g.ex1, g.ey1, g.ex2, g.ey2, g.o1, y, lo, hi);
+    edge_span(g.ex2, g.ey2, g.ex0, g.ey0, g.o2, y, lo, hi);
+    lo = max(g.xmin, lo - 1);
+    hi = min(g.xmax, hi + 1);
+    for (int x = lo + first; x <= hi; x += stride) {
+        const int e0 = (g.ex1 - g.ex0) * (y - g.ey0) - (g.ey1 - g.ey0) * (x - g.ex0);
+        const int e1 = (g.ex2 - g.ex1) * (y - g.ey1) - (g.ey2 - g.ey1) * (x - g.ex1);
+        const int e2 = (g.ex0 - g.ex2) * (y - g.ey2) - (g.ey0 - g.ey2) * (x - g.ex2);
+        if (!((e0 > 0 || (e0 == 0 && g.o0)) && (e1 > 0 || (e1 == 0 && g.o1)) && (e2 > 0 || (e2 == 0 && g.o2))))
+            continue;
+        const float t1 = __fmul_rn(g.fa, __int2float_rn(x));
+        const float t2 = __fmul_rn(g.fb, __int2float_rn(y));
+        const float mu = __fadd_rn(__fadd_rn(t1, t2), g.fc);
+        const int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
+        dplane[(size_t)y * w + x] = (int16_t)min(max(dp, dmin), dmax);
     }
 }
 
-struct DenseArgs {
-    int w, h, dmin, dmax, sradius, match_texture, G, gw, nw, dir, full, prior_off;
+__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
+    const int side = blockIdx.y;
+    const RasterSide S = side ? a.s[1] : a.s[0];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int ntri = side_ntri(S);
+    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntri; t += gridDim.x * wpb) {
+        const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
+        if (g.empty) continue;
+        const int rows = g.ymax - g.ymin + 1;
+        if ((g.xmax - g.xmin + 1) * rows > kBigArea) {  // spread over every CTA later
+            if (lane == 0) a.big[atomicAdd(a.nbig, 1)] = (side << 30) | t;
+            continue;
+        }
+        for (int r = lane; r < rows; r += 32) raster_row(g, g.ymin + r, 0, 1, a.w, a.dmin, a.dmax, S.dplane);
+    }
+}
+
+// Big triangles, one CTA each (grid-stride over the list): the CTA's warps
+// take the rows in turn and their lanes stride across x.
+__global__ void __launch_bounds__(256) plane_raster_big_kernel(RasterArgs a) {
+    const int n = *a.nbig;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int e = a.big[k];
+        const int side = e >> 30, t = e & ((1 << 30) - 1);
+        const RasterSide S = side ? a.s[1] : a.s[0];
+        const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
+        const int rows = g.ymax - g.ymin + 1;
+        for (int r = warp; r < rows; r += wpb) raster_row(g, g.ymin + r, lane, 32, a.w, a.dmin, a.dmax, S.dplane);
+    }
+}
+
+struct CellSide {
+    const uint4 *ref, *oth;
+    const uint32_t *grid;   // [gh][gw][nw]
+    const int16_t *dplane;  // prior map (may be NULL with full range)
+    int16_t *out;
+    int dir;
+};
+
+struct CellArgs {
+    CellSide s[2];
+    int w, h, G, gw, nw, dmin, dmax, sradius, match_texture, full, prior_off;
     int P[kMaxSradius + 1];
 };
 
-__global__ void __launch_bounds__(256)
-dense_kernel(const uint4 *__restrict__ ref, const uint4 *__restrict__ oth, const int16_t *__restrict__ dplane,
-             const uint32_t *__restrict__ grid, DenseArgs a, int16_t *__restrict__ out) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
-    if (u >= a.w || v >= a.h) return;
-    int res = -1;
-    const size_t row = (size_t)v * a.w;
-    if (u >= 2 && u <= a.w - 3 && v >= 2 && v <= a.h - 3) {
-        const uint4 r = __ldg(ref + row + u);
-        const int dp = a.full ? -1 : __ldg(dplane + row + u);
-        if ((int)texture16(r) >= a.match_texture && (a.full || dp >= 0)) {
-            // admissible disparities: 2 <= u + dir*d <= w-3
-            int lo, hi;
-            if (a.dir < 0) {
-                lo = max(a.dmin, u - (a.w - 3));
-                hi = min(a.dmax, u - 2);
-            } else {
-                lo = max(a.dmin, 2 - u);
-                hi = min(a.dmax, a.w - 3 - u);
+__global__ void __launch_bounds__(512) cell_kernel(CellArgs a) {
+    __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + 4];
+    __shared__ int s_P[kMaxSradius + 1];
+    __shared__ int s_nlist;
+
+    const CellSide S = blockIdx.z ? a.s[1] : a.s[0];
+    const int cx = blockIdx.x, cy = blockIdx.y;
+    const int x0 = cx * a.G, y0 = cy * a.G;
+    const int cw = min(a.G, a.w - x0), ch = min(a.G, a.h - y0);
+    const int npx = cw * ch;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cell = cy * a.gw + cx;
+
+    // ---- candidate list of the cell, ascending ---------------------------------
+    if (tid <= kMaxSradius) s_P[tid] = a.P[tid];
+    if (!a.full && warp == 0) {
+        const uint32_t *g = S.grid + (size_t)cell * a.nw;
+        int base = 0;
+        for (int w0 = 0; w0 < a.nw; w0 += 32) {
+            const int wi = w0 + lane;
+            uint32_t m = wi < a.nw ? __ldg(g + wi) : 0u;
+            // keep the bits inside [dmin, dmax]
+            const int lo = a.dmin - 32 * wi, hi = a.dmax - 32 * wi;
+            if (lo > 0) m &= lo >= 32 ? 0u : (0xFFFFFFFFu << lo);
+            if (hi < 31) m &= hi < 0 ? 0u : (0xFFFFFFFFu >> (31 - hi));
+            const int c = __popc(m);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
             }
-            int bc = 0x7FFFFFFF, bd = -1;
-            const uint4 *orow = oth + row;
-            if (a.full) {
-                for (int d = lo; d <= hi; ++d) {  // no plane, so no prior term
-                    const int c = (int)sad16(r, __ldg(orow + u + a.dir * d));
-                    if (c < bc) { bc = c; bd = d; }
-                }
-            } else {
-                const uint32_t *cell = grid + ((size_t)(v / a.G) * a.gw + (u / a.G)) * a.nw;
-                for (int wd = 0; wd < a.nw; ++wd) {
-                    uint32_t m = __ldg(cell + wd);
-                    while (m) {
-                        const int d = wd * 32 + __ffs(m) - 1;
-                        m &= m - 1;
-                        if (d < lo || d > hi) continue;
-                        int c = (int)sad16(r, __ldg(orow + u + a.dir * d));
-                        const int ad = abs(d - dp);
-                        if (!a.prior_off && ad <= a.sradius) c += a.P[ad];
-                        if (c < bc || (c == bc && d < bd)) { bc = c; bd = d; }
+            int pos = base + incl - c;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                s_list[pos++] = (uint16_t)(32 * wi + b);
+            }
+            base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+        // pad to a multiple of 4 with a disparity above every dmax
+        if (lane < 4) s_list[base + lane] = (uint16_t)2047;
+        if (lane == 0) s_nlist = base;
+    }
+    __syncthreads();
+    const int nlist4 = a.full ? 0 : (s_nlist + 3) & ~3;
+
+    // ---- per-pixel argmin -------------------------------------------------------
+    for (int p = tid; p < npx; p += blockDim.x) {
+        const int x = x0 + p % cw, y = y0 + p / cw;
+        const size_t row = (size_t)y * a.w;
+        int res = -1;
+        if (x >= 2 && x <= a.w - 3 && y >= 2 && y <= a.h - 3) {
+            const uint4 r = __ldg(S.ref + row + x);
+            const int dp = a.full ? -1 : (int)__ldg(S.dplane + row + x);
+            if ((int)texture16(r) >= a.match_texture && (a.full || dp >= 0)) {
+                // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
+                // (the lower bound of the first condition is <= 0; the list's
+                // padding value 2047 exceeds every dmax)
+                const int dlim = min(a.dmax, S.dir < 0 ? x - 2 : a.w - 3 - x);
+                const uint4 *orow = S.oth + row + x;
+                int best = 0x7FFFFFFF;
+                if (a.full) {
+                    for (int d = a.dmin; d <= dlim; ++d) {  // no plane, so no prior term
+                        const int c = (int)sad16(r, __ldg(orow + S.dir * d));
+                        best = min(best, ((c + kKeyBias) << 11) | d);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < nlist4; ++k) {
+                        const int d = s_list[k];
+                        if (d <= dlim) {
+                            const int c = (int)sad16(r, __ldg(orow + S.dir * d));
+                            best = min(best, ((c + kKeyBias) << 11) | d);
+                        }
+                    }
+                    const int lo = max(a.dmin, dp - a.sradius), hi = min(dlim, dp + a.sradius);
+                    for (int d = lo; d <= hi; ++d) {
+                        int c = (int)sad16(r, __ldg(orow + S.dir * d));
+                        if (!a.prior_off) c += s_P[abs(d - dp)];
+                        best = min(best, ((c + kKeyBias) << 11) | d);
                     }
                 }
-                for (int d = max(lo, dp - a.sradius); d <= min(hi, dp + a.sradius); ++d) {
-                    if ((__ldg(cell + (d >> 5)) >> (d & 31)) & 1u) continue;  // already evaluated
-                    int c = (int)sad16(r, __ldg(orow + u + a.dir * d));
-                    if (!a.prior_off) c += a.P[abs(d - dp)];
-                    if (c < bc || (c == bc && d < bd)) { bc = c; bd = d; }
-                }
+                if (best != 0x7FFFFFFF) res = best & 2047;
             }
-            res = bd;
         }
+        S.out[row + x] = (int16_t)res;
     }
-    out[row + u] = (int16_t)res;
 }
 
-elas_status launch_plane_prior(const int16_t *list, const int32_t *tri, int ntri, int right, int w, int h,
-                               const elas_params *p, int16_t *dplane, cudaStream_t st) {
-    if (cudaMemsetAsync(dplane, 0xFF, (size_t)w * h * sizeof(int16_t), st) != cudaSuccess)
-        return launch_status("memset d_plane");
-    if (ntri <= 0) return ELAS_OK;
-    PriorArgs a{w, h, p->disp_min, p->disp_max, right};
-    const int wpb = 8;
-    int blocks = (ntri + wpb - 1) / wpb;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    plane_prior_kernel<<<blocks, 32 * wpb, 0, st>>>(list, tri, ntri, a, dplane);
-    return launch_status("plane_prior_kernel");
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+int max_triangles(int w, int h, const elas_params *p) {
+    return 2 * (w / p->candidate_stepsize) * (h / p->candidate_stepsize) + 8;
 }
 
-elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
-                         const int16_t *dplane, const uint32_t *grid, int right, int16_t *out, cudaStream_t st) {
-    DenseArgs a;
+static elas_status fill_prior_table(const elas_params *p, int *P) {
+    for (int k = 0; k <= kMaxSradius; ++k) P[k] = 0;
+    prior_table(p, P);
+    for (int k = 0; k <= p->sradius; ++k)
+        if (P[k] < -(kKeyBias - 1) || P[k] > kKeyBias - 1)
+            return fail(ELAS_ERR_INVALID_ARG, "prior P[%d] = %d outside +-65535 (beta too small)", k, P[k]);
+    return ELAS_OK;
+}
+
+// Scratch of the rasteriser: the big-triangle list and its counter.
+size_t raster_scratch_bytes(int ntri_total) {
+    return align_up(sizeof(int32_t) * 4, 256) + align_up(sizeof(int32_t) * (size_t)(ntri_total > 0 ? ntri_total : 1), 256);
+}
+
+// Prior maps of one or two meshes.  With two, the maps must be contiguous
+// (dplane1 == dplane0 + w*h) so that one memset clears both.
+static elas_status raster_meshes(const int16_t *list, const RasterSide *sides, int nsides, int w, int h,
+                                 const elas_params *p, void *scratch, cudaStream_t st) {
+    const size_t bytes = (size_t)w * h * sizeof(int16_t) * nsides;
+    if (cudaMemsetAsync(sides[0].dplane, 0xFF, bytes, st) != cudaSuccess) return launch_status("memset d_plane");
+    RasterArgs a{};
+    a.list = list;
+    a.nbig = reinterpret_cast<int32_t *>(scratch);
+    a.big = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scratch) + align_up(sizeof(int32_t) * 4, 256));
     a.w = w;
     a.h = h;
     a.dmin = p->disp_min;
     a.dmax = p->disp_max;
-    a.sradius = p->sradius;
-    a.match_texture = p->match_texture;
-    a.G = p->grid_size;
-    const GridGeom g = grid_geom(w, h, p);
-    a.gw = g.gw;
-    a.nw = g.nw;
-    a.dir = right ? +1 : -1;
-    a.full = (p->test_flags & ELAS_FLAG_FULL_RANGE) ? 1 : 0;
-    a.prior_off = (p->test_flags & ELAS_FLAG_PRIOR_OFF) ? 1 : 0;
-    for (int k = 0; k <= kMaxSradius; ++k) a.P[k] = 0;
-    prior_table(p, a.P);
-    const uint4 *ref = reinterpret_cast<const uint4 *>(right ? descR : descL);
-    const uint4 *oth = reinterpret_cast<const uint4 *>(right ? descL : descR);
-    dim3 block(32, 8);
-    dim3 gridd((w + 31) / 32, (h + 7) / 8);
-    dense_kernel<<<gridd, block, 0, st>>>(ref, oth, dplane, grid, a, out);
-    return launch_status("dense_kernel");
+    int maxt = 0;
+    for (int i = 0; i < nsides; ++i) {
+        a.s[i] = sides[i];
+        maxt = max(maxt, sides[i].ntri);
+    }
+    if (maxt == 0) return ELAS_OK;
+    if (cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) return launch_status("memset big count");
+    const int wpb = 8;
+    int blocks = (maxt + wpb - 1) / wpb;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    plane_raster_kernel<<<dim3(blocks, nsides), 32 * wpb, 0, st>>>(a);
+    elas_status s = launch_status("plane_raster_kernel");
+    if (s != ELAS_OK) return s;
+    plane_raster_big_kernel<<<2 * 152, 256, 0, st>>>(a);
+    return launch_status("plane_raster_big_kernel");
 }
 
-size_t dense_workspace(int w, int h) { return 2 * align_up((size_t)w * h * sizeof(int16_t), 256); }
+static CellArgs cell_args(int w, int h, const elas_params *p, const int *P) {
+    CellArgs a{};
+    const GridGeom g = grid_geom(w, h, p);
+    a.w = w;
+    a.h = h;
+    a.G = p->grid_size;
+    a.gw = g.gw;
+    a.nw = g.nw;
+    a.dmin = p->disp_min;
+    a.dmax = p->disp_max;
+    a.sradius = p->sradius;
+    a.match_texture = p->match_texture;
+    a.full = (p->test_flags & ELAS_FLAG_FULL_RANGE) ? 1 : 0;
+    a.prior_off = (p->test_flags & ELAS_FLAG_PRIOR_OFF) ? 1 : 0;
+    for (int k = 0; k <= kMaxSradius; ++k) a.P[k] = P[k];
+    return a;
+}
+
+static elas_status launch_cells(const CellArgs &a, int nsides, int w, int h, const elas_params *p, cudaStream_t st) {
+    const GridGeom g = grid_geom(w, h, p);
+    // one warp per 32 pixels of the cell, at most 16 warps
+    const int warps = min(16, max(1, (p->grid_size * p->grid_size + 31) / 32));
+    cell_kernel<<<dim3(g.gw, g.gh, nsides), 32 * warps, 0, st>>>(a);
+    return launch_status("cell_kernel");
+}
+
+elas_status launch_plane_prior(const int16_t *list, const int32_t *tri, int ntri, int right, int w, int h,
+                               const elas_params *p, int16_t *dplane, void *scratch, cudaStream_t st) {
+    RasterSide side{tri, ntri, right ? 1 : 0, dplane, nullptr};
+    return raster_meshes(list, &side, 1, w, h, p, scratch, st);
+}
+
+elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                         const int16_t *dplane, const uint32_t *grid, int right, int16_t *out, cudaStream_t st) {
+    int P[kMaxSradius + 1];
+    elas_status s = fill_prior_table(p, P);
+    if (s != ELAS_OK) return s;
+    CellArgs a = cell_args(w, h, p, P);
+    CellSide &cs = a.s[0];
+    cs.ref = reinterpret_cast<const uint4 *>(right ? descR : descL);
+    cs.oth = reinterpret_cast<const uint4 *>(right ? descL : descR);
+    cs.grid = grid;
+    cs.dplane = dplane;
+    cs.out = out;
+    cs.dir = right ? +1 : -1;
+    return launch_cells(a, 1, w, h, p, st);
+}
+
+size_t dense_workspace(int w, int h, const elas_params *p) {
+    return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(2 * max_triangles(w, h, p));
+}
+
+elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                              const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
+                              const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
+                              cudaStream_t st, const int32_t *ntri_dev) {
+    int16_t *dpL = reinterpret_cast<int16_t *>(ws);
+    int16_t *dpR = dpL + (size_t)w * h;
+    const RasterSide sides[2] = {{triL, ntriL, 0, dpL, ntri_dev ? ntri_dev : nullptr},
+                                 {triR, ntriR, 1, dpR, ntri_dev ? ntri_dev + 1 : nullptr}};
+    void *scratch = reinterpret_cast<char *>(ws) + align_up(2 * (size_t)w * h * sizeof(int16_t), 256);
+    elas_status s = raster_meshes(list, sides, 2, w, h, p, scratch, st);
+    if (s != ELAS_OK) return s;
+    int P[kMaxSradius + 1];
+    if ((s = fill_prior_table(p, P)) != ELAS_OK) return s;
+    CellArgs a = cell_args(w, h, p, P);
+    for (int i = 0; i < 2; ++i) {
+        CellSide &cs = a.s[i];
+        cs.ref = reinterpret_cast<const uint4 *>(i ? descR : descL);
+        cs.oth = reinterpret_cast<const uint4 *>(i ? descL : descR);
+        cs.grid = i ? gridR : gridL;
+        cs.dplane = i ? dpR : dpL;
+        cs.out = i ? dR : dL;
+        cs.dir = i ? +1 : -1;
+    }
+    return launch_cells(a, 2, w, h, p, st);
+}
 
 }  // namespace elas
 
+extern "C" size_t elas_plane_prior_workspace_bytes(int32_t ntri) {
+    return ntri < 0 ? 0 : elas::raster_scratch_bytes(ntri);
+}
+
 extern "C" elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,
                                         int32_t right, int32_t w, int32_t h, const elas_params *p,
-                                        int16_t *d_plane, elas_stream stream) {
+                                        int16_t *d_plane, void *workspace, size_t workspace_bytes,
+                                        elas_stream stream) {
     using namespace elas;
     elas_status s = check_params(p, w, h);
     if (s != ELAS_OK) return s;
-    if (!d_plane || (ntri > 0 && (!list || !tri))) return fail(ELAS_ERR_INVALID_ARG, "NULL buffer");
+    if (!d_plane || !workspace || (ntri > 0 && (!list || !tri))) return fail(ELAS_ERR_INVALID_ARG, "NULL buffer");
     if (n < 0 || ntri < 0) return fail(ELAS_ERR_INVALID_ARG, "negative count");
-    return launch_plane_prior(list, tri, ntri, right, w, h, p, d_plane, to_stream(stream));
+    if (ntri >= (1 << 30)) return fail(ELAS_ERR_INVALID_ARG, "too many triangles");
+    if (!aligned(workspace, 256)) return fail(ELAS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (workspace_bytes < raster_scratch_bytes(ntri))
+        return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, raster_scratch_bytes(ntri));
+    return launch_plane_prior(list, tri, ntri, right, w, h, p, d_plane, workspace, to_stream(stream));
 }
 
 extern "C" elas_status elas_dense_argmin(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
@@ -216,7 +458,7 @@ extern "C" elas_status elas_dense_argmin(const uint8_t *descL, const uint8_t *de
 
 extern "C" size_t elas_dense_workspace_bytes(int32_t w, int32_t h, const elas_params *p) {
     if (elas::check_params(p, w, h) != ELAS_OK) return 0;
-    return elas::dense_workspace(w, h);
+    return elas::dense_workspace(w, h, p);
 }
 
 extern "C" elas_status elas_dense_match(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
@@ -232,16 +474,12 @@ extern "C" elas_status elas_dense_match(const uint8_t *descL, const uint8_t *des
     if ((ntriL > 0 || ntriR > 0) && !list) return fail(ELAS_ERR_INVALID_ARG, "NULL support list");
     if ((ntriL > 0 && !triL) || (ntriR > 0 && !triR)) return fail(ELAS_ERR_INVALID_ARG, "NULL triangles");
     if (n < 0 || ntriL < 0 || ntriR < 0) return fail(ELAS_ERR_INVALID_ARG, "negative count");
+    if (ntriL > max_triangles(w, h, p) || ntriR > max_triangles(w, h, p))
+        return fail(ELAS_ERR_CAPACITY, "triangle counts %d/%d above %d", ntriL, ntriR, max_triangles(w, h, p));
     if (!aligned(descL, 16) || !aligned(descR, 16)) return fail(ELAS_ERR_INVALID_ARG, "descriptors not 16-byte aligned");
     if (!aligned(workspace, 256)) return fail(ELAS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
-    if (workspace_bytes < dense_workspace(w, h))
-        return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, dense_workspace(w, h));
-    cudaStream_t st = to_stream(stream);
-    int16_t *dpL = reinterpret_cast<int16_t *>(workspace);
-    int16_t *dpR = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(workspace) +
-                                               align_up((size_t)w * h * sizeof(int16_t), 256));
-    if ((s = launch_plane_prior(list, triL, ntriL, 0, w, h, p, dpL, st)) != ELAS_OK) return s;
-    if ((s = launch_plane_prior(list, triR, ntriR, 1, w, h, p, dpR, st)) != ELAS_OK) return s;
-    if ((s = launch_dense(descL, descR, w, h, p, dpL, grid_L, 0, dL, st)) != ELAS_OK) return s;
-    return launch_dense(descL, descR, w, h, p, dpR, grid_R, 1, dR, st);
+    if (workspace_bytes < dense_workspace(w, h, p))
+        return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, dense_workspace(w, h, p));
+    return launch_dense_both(descL, descR, w, h, p, list, triL, ntriL, triR, ntriR, grid_L, grid_R, dL, dR,
+                             workspace, to_stream(stream), nullptr);
 }

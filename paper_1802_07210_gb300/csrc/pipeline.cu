@@ -93,6 +93,11 @@ struct elas_pipeline {
     int32_t *h_tri = nullptr;
     size_t countlist_bytes = 0;
     int tri_cap = 0;  // per side
+    // triangulation on the GPU (default) or on the host
+    int gpu_tri = 1;
+    void *ws_dt = nullptr;
+    size_t ws_dt_bytes = 0;
+    cudaStream_t last_stream = nullptr;
     // last run
     elas_pipeline_stats stats{};
     std::vector<int32_t> triL_v, triR_v;
@@ -109,7 +114,7 @@ void release(elas_pipeline *pl) {
     if (!pl) return;
     delete pl->helper;
     void *dev[] = {pl->img, pl->descL, pl->descR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
-                   pl->ws_support, pl->ws_dense, pl->ws_post, pl->dL, pl->dR, pl->post};
+                   pl->ws_support, pl->ws_dense, pl->ws_post, pl->dL, pl->dR, pl->post, pl->ws_dt};
     for (void *d : dev)
         if (d) cudaFree(d);
     if (pl->h_countlist) cudaFreeHost(pl->h_countlist);
@@ -158,8 +163,9 @@ extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_par
     pl->tri_cap = 2 * pl->nc + 8;
     pl->countlist_bytes = 16 + align_up((size_t)pl->nc * 3 * sizeof(int16_t) + 16, 16);
     pl->ws_support_bytes = support_workspace(w, h, p);
-    pl->ws_dense_bytes = dense_workspace(w, h);
+    pl->ws_dense_bytes = dense_workspace(w, h, p);
     pl->ws_post_bytes = post_workspace(w, h);
+    pl->ws_dt_bytes = triangulate_device_workspace(pl->nc, w, h, 2);
     bool ok = dalloc(&pl->img, 2 * align_up(npx, 256)) == cudaSuccess &&
               dalloc(&pl->descL, npx * 16) == cudaSuccess && dalloc(&pl->descR, npx * 16) == cudaSuccess &&
               dalloc(&pl->dcan, (size_t)pl->nc * 2 + 16) == cudaSuccess &&
@@ -170,7 +176,7 @@ extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_par
               dalloc(&pl->ws_dense, pl->ws_dense_bytes) == cudaSuccess &&
               dalloc(&pl->ws_post, pl->ws_post_bytes) == cudaSuccess &&
               dalloc(&pl->dL, npx * 2) == cudaSuccess && dalloc(&pl->dR, npx * 2) == cudaSuccess &&
-              dalloc(&pl->post, npx * 4) == cudaSuccess &&
+              dalloc(&pl->post, npx * 4) == cudaSuccess && dalloc(&pl->ws_dt, pl->ws_dt_bytes) == cudaSuccess &&
               cudaMallocHost(reinterpret_cast<void **>(&pl->h_countlist), pl->countlist_bytes) == cudaSuccess &&
               cudaMallocHost(reinterpret_cast<void **>(&pl->h_tri), sizeof(int32_t) * 3 * 2 * (size_t)pl->tri_cap) ==
                   cudaSuccess;
@@ -199,38 +205,51 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
     int16_t *list = reinterpret_cast<int16_t *>(pl->countlist + 16);
     int32_t *count = reinterpret_cast<int32_t *>(pl->countlist);
     elas_status s;
+    pl->last_stream = st;
     if ((s = launch_descriptors(imgL, imgR, w, h, pitch, pl->descL, pl->descR, st)) != ELAS_OK) return s;
     if ((s = launch_support(pl->descL, pl->descR, w, h, p, pl->dcan, list, count, pl->gridL, pl->gridR,
                             pl->ws_support, st)) != ELAS_OK)
         return s;
-    if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, pl->countlist_bytes, cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return launch_status("support list to host");
-    const int n = *reinterpret_cast<const int32_t *>(pl->h_countlist);
-    if (n < 0 || n > pl->nc) return fail(ELAS_ERR_INTERNAL, "support count %d out of range", n);
-    const auto t0 = std::chrono::steady_clock::now();
-    int ntL = 0, ntR = 0;
-    if ((s = triangulate_both(pl, n, reinterpret_cast<const int16_t *>(pl->h_countlist + 16), &ntL, &ntR)) !=
-        ELAS_OK)
-        return s;
-    const auto t1 = std::chrono::steady_clock::now();
-    pl->stats.n_support = n;
-    pl->stats.n_tri_left = ntL;
-    pl->stats.n_tri_right = ntR;
-    pl->stats.triangulate_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    if (ntL + ntR > 0 &&
-        cudaMemcpyAsync(pl->tri, pl->h_tri, sizeof(int32_t) * 3 * (size_t)(ntL + ntR), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess)
-        return launch_status("triangles to device");
-    int16_t *dpL = reinterpret_cast<int16_t *>(pl->ws_dense);
-    int16_t *dpR = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(pl->ws_dense) +
-                                               align_up((size_t)w * h * sizeof(int16_t), 256));
     int16_t *outR = dR ? dR : pl->dR;
-    if ((s = launch_plane_prior(list, pl->tri, ntL, 0, w, h, p, dpL, st)) != ELAS_OK) return s;
-    if ((s = launch_plane_prior(list, pl->tri + 3 * (size_t)ntL, ntR, 1, w, h, p, dpR, st)) != ELAS_OK) return s;
-    if ((s = launch_dense(pl->descL, pl->descR, w, h, p, dpL, pl->gridL, 0, dL, st)) != ELAS_OK) return s;
-    if ((s = launch_dense(pl->descL, pl->descR, w, h, p, dpR, pl->gridR, 1, outR, st)) != ELAS_OK) return s;
+    if (pl->gpu_tri) {
+        // everything stays on the device: no synchronisation in the step
+        int32_t *ntri_dev = count + 1;  // [count, ntri left, ntri right, -] then the list
+        const int rights[2] = {0, 1};
+        int32_t *tris[2] = {pl->tri, pl->tri + 3 * (size_t)pl->tri_cap};
+        int32_t *nts[2] = {ntri_dev, ntri_dev + 1};
+        if ((s = launch_triangulate_device(list, count, pl->nc, w, h, 2, rights, tris, nts, pl->tri_cap, pl->ws_dt,
+                                           st)) != ELAS_OK)
+            return s;
+        if ((s = launch_dense_both(pl->descL, pl->descR, w, h, p, list, tris[0], pl->tri_cap, tris[1], pl->tri_cap,
+                                   pl->gridL, pl->gridR, dL, outR, pl->ws_dense, st, ntri_dev)) != ELAS_OK)
+            return s;
+        if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return launch_status("stats to host");
+        pl->stats.triangulate_ms = 0.0;
+    } else {
+        if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, pl->countlist_bytes, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return launch_status("support list to host");
+        const int n = *reinterpret_cast<const int32_t *>(pl->h_countlist);
+        if (n < 0 || n > pl->nc) return fail(ELAS_ERR_INTERNAL, "support count %d out of range", n);
+        const auto t0 = std::chrono::steady_clock::now();
+        int ntL = 0, ntR = 0;
+        if ((s = triangulate_both(pl, n, reinterpret_cast<const int16_t *>(pl->h_countlist + 16), &ntL, &ntR)) !=
+            ELAS_OK)
+            return s;
+        const auto t1 = std::chrono::steady_clock::now();
+        pl->stats.n_support = n;
+        pl->stats.n_tri_left = ntL;
+        pl->stats.n_tri_right = ntR;
+        pl->stats.triangulate_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        if (ntL + ntR > 0 && cudaMemcpyAsync(pl->tri, pl->h_tri, sizeof(int32_t) * 3 * (size_t)(ntL + ntR),
+                                             cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return launch_status("triangles to device");
+        if ((s = launch_dense_both(pl->descL, pl->descR, w, h, p, list, pl->tri, ntL, pl->tri + 3 * (size_t)ntL,
+                                   ntR, pl->gridL, pl->gridR, dL, outR, pl->ws_dense, st, nullptr)) != ELAS_OK)
+            return s;
+    }
     if ((s = launch_lr_check(dL, outR, w, h, p->lr_threshold, nullptr, nullptr, st)) != ELAS_OK) return s;
     if (post) return launch_post(dL, w, h, p, post, pl->ws_post, st);
     return ELAS_OK;
@@ -258,9 +277,23 @@ extern "C" elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *
     return ELAS_OK;
 }
 
+extern "C" elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu) {
+    if (!pl) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL pipeline");
+    pl->gpu_tri = on_gpu ? 1 : 0;
+    return ELAS_OK;
+}
+
 extern "C" elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st) {
     if (!pl || !st) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL argument");
     *st = pl->stats;
+    if (pl->gpu_tri) {
+        if (cudaStreamSynchronize(pl->last_stream) != cudaSuccess) return elas::launch_status("stats sync");
+        const int32_t *c = reinterpret_cast<const int32_t *>(pl->h_countlist);
+        st->n_support = c[0];
+        st->n_tri_left = c[1];
+        st->n_tri_right = c[2];
+        if (c[1] < 0 || c[2] < 0) return elas::fail(ELAS_ERR_INTERNAL, "device triangulation failed");
+    }
     return ELAS_OK;
 }
 

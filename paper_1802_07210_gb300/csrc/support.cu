@@ -3,16 +3,20 @@
 // one-hot masks, Sec. VI.D) and raster-order compaction.
 //
 // Kernels, in launch order:
-//   support_match_kernel   one warp per lattice candidate; lanes stride the
-//                          disparity range, each lane keeps (best, second)
-//                          and the warp merges them with two min-reductions;
-//                          the right-to-left re-match runs in the same warp.
-//   consistency_kernel     one thread per candidate, window count.
-//   redundancy_kernel      one thread per candidate, four directional scans.
-//   grid_vector_kernel     one thread per surviving point, atomicOr of the
-//                          {d-1,d,d+1} bits into the 3x3 cells (OR is order
-//                          free, so the masks are deterministic).
-//   compact_kernel         one CTA, block-wide exclusive scan, raster order.
+//   support_match_kernel    one warp per lattice candidate; lanes stride the
+//                           disparity range, each lane keeps (best, second)
+//                           and the warp merges them with two min-reductions;
+//                           the right-to-left re-match runs in the same warp.
+//   consistency_kernel      32x8 candidate tile with its halo in shared
+//                           memory, window count per candidate; also clears
+//                           the grid-vector masks.
+//   redundancy_grid_kernel  one lattice row per CTA: four directional scans,
+//                           atomicOr of the {d-1,d,d+1} bits of every
+//                           surviving point into the 3x3 cells around it (OR
+//                           is order free, so the masks are deterministic),
+//                           and the row's point count.
+//   compact_rows_kernel     one lattice row per CTA: offset = points in the
+//                           rows above, ballot-based placement; raster order.
 #include "launch.cuh"
 
 namespace elas {
@@ -102,52 +106,47 @@ support_match_kernel(const uint4 *__restrict__ dL, const uint4 *__restrict__ dR,
     if (lane == 0) raw[warp] = (int16_t)out;
 }
 
-__global__ void consistency_kernel(const int16_t *__restrict__ in, int wc, int hc, int r, int thr, int min_support,
-                                   int16_t *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= wc * hc) return;
-    const int ic = i / wc, jc = i - ic * wc;
-    const int d = in[i];
+// Consistency filter on a 32x8 tile of candidates staged with its halo in
+// shared memory; also zeroes the grid-vector masks (grid-stride) so that the
+// next kernel can OR into them.
+constexpr int kConsTX = 32, kConsTY = 8;
+
+__global__ void __launch_bounds__(kConsTX *kConsTY)
+consistency_kernel(const int16_t *__restrict__ in, int wc, int hc, int r, int thr, int min_support,
+                   int16_t *__restrict__ out, uint32_t *__restrict__ gL, uint32_t *__restrict__ gR, int gwords) {
+    extern __shared__ int16_t s_g[];
+    const int SW = kConsTX + 2 * r, SH = kConsTY + 2 * r;
+    const int j0 = blockIdx.x * kConsTX - r, i0 = blockIdx.y * kConsTY - r;
+    const int tid = threadIdx.y * kConsTX + threadIdx.x;
+    constexpr int NT = kConsTX * kConsTY;
+    for (int k = tid; k < SW * SH; k += NT) {
+        const int gi = i0 + k / SW, gj = j0 + k % SW;
+        s_g[k] = (gi >= 0 && gi < hc && gj >= 0 && gj < wc) ? in[gi * wc + gj] : (int16_t)-1;
+    }
+    const int nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    for (int k = bid * NT + tid; k < gwords; k += nblk * NT) {
+        if (gL) gL[k] = 0u;
+        if (gR) gR[k] = 0u;
+    }
+    __syncthreads();
+    const int jc = blockIdx.x * kConsTX + threadIdx.x, ic = blockIdx.y * kConsTY + threadIdx.y;
+    if (jc >= wc || ic >= hc) return;
+    const int16_t *c = s_g + (threadIdx.y + r) * SW + threadIdx.x + r;
+    const int d = c[0];
     int res = -1;
     if (d >= 0) {
         int cnt = 0;
-        const int i0 = max(0, ic - r), i1 = min(hc - 1, ic + r);
-        const int j0 = max(0, jc - r), j1 = min(wc - 1, jc + r);
-        for (int i2 = i0; i2 <= i1; ++i2)
-            for (int j2 = j0; j2 <= j1; ++j2) {
-                const int d2 = in[i2 * wc + j2];
-                cnt += (d2 >= 0) & (abs(d2 - d) <= thr) & !(i2 == ic && j2 == jc);
+        for (int di = -r; di <= r; ++di) {
+            const int16_t *rowp = c + di * SW;
+            for (int dj = -r; dj <= r; ++dj) {
+                const int v = rowp[dj];
+                cnt += (v >= 0) & (abs(v - d) <= thr);
             }
+        }
+        cnt -= (thr >= 0);  // the point itself
         if (cnt >= min_support) res = d;
     }
-    out[i] = (int16_t)res;
-}
-
-__global__ void redundancy_kernel(const int16_t *__restrict__ in, int wc, int hc, int maxd, int enabled,
-                                  int16_t *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= wc * hc) return;
-    const int ic = i / wc, jc = i - ic * wc;
-    const int d = in[i];
-    int res = d;
-    if (d >= 0 && enabled) {
-        const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
-        bool redundant = true;
-        for (int k = 0; k < 4 && redundant; ++k) {
-            bool found = false;
-            for (int s = 1; s <= maxd; ++s) {
-                const int i2 = ic + s * di[k], j2 = jc + s * dj[k];
-                if (i2 < 0 || i2 >= hc || j2 < 0 || j2 >= wc) break;
-                if (in[i2 * wc + j2] == d) {
-                    found = true;
-                    break;
-                }
-            }
-            redundant = found;
-        }
-        if (redundant) res = -1;
-    }
-    out[i] = (int16_t)(d >= 0 ? res : -1);
+    out[ic * wc + jc] = (int16_t)res;
 }
 
 __device__ __forceinline__ void or_bits(uint32_t *cell, int d, int dmin, int dmax) {
@@ -155,77 +154,100 @@ __device__ __forceinline__ void or_bits(uint32_t *cell, int d, int dmin, int dma
         if (dd >= dmin && dd <= dmax) atomicOr(cell + (dd >> 5), 1u << (dd & 31));
 }
 
-__global__ void grid_vector_kernel(const int16_t *__restrict__ dcan, int wc, int hc, int step, int G, int gw,
-                                   int gh, int nw, int dmin, int dmax, uint32_t *__restrict__ gridL,
-                                   uint32_t *__restrict__ gridR) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= wc * hc) return;
-    const int d = dcan[i];
-    if (d < 0) return;
-    const int ic = i / wc, jc = i - ic * wc;
-    const int u = jc * step, v = ic * step;
-    const int cy = v / G;
-    for (int side = 0; side < 2; ++side) {
-        uint32_t *grid = side ? gridR : gridL;
-        if (!grid) continue;
-        const int cx = (side ? u - d : u) / G;
-        for (int y = cy - 1; y <= cy + 1; ++y) {
-            if (y < 0 || y >= gh) continue;
-            for (int x = cx - 1; x <= cx + 1; ++x) {
-                if (x < 0 || x >= gw) continue;
-                or_bits(grid + ((size_t)y * gw + x) * nw, d, dmin, dmax);
+struct GridArgs {
+    int step, G, gw, gh, nw, dmin, dmax;
+};
+
+// Redundancy filter for one lattice row per CTA, the grid-vector bits of the
+// surviving points (atomicOr: order free) and the row's point count.
+__global__ void __launch_bounds__(128)
+redundancy_grid_kernel(const int16_t *__restrict__ con, int wc, int hc, int maxd, int enabled, GridArgs g,
+                       int16_t *__restrict__ dcan, uint32_t *__restrict__ gridL, uint32_t *__restrict__ gridR,
+                       int32_t *__restrict__ rowcount) {
+    __shared__ int s_cnt[4];
+    const int ic = blockIdx.x;
+    int mine = 0;
+    for (int jc = threadIdx.x; jc < wc; jc += blockDim.x) {
+        const int d = con[ic * wc + jc];
+        int res = d;
+        if (d >= 0 && enabled) {
+            const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
+            bool redundant = true;
+            for (int k = 0; k < 4 && redundant; ++k) {
+                bool found = false;
+                for (int s = 1; s <= maxd; ++s) {
+                    const int i2 = ic + s * di[k], j2 = jc + s * dj[k];
+                    if (i2 < 0 || i2 >= hc || j2 < 0 || j2 >= wc) break;
+                    if (con[i2 * wc + j2] == d) {
+                        found = true;
+                        break;
+                    }
+                }
+                redundant = found;
+            }
+            if (redundant) res = -1;
+        }
+        dcan[ic * wc + jc] = (int16_t)res;
+        if (res >= 0) {
+            ++mine;
+            const int u = jc * g.step, v = ic * g.step;
+            const int cy = v / g.G;
+            for (int side = 0; side < 2; ++side) {
+                uint32_t *grid = side ? gridR : gridL;
+                if (!grid) continue;
+                const int cx = (side ? u - res : u) / g.G;
+                for (int y = max(0, cy - 1); y <= min(g.gh - 1, cy + 1); ++y)
+                    for (int x = max(0, cx - 1); x <= min(g.gw - 1, cx + 1); ++x)
+                        or_bits(grid + ((size_t)y * g.gw + x) * g.nw, res, g.dmin, g.dmax);
             }
         }
     }
+    mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) rowcount[ic] = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
 }
 
-constexpr int kCompactThreads = 1024;
-
-__global__ void __launch_bounds__(kCompactThreads)
-compact_kernel(const int16_t *__restrict__ dcan, int wc, int hc, int step, int16_t *__restrict__ list,
-               int32_t *__restrict__ count) {
-    __shared__ int s_warp[kCompactThreads / 32];
-    const int nc = wc * hc;
-    const int t = threadIdx.x;
-    const int chunk = (nc + kCompactThreads - 1) / kCompactThreads;
-    const int b0 = min(nc, t * chunk), b1 = min(nc, b0 + chunk);
-    int mine = 0;
-    for (int i = b0; i < b1; ++i) mine += dcan[i] >= 0;
-    // block-wide exclusive scan of `mine`
-    const int lane = t & 31, wid = t >> 5;
-    int incl = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[wid] = incl;
+// Raster-order compaction, one lattice row per CTA: the row's offset is the
+// sum of the counts of the rows above; entries are placed with warp ballots.
+__global__ void __launch_bounds__(128)
+compact_rows_kernel(const int16_t *__restrict__ dcan, int wc, int hc, int step, const int32_t *__restrict__ rowcount,
+                    int16_t *__restrict__ list, int32_t *__restrict__ count) {
+    __shared__ int s_w[4];
+    const int ic = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int part = 0;
+    for (int k = tid; k < ic; k += 128) part += rowcount[k];
+    part = __reduce_add_sync(0xFFFFFFFFu, part);
+    if (lane == 0) s_w[warp] = part;
     __syncthreads();
-    if (wid == 0) {
-        int x = s_warp[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
+    int base = s_w[0] + s_w[1] + s_w[2] + s_w[3];
+    __syncthreads();
+    for (int j0 = 0; j0 < wc; j0 += 128) {
+        const int jc = j0 + tid;
+        const int d = jc < wc ? dcan[ic * wc + jc] : -1;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, d >= 0);
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        int off = base + __popc(bal & ((1u << lane) - 1u));
+        for (int k = 0; k < warp; ++k) off += s_w[k];
+        if (d >= 0) {
+            list[3 * off + 0] = (int16_t)(jc * step);
+            list[3 * off + 1] = (int16_t)(ic * step);
+            list[3 * off + 2] = (int16_t)d;
         }
-        s_warp[lane] = x;  // inclusive totals per warp
+        base += s_w[0] + s_w[1] + s_w[2] + s_w[3];
+        __syncthreads();
     }
-    __syncthreads();
-    int pos = incl - mine + (wid ? s_warp[wid - 1] : 0);
-    for (int i = b0; i < b1; ++i) {
-        const int d = dcan[i];
-        if (d < 0) continue;
-        const int ic = i / wc, jc = i - ic * wc;
-        list[3 * pos + 0] = (int16_t)(jc * step);
-        list[3 * pos + 1] = (int16_t)(ic * step);
-        list[3 * pos + 2] = (int16_t)d;
-        ++pos;
-    }
-    if (t == kCompactThreads - 1) *count = pos;
+    if (ic == hc - 1 && tid == 0) *count = base;
 }
 
 size_t support_workspace(int w, int h, const elas_params *p) {
-    const size_t nc = (size_t)(w / p->candidate_stepsize) * (h / p->candidate_stepsize);
-    return 2 * align_up(nc * sizeof(int16_t) + 16, 256);
+    const size_t hc = (size_t)(h / p->candidate_stepsize);
+    const size_t nc = (size_t)(w / p->candidate_stepsize) * hc;
+    return 2 * align_up(nc * sizeof(int16_t) + 16, 256) + align_up(hc * sizeof(int32_t) + 16, 256);
 }
+
+constexpr int kMaxConsistencyWindow = 64;
 
 elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                            int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
@@ -243,34 +265,41 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     a.lr_threshold = p->lr_threshold;
     const int nc = a.wc * a.hc;
     const GridGeom g = grid_geom(w, h, p);
-    const size_t gbytes = (size_t)g.gw * g.gh * g.nw * sizeof(uint32_t);
-    if (grid_L && cudaMemsetAsync(grid_L, 0, gbytes, st) != cudaSuccess) return launch_status("memset grid_L");
-    if (grid_R && cudaMemsetAsync(grid_R, 0, gbytes, st) != cudaSuccess) return launch_status("memset grid_R");
+    const int gwords = g.gw * g.gh * g.nw;
+    if (p->incon_window_size > kMaxConsistencyWindow)
+        return fail(ELAS_ERR_INVALID_ARG, "incon_window_size %d above %d", p->incon_window_size, kMaxConsistencyWindow);
     if (nc == 0) {
-        if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return launch_status("memset count");
+        if ((grid_L && cudaMemsetAsync(grid_L, 0, (size_t)gwords * 4, st) != cudaSuccess) ||
+            (grid_R && cudaMemsetAsync(grid_R, 0, (size_t)gwords * 4, st) != cudaSuccess) ||
+            cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess)
+            return launch_status("memset empty support");
         return ELAS_OK;
     }
     int16_t *raw = reinterpret_cast<int16_t *>(ws);
     int16_t *con = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(ws) + align_up(nc * sizeof(int16_t) + 16, 256));
+    int32_t *rowcount =
+        reinterpret_cast<int32_t *>(reinterpret_cast<char *>(ws) + 2 * align_up(nc * sizeof(int16_t) + 16, 256));
     const int warps_per_block = 8;
     support_match_kernel<<<(nc + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
         reinterpret_cast<const uint4 *>(descL), reinterpret_cast<const uint4 *>(descR), a, raw);
     elas_status s = launch_status("support_match_kernel");
     if (s != ELAS_OK) return s;
-    const int tb = 256, nb = (nc + tb - 1) / tb;
-    consistency_kernel<<<nb, tb, 0, st>>>(raw, a.wc, a.hc, p->incon_window_size, p->incon_threshold,
-                                          p->incon_min_support, con);
+    const int r = p->incon_window_size;
+    const size_t smem = (size_t)(kConsTX + 2 * r) * (kConsTY + 2 * r) * sizeof(int16_t);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(consistency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return launch_status("consistency_kernel shared memory attribute");
+    consistency_kernel<<<dim3((a.wc + kConsTX - 1) / kConsTX, (a.hc + kConsTY - 1) / kConsTY), dim3(kConsTX, kConsTY),
+                         smem, st>>>(raw, a.wc, a.hc, r, p->incon_threshold, p->incon_min_support, con, grid_L,
+                                     grid_R, gwords);
     if ((s = launch_status("consistency_kernel")) != ELAS_OK) return s;
-    redundancy_kernel<<<nb, tb, 0, st>>>(con, a.wc, a.hc, p->redun_max_dist,
-                                         (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1, d_can);
-    if ((s = launch_status("redundancy_kernel")) != ELAS_OK) return s;
-    if (grid_L || grid_R) {
-        grid_vector_kernel<<<nb, tb, 0, st>>>(d_can, a.wc, a.hc, a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin,
-                                              a.dmax, grid_L, grid_R);
-        if ((s = launch_status("grid_vector_kernel")) != ELAS_OK) return s;
-    }
-    compact_kernel<<<1, kCompactThreads, 0, st>>>(d_can, a.wc, a.hc, a.step, list, count);
-    return launch_status("compact_kernel");
+    GridArgs ga{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax};
+    redundancy_grid_kernel<<<a.hc, 128, 0, st>>>(con, a.wc, a.hc, p->redun_max_dist,
+                                                 (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1, ga, d_can,
+                                                 grid_L, grid_R, rowcount);
+    if ((s = launch_status("redundancy_grid_kernel")) != ELAS_OK) return s;
+    compact_rows_kernel<<<a.hc, 128, 0, st>>>(d_can, a.wc, a.hc, a.step, rowcount, list, count);
+    return launch_status("compact_rows_kernel");
 }
 
 }  // namespace elas
