@@ -200,8 +200,9 @@ elas_status elas_triangulate(const int16_t *list, int32_t n, int32_t right, int3
  * indices, coincident right-image points keep the lowest index).  Each point
  * builds its own star by exact gift-wrapping among its neighbours, certified
  * by the circumdisc test; uncertified stars are redone with a larger radius.
- * list: device int16 [cap][3]; count: device int32, number of points (<= cap);
- * right: 0 = (u, v), 1 = (u - d, v).  Outputs on the device: tri int32
+ * list: device int16 [cap][3] with 0 <= v < h (u - d may be negative);
+ * count: device int32, number of points (<= cap); right: 0 = (u, v),
+ * 1 = (u - d, v).  Outputs on the device: tri int32
  * [cap_tri][3] (counter-clockwise, each triangle once, deterministic order),
  * *ntri = triangle count, or -1 if the triangulation failed.  cap_tri must be
  * >= 2*cap + 8.  workspace: device, 256-byte aligned,

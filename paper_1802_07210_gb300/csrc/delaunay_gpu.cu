@@ -14,14 +14,18 @@
 //      the symbolic tie-break: a strict total order, so a warp min-reduction
 //      finds it); continue with (p, b) until the star closes at a0 or no
 //      point is left of the edge (p on the hull), then wrap clockwise from a0.
-// Pass 1 (one warp per point) caches the points within 32 pixels of p, taken
-// from a 16-pixel grid, in shared memory and wraps among them; the star is
-// accepted when it closes and every triangle's circumdisc lies inside that
-// disc (4 r^2 <= 32^2 in exact arithmetic), so no farther point can matter.
-// Stars that stay open (hull points), or leave the disc, are redone in pass
-// 2 by one CTA per point with every point as a candidate.  Each triangle is
-// emitted once, by its lowest-index vertex, at an offset from an exclusive
-// scan of the per-point counts, so the output order is deterministic.
+// Pass 1 (a group of 8 lanes per point) lists the points within 32 pixels
+// of p from a 16-pixel grid and wraps the star among them with the pencil
+// key; it is accepted when every triangle's circumdisc lies inside that disc
+// (4 r^2 <= 32^2 in exact arithmetic, so no farther point can matter) and,
+// where the star stays open (p on the hull), nothing lies beyond either open
+// edge (checked against the extreme points of every image row).  The other
+// stars are rebuilt by one CTA per point: each step takes the best of the
+// points within 192 pixels when its circle fits that radius (pass 2, 256
+// threads); stars with a step whose circle does not fit are rebuilt by 1024
+// threads that scan every point for such steps (pass 3), which is exact.  Each triangle is emitted
+// once, by its lowest-index vertex, at an offset from an exclusive scan of
+// the per-point counts, so the output order is deterministic.
 #include "launch.cuh"
 
 namespace elas {
@@ -37,12 +41,15 @@ struct DtSide {
     int32_t *cell_cnt;     // [ncell + 1]
     int32_t *cell_start;   // [ncell + 1]
     int32_t *cell_fill;    // [ncell + 1]
-    int32_t *status;       // [cap] 0 pending, 1/2 certified in pass 1/2, -1 duplicate
+    int32_t *status;       // [cap] 0 pending, k: star done in pass k, -1 duplicate
     int32_t *owned;        // [cap] triangles owned (lowest-index vertex)
     int32_t *offset;       // [cap] exclusive scan of owned
     int32_t *slots;        // [cap][kDtSlots][2] owned triangles (the other two vertices)
     int32_t *pending;      // [cap] points queued for pass 2
     int32_t *npending;     // queue length
+    int32_t *pending2;     // [cap] points queued for pass 3
+    int32_t *npending2;
+    int32_t *rowmin, *rowmax;  // [h] extreme x of the points of each image row
     int32_t *tri;          // output [cap_tri][3]
     int32_t *ntri;         // output count
     int32_t *err;          // bit 0: a star failed, bit 1: capacity, bit 2: slots overflowed
@@ -73,12 +80,16 @@ __device__ __forceinline__ int64_t dt_orient(int ax, int ay, int bx, int by, int
 }
 
 // Sign of "C strictly inside the circle through P, A, B" (P, A, B
-// counter-clockwise), with the symbolic tie-break on the list indices.
+// counter-clockwise), with the symbolic tie-break on the list indices.  T is
+// the arithmetic type of the determinant: int is exact while every coordinate
+// differs from P's by at most 64 (6 terms of at most 64*64*8192), int64_t
+// always (differences below 2^15).
+template <typename T>
 __device__ __forceinline__ int dt_incircle(const int4 &P, const int4 &A, const int4 &B, const int4 &C) {
-    const int64_t ax = A.x - P.x, ay = A.y - P.y, bx = B.x - P.x, by = B.y - P.y, cx = C.x - P.x, cy = C.y - P.y;
-    const int64_t al = ax * ax + ay * ay, bl = bx * bx + by * by, cl = cx * cx + cy * cy;
+    const T ax = A.x - P.x, ay = A.y - P.y, bx = B.x - P.x, by = B.y - P.y, cx = C.x - P.x, cy = C.y - P.y;
+    const T al = ax * ax + ay * ay, bl = bx * bx + by * by, cl = cx * cx + cy * cy;
     // value = -det[[a, |a|^2], [b, |b|^2], [c, |c|^2]] (relative to P)
-    const int64_t det = ax * (by * cl - bl * cy) - ay * (bx * cl - bl * cx) + al * (bx * cy - by * cx);
+    const T det = ax * (by * cl - bl * cy) - ay * (bx * cl - bl * cx) + al * (bx * cy - by * cx);
     if (det != 0) return det < 0 ? 1 : -1;
     // raising lift i by eps_i adds eps_P*orient(A,B,C) + eps_A*orient(B,P,C)
     // + eps_B*orient(P,A,C) - eps_C*orient(P,A,B); the lowest index decides
@@ -107,6 +118,10 @@ __global__ void dt_points_kernel(DtArgs a) {
         S.status[i] = 0;
         S.owned[i] = 0;
         atomicAdd(S.cell_cnt + dt_cell(a, x, v), 1);
+        if (v >= 0 && v < a.h) {
+            atomicMin(S.rowmin + v, x);
+            atomicMax(S.rowmax + v, x);
+        }
     }
 }
 
@@ -188,6 +203,11 @@ constexpr int kDtCandCap = 160;   // pass-1 candidates cached per warp
 constexpr int kDtSlots = 32;      // owned triangles kept per point
 constexpr int kDtWarps = 8;       // warps per CTA
 
+__device__ __forceinline__ int4 shfl4_from(const int4 &v, int src) {
+    return make_int4(__shfl_sync(0xFFFFFFFFu, v.x, src), __shfl_sync(0xFFFFFFFFu, v.y, src),
+                     __shfl_sync(0xFFFFFFFFu, v.z, src), __shfl_sync(0xFFFFFFFFu, v.w, src));
+}
+
 __device__ __forceinline__ int4 shfl4(const int4 &v, int src_xor) {
     return make_int4(__shfl_xor_sync(0xFFFFFFFFu, v.x, src_xor), __shfl_xor_sync(0xFFFFFFFFu, v.y, src_xor),
                      __shfl_xor_sync(0xFFFFFFFFu, v.z, src_xor), __shfl_xor_sync(0xFFFFFFFFu, v.w, src_xor));
@@ -196,17 +216,34 @@ __device__ __forceinline__ int4 shfl4(const int4 &v, int src_xor) {
 // Better of two third-vertex candidates in the pencil order of edge (p, e):
 // ccw: triangles (p, e, c); else (p, c, e).  c2 beats c1 iff c2 lies inside
 // the circle of c1's triangle.  w = 0 marks "no candidate".
+template <typename T>
 __device__ __forceinline__ int4 dt_better(const int4 &c1, const int4 &c2, const int4 &p, const int4 &e, bool ccw) {
     if (!c2.w) return c1;
     if (!c1.w) return c2;
-    const int s = ccw ? dt_incircle(p, e, c1, c2) : dt_incircle(p, c1, e, c2);
+    const int s = ccw ? dt_incircle<T>(p, e, c1, c2) : dt_incircle<T>(p, c1, e, c2);
     return (s > 0 || (s == 0 && c2.z < c1.z)) ? c2 : c1;
 }
 
+template <typename T>
 __device__ __forceinline__ int4 dt_warp_best(int4 best, const int4 &p, const int4 &e, bool ccw) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = dt_better(best, shfl4(best, o), p, e, ccw);
+    for (int o = 16; o > 0; o >>= 1) best = dt_better<T>(best, shfl4(best, o), p, e, ccw);
     return best;
+}
+
+// True iff no point lies strictly left (left = true) or strictly right of the
+// line p->e.  Within one image row the orientation is affine in x, so the
+// row's two extreme points decide for the whole row.  Warp collective.
+__device__ __forceinline__ bool dt_open_edge_ok(const DtSide &S, int h, const int4 &p, const int4 &e, bool left,
+                                                int lane) {
+    bool bad = false;
+    for (int y = lane; y < h && !bad; y += 32) {
+        const int x0 = S.rowmin[y], x1 = S.rowmax[y];
+        if (x0 > x1) continue;
+        const int64_t o0 = dt_orient(p.x, p.y, e.x, e.y, x0, y), o1 = dt_orient(p.x, p.y, e.x, e.y, x1, y);
+        bad = left ? (o0 > 0 || o1 > 0) : (o0 < 0 || o1 < 0);
+    }
+    return !__any_sync(0xFFFFFFFFu, bad);
 }
 
 __device__ __forceinline__ unsigned long long dt_nn_key(const int4 &p, const int4 &q) {
@@ -247,174 +284,589 @@ __device__ __forceinline__ void dt_record(const DtSide &S, int i, int &written, 
     }
 }
 
-// Pass 1: one warp per point, candidates within kDtRadius cached in shared
-// memory.  Open stars (hull points), stars with too many candidates and
-// stars whose circles leave the radius are queued for pass 2.
-__global__ void __launch_bounds__(32 * kDtWarps) dt_pass1_kernel(DtArgs a) {
-    __shared__ int4 s_cand[kDtWarps][kDtCandCap];
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
-    const int n = min(max(*a.count, 0), a.cap);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int4 *cand = s_cand[warp];
-    const int R = kDtRadius;
-    const int64_t R2 = (int64_t)R * R;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
-        if (S.status[i] < 0) continue;  // duplicate
-        const int4 p = S.pts[S.slot[i]];
-        // gather the candidates
-        int k = 0;
-        bool overflow = false;
-        const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, (p.x + R) / kDtCell);
-        const int cy0 = max(0, p.y - R) / kDtCell, cy1 = min(a.gh - 1, (p.y + R) / kDtCell);
-        for (int cy = cy0; cy <= cy1; ++cy) {
-            const int s0 = S.cell_start[cy * a.gw + cx0], e0 = S.cell_start[cy * a.gw + cx1 + 1];
-            for (int j = s0; j < e0; j += 32) {
-                bool take = false;
-                int4 q = make_int4(0, 0, 0, 0);
-                if (j + lane < e0) {
-                    q = S.pts[j + lane];
-                    const int64_t dx = q.x - p.x, dy = q.y - p.y;
-                    take = q.w && q.z != p.z && dx * dx + dy * dy <= R2;
-                }
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-                const int pos = k + __popc(m & ((1u << lane) - 1u));
-                if (take && pos < kDtCandCap) cand[pos] = q;
-                k += __popc(m);
+// The Delaunay third vertex of directed edge (p, e) on side s (+1 left,
+// -1 right) is the candidate c with s*orient(p,e,c) > 0 that minimises the
+// pencil parameter t(c) = N/D, N = |c-p|^2 - (e-p).(c-p), D = 2 s orient(p,e,c)
+// (the circles through p and e are nested on each side in the order of t).
+// Equal t means cocircular: the symbolic tie-break decides.  T: arithmetic
+// type of the cross-multiplied comparison.
+template <typename T>
+struct DtKey {
+    T N, D;
+};
+
+template <typename T>
+__device__ __forceinline__ DtKey<T> dt_key(const int4 &p, const int4 &e, const int4 &c, int side) {
+    const T ex = e.x - p.x, ey = e.y - p.y, cx = c.x - p.x, cy = c.y - p.y;
+    DtKey<T> k;
+    k.N = cx * cx + cy * cy - (ex * cx + ey * cy);
+    k.D = 2 * side * (ex * cy - ey * cx);
+    return k;
+}
+
+// Does c2 (key k2) beat c1 (key k1) for edge (p, e) on side s?
+template <typename T>
+__device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T> &k2, const int4 &p, const int4 &e,
+                                              const int4 &c1, const int4 &c2, int side) {
+    const T l = k2.N * k1.D, r = k1.N * k2.D;
+    if (l != r) return l < r;
+    const int s = side > 0 ? dt_incircle<int64_t>(p, e, c1, c2) : dt_incircle<int64_t>(p, c1, e, c2);
+    return s > 0 || (s == 0 && c2.z < c1.z);
+}
+
+// Pass 1: one group of kDtGroup lanes per point.  The group lists the
+// points within kDtRadius of p (indices into the grid-sorted array, in
+// shared memory), then wraps the star: each lane keeps the best candidate of
+// its share of the list under the pencil key (32-bit integers are exact:
+// every difference is at most 32) and the group reduces with shuffles.  A
+// star is accepted when every triangle's circumdisc lies inside the radius
+// (4 r^2 <= R^2, exact) and, for an open star (p on the hull), nothing lies
+// beyond either open edge (checked against the extreme points of every image
+// row).  Other stars are queued for pass 2.
+constexpr int kDtGroup = 8;
+constexpr int kDtGroupThreads = 256;
+constexpr int kDtListCap = 128;  // candidates per point (the radius-32 disc holds at most ~120 lattice points)
+
+__device__ __forceinline__ bool dt_small_circle_exact(const int4 &p, const int4 &a, const int4 &b, int R) {
+    const int64_t pa = (int64_t)(a.x - p.x) * (a.x - p.x) + (int64_t)(a.y - p.y) * (a.y - p.y);
+    const int64_t pb = (int64_t)(b.x - p.x) * (b.x - p.x) + (int64_t)(b.y - p.y) * (b.y - p.y);
+    const int64_t ab = (int64_t)(b.x - a.x) * (b.x - a.x) + (int64_t)(b.y - a.y) * (b.y - a.y);
+    const int64_t ar = dt_orient(p.x, p.y, a.x, a.y, b.x, b.y);
+    return pa * pb * ab <= (int64_t)R * R * ar * ar;  // below 2^43 for R = 32
+}
+
+__device__ __forceinline__ int4 gshfl4(unsigned m, const int4 &v, int src) {
+    return make_int4(__shfl_sync(m, v.x, src), __shfl_sync(m, v.y, src), __shfl_sync(m, v.z, src),
+                     __shfl_sync(m, v.w, src));
+}
+
+// Group reduction of (best, key) under the pencil order of edge (p, e).
+__device__ __forceinline__ int4 dt_group_best(unsigned m, int4 best, DtKey<int> bk, const int4 &p, const int4 &e,
+                                              int side) {
+#pragma unroll
+    for (int o = kDtGroup / 2; o > 0; o >>= 1) {
+        int4 ob;
+        ob.x = __shfl_xor_sync(m, best.x, o);
+        ob.y = __shfl_xor_sync(m, best.y, o);
+        ob.z = __shfl_xor_sync(m, best.z, o);
+        ob.w = __shfl_xor_sync(m, best.w, o);
+        DtKey<int> ok;
+        ok.N = __shfl_xor_sync(m, bk.N, o);
+        ok.D = __shfl_xor_sync(m, bk.D, o);
+        bool take = false;
+        if (ob.w) {
+            if (!best.w) {
+                take = true;
+            } else {
+                // the same decision on both lanes of the pair: compare in a
+                // fixed order (lower index first)
+                const bool mine_first = best.z < ob.z;
+                const bool second_wins = mine_first ? dt_key_better<int>(bk, ok, p, e, best, ob, side)
+                                                    : dt_key_better<int>(ok, bk, p, e, ob, best, side);
+                take = mine_first ? second_wins : !second_wins;
             }
         }
-        if (k > kDtCandCap) overflow = true;
-        __syncwarp();
-        bool certified = !overflow && k > 0;
-        int written = 0;
-        if (certified) {
-            unsigned long long key = ~0ull;
-            for (int j = lane; j < k; j += 32) {
-                const unsigned long long kk = dt_nn_key(p, cand[j]);
-                key = kk < key ? kk : key;
+        if (take) {
+            best = ob;
+            bk = ok;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel(DtArgs a) {
+    __shared__ int s_list[kDtGroupThreads / kDtGroup][kDtListCap];
+    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+    const int n = min(max(*a.count, 0), a.cap);
+    const int lane = threadIdx.x & 31, gl = lane & (kDtGroup - 1), gbase = lane & ~(kDtGroup - 1);
+    const unsigned gm = ((1u << kDtGroup) - 1u) << gbase;
+    int *list = s_list[threadIdx.x / kDtGroup];
+    const int R = kDtRadius;
+    const int groups = gridDim.x * (kDtGroupThreads / kDtGroup);
+    for (int j = blockIdx.x * (kDtGroupThreads / kDtGroup) + threadIdx.x / kDtGroup; j < n; j += groups) {
+        const int4 p = S.pts[j];
+        if (!p.w || S.status[p.z] != 0) continue;
+        // candidates: lanes fetch the cell rows' ranges, then stride over them
+        const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, max(0, p.x + R) / kDtCell);
+        const int cy0 = max(0, p.y - R) / kDtCell, cy1 = min(a.gh - 1, max(0, p.y + R) / kDtCell);
+        const int nrows = cy1 - cy0 + 1;  // at most 5
+        int rs = 0, re = 0;
+        if (gl < nrows) {
+            rs = S.cell_start[(cy0 + gl) * a.gw + cx0];
+            re = S.cell_start[(cy0 + gl) * a.gw + cx1 + 1];
+        }
+        int k = 0;
+        unsigned long long key = ~0ull;
+        int nn = -1;
+        for (int r = 0; r < nrows; ++r) {
+            const int s0 = __shfl_sync(gm, rs, gbase + r), e0 = __shfl_sync(gm, re, gbase + r);
+            for (int c = s0; c < e0; c += kDtGroup) {
+                bool take = false;
+                if (c + gl < e0) {
+                    const int4 q = S.pts[c + gl];
+                    const int dx = q.x - p.x, dy = q.y - p.y, d2 = dx * dx + dy * dy;
+                    take = q.w && q.z != p.z && d2 <= R * R;
+                    if (take) {
+                        const unsigned long long kk = ((unsigned long long)d2 << 32) | (unsigned)q.z;
+                        if (kk < key) {
+                            key = kk;
+                            nn = c + gl;
+                        }
+                    }
+                }
+                const unsigned b = __ballot_sync(gm, take) >> gbase;
+                const int pos = k + __popc(b & ((1u << gl) - 1u));
+                if (take && pos < kDtListCap) list[pos] = c + gl;
+                k += __popc(b);
             }
-            key = warp_min64(key);
-            int4 first = make_int4(0, 0, (int)(unsigned)(key & 0xFFFFFFFFu), 1);
-            for (int j = 0; j < k; ++j)  // coordinates of the nearest neighbour
-                if (cand[j].z == first.z) first = cand[j];
+        }
+        __syncwarp(gm);
+        bool certified = k > 0 && k <= kDtListCap;
+        int written = 0;
+        bool open_l = false, open_r = false;
+        int4 e_l = p, e_r = p;
+        if (certified) {
+            // nearest neighbour of the group
+            unsigned long long kmin = key;
+#pragma unroll
+            for (int o = kDtGroup / 2; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(gm, kmin, o);
+                kmin = other < kmin ? other : kmin;
+            }
+            const int src = __ffs(__ballot_sync(gm, key == kmin) >> gbase) - 1;
+            const int first_slot = __shfl_sync(gm, nn, gbase + src);
+            const int4 first = S.pts[first_slot];
             int4 cur = first;
             bool closed = false;
-            for (int step = 0; step < k + 1 && certified; ++step) {
+            for (int step = 0; step <= k && certified; ++step) {  // counter-clockwise
                 int4 best = make_int4(0, 0, 0, 0);
-                for (int j = lane; j < k; j += 32) {
-                    const int4 q = cand[j];
-                    if (q.z != cur.z && dt_orient(p.x, p.y, cur.x, cur.y, q.x, q.y) > 0)
-                        best = dt_better(best, q, p, cur, true);
+                DtKey<int> bk{0, 1};
+                for (int c = gl; c < k; c += kDtGroup) {
+                    const int4 q = S.pts[list[c]];
+                    if (q.z == cur.z) continue;
+                    const DtKey<int> qk = dt_key<int>(p, cur, q, +1);
+                    if (qk.D <= 0) continue;
+                    if (!best.w || dt_key_better<int>(bk, qk, p, cur, best, q, +1)) {
+                        best = q;
+                        bk = qk;
+                    }
                 }
-                best = dt_warp_best(best, p, cur, true);
-                if (!best.w || !dt_small_circle(p, cur, best, R)) {
-                    certified = false;  // open side or large circle: pass 2
+                best = dt_group_best(gm, best, bk, p, cur, +1);
+                if (!best.w) {
+                    open_l = true;
+                    e_l = cur;
                     break;
                 }
-                dt_record(S, i, written, p, cur, best, lane == 0);
+                if (!dt_small_circle_exact(p, cur, best, R)) {
+                    certified = false;
+                    break;
+                }
+                dt_record(S, p.z, written, p, cur, best, gl == 0);
                 if (best.z == first.z) {
                     closed = true;
                     break;
                 }
                 cur = best;
             }
-            if (!closed) certified = false;
-        }
-        if (lane == 0) {
-            if (certified) {
-                S.status[i] = 1;
-                S.owned[i] = written;
-                if (written > kDtSlots) atomicOr(S.err, 4);
-            } else {
-                S.pending[atomicAdd(S.npending, 1)] = i;
+            if (certified && !closed) {
+                if (!open_l) certified = false;  // ran out of steps
+                cur = first;
+                for (int step = 0; step <= k && certified; ++step) {  // clockwise
+                    int4 best = make_int4(0, 0, 0, 0);
+                    DtKey<int> bk{0, 1};
+                    for (int c = gl; c < k; c += kDtGroup) {
+                        const int4 q = S.pts[list[c]];
+                        if (q.z == cur.z) continue;
+                        const DtKey<int> qk = dt_key<int>(p, cur, q, -1);
+                        if (qk.D <= 0) continue;
+                        if (!best.w || dt_key_better<int>(bk, qk, p, cur, best, q, -1)) {
+                            best = q;
+                            bk = qk;
+                        }
+                    }
+                    best = dt_group_best(gm, best, bk, p, cur, -1);
+                    if (!best.w) {
+                        open_r = true;
+                        e_r = cur;
+                        break;
+                    }
+                    if (!dt_small_circle_exact(p, best, cur, R)) {
+                        certified = false;
+                        break;
+                    }
+                    dt_record(S, p.z, written, p, best, cur, gl == 0);
+                    cur = best;
+                }
+                if (!open_r) certified = false;
+            }
+            // open edges (p on the hull): nothing may lie beyond them
+            for (int side = 0; side < 2 && certified; ++side) {
+                const bool open = side ? open_r : open_l;
+                if (!open) continue;
+                const int4 e = side ? e_r : e_l;
+                bool bad = false;
+                for (int y = gl; y < a.h && !bad; y += kDtGroup) {
+                    const int x0 = S.rowmin[y], x1 = S.rowmax[y];
+                    if (x0 > x1) continue;
+                    const int64_t o0 = dt_orient(p.x, p.y, e.x, e.y, x0, y);
+                    const int64_t o1 = dt_orient(p.x, p.y, e.x, e.y, x1, y);
+                    bad = side ? (o0 < 0 || o1 < 0) : (o0 > 0 || o1 > 0);
+                }
+                if (__ballot_sync(gm, bad) & gm) certified = false;
             }
         }
+        if (gl == 0) {
+            if (certified) {
+                S.status[p.z] = 1;
+                S.owned[p.z] = written;
+                if (written > kDtSlots) atomicOr(S.err, 4);
+            } else {
+                S.pending[atomicAdd(S.npending, 1)] = p.z;
+            }
+        }
+        __syncwarp(gm);
     }
 }
 
-// Pass 2: one CTA per queued point, every point a candidate (so the star is
-// exact and open sides are hull edges).
-__device__ __forceinline__ int4 dt_block_best(int4 best, const int4 &p, const int4 &e, bool ccw, int4 *s_red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    best = dt_warp_best(best, p, e, ccw);
-    __syncthreads();
-    if (lane == 0) s_red[warp] = best;
-    __syncthreads();
-    int4 r = lane < (int)(blockDim.x >> 5) ? s_red[lane] : make_int4(0, 0, 0, 0);
-    r = dt_warp_best(r, p, e, ccw);
-    return r;  // every warp holds the same result
+// Pass 2: one CTA per queued point.  The points within kDtRadius2 are cached
+// in shared memory; every wrap step first takes the best cached candidate and
+// keeps it when its circumdisc lies inside that radius (then no other point
+// can beat it); otherwise (large circle, no cached candidate on that side, or
+// the cache overflowed) the step scans every point, which is exact.  So
+// every queued star comes out exact.
+constexpr int kDtRadius2 = 192;
+constexpr int kDtCandCap2 = 3072;  // pass-2 candidates cached per CTA (48 KB)
+constexpr int kDtMaxRows = 64;     // cell rows a radius-192 disc spans, with margin
+static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "pass-2 disc must fit the row table");
+
+// CTA reduction of the threads' (best, key) under the pencil order: each
+// warp reduces with shuffles, warp 0 reduces the warps' results, and every
+// thread reads the winner from shared memory.
+template <int UNUSED = 0>
+__device__ __forceinline__ int4 dt_warp_key_best(int4 best, DtKey<int64_t> &bk, const int4 &p, const int4 &e,
+                                                 int side) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int4 ob = shfl4(best, o);
+        DtKey<int64_t> ok;
+        ok.N = __shfl_xor_sync(0xFFFFFFFFu, bk.N, o);
+        ok.D = __shfl_xor_sync(0xFFFFFFFFu, bk.D, o);
+        if (ob.w && (!best.w || dt_key_better<int64_t>(bk, ok, p, e, best, ob, side))) {
+            best = ob;
+            bk = ok;
+        }
+    }
+    return best;
 }
 
-__global__ void __launch_bounds__(32 * kDtWarps) dt_pass2_kernel(DtArgs a) {
-    __shared__ int4 s_red[kDtWarps];
-    __shared__ unsigned long long s_key[kDtWarps];
+__device__ __forceinline__ int4 dt_block_best(int4 best, DtKey<int64_t> bk, const int4 &p, const int4 &e, int side,
+                                              int4 *s_red, int64_t *s_n, int64_t *s_d) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    best = dt_warp_key_best(best, bk, p, e, side);
+    __syncthreads();
+    if (lane == 0) {
+        s_red[warp] = best;
+        s_n[warp] = bk.N;
+        s_d[warp] = bk.D;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int4 b = lane < nw ? s_red[lane] : make_int4(0, 0, 0, 0);
+        DtKey<int64_t> k{lane < nw ? s_n[lane] : 0, lane < nw ? s_d[lane] : 1};
+        b = dt_warp_key_best(b, k, p, e, side);
+        if (lane == 0) s_red[32] = b;
+    }
+    __syncthreads();
+    return s_red[32];
+}
+
+struct DtBlockShared {
+    int4 red[33];
+    int64_t rn[32], rd[32];
+    unsigned long long key[32];
+    int rs[kDtMaxRows], rlen[kDtMaxRows + 1], cnt;
+};
+
+// Best third vertex for edge (p, cur) on `side`, over the cache (cand, k) or,
+// with cand == NULL, over every alive point.
+__device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, const int4 &cur, int side,
+                                              const int4 *cand, int k, int n, DtBlockShared &sh) {
+    int4 best = make_int4(0, 0, 0, 0);
+    DtKey<int64_t> bk{0, 1};
+    auto consider = [&](const int4 &q) {
+        if (q.z == cur.z || q.z == p.z || !q.w) return;
+        const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
+        if (qk.D <= 0) return;
+        if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
+            best = q;
+            bk = qk;
+        }
+    };
+    if (cand) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) consider(cand[j]);
+    } else {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) consider(S.pts[j]);
+    }
+    return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
+}
+
+// Exact step for edge (p, cur) on `side` without the radius limit.  Only
+// points strictly inside the closed circumdisc of (p, cur, bc) can beat the
+// cached best bc, and with no cached candidate only the open half-plane on
+// that side matters; so the CTA scans the grid cells that meet that region
+// (disc or half-plane, widened by 2 pixels and one cell, in double precision:
+// a superset), taking each cell row's cells as one contiguous range.
+__device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int4 &p, const int4 &cur, int side,
+                                     const int4 &bc, DtBlockShared &sh, int *r_start, int *r_pre) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    double ccx = 0, ccy = 0, rad = 0;
+    const bool disc = bc.w != 0;
+    if (disc) {
+        const double ax = cur.x - p.x, ay = cur.y - p.y, bx = bc.x - p.x, by = bc.y - p.y;
+        const double d = 2.0 * (ax * by - ay * bx);
+        const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+        const double ux = (by * a2 - ay * b2) / d, uy = (ax * b2 - bx * a2) / d;
+        ccx = p.x + ux;
+        ccy = p.y + uy;
+        rad = sqrt(ux * ux + uy * uy) + 2.0;
+    }
+    // half-plane: side * ((cur.x-p.x)(y-p.y) - (cur.y-p.y)(x-p.x)) > 0
+    const double ex = cur.x - p.x, ey = cur.y - p.y;
+    for (int cy = tid; cy < a.gh; cy += nth) {
+        const double y0 = cy * kDtCell - 2.0, y1 = cy * kDtCell + kDtCell + 1.0;
+        double xlo = -1e30, xhi = 1e30;
+        bool any = true;
+        if (disc) {
+            const double dy = ccy < y0 ? y0 - ccy : (ccy > y1 ? ccy - y1 : 0.0);
+            if (dy > rad) {
+                any = false;
+            } else {
+                const double hc = sqrt(rad * rad - dy * dy) + 2.0;
+                xlo = ccx - hc;
+                xhi = ccx + hc;
+            }
+        } else if (ey != 0.0) {
+            // boundary x at the band's two edges; the admissible side of x
+            double xa = p.x + ex * (y0 - p.y) / ey, xb = p.x + ex * (y1 - p.y) / ey;
+            const double xm = xa < xb ? xa : xb, xM = xa < xb ? xb : xa;
+            // side*(ex*(y-py) - ey*(x-px)) > 0  <=>  x < boundary if side*ey > 0
+            if (side * ey > 0) xhi = xM + 2.0; else xlo = xm - 2.0;
+        } else {
+            // horizontal edge: the whole row is in or out
+            any = side * ex * ((y0 + y1) * 0.5 - p.y) > 0 || (y0 <= p.y && p.y <= y1);
+        }
+        int c0 = 0, c1 = a.gw - 1;
+        if (any) {
+            c0 = xlo < 0 ? 0 : (int)fmin((double)(a.gw - 1), floor(xlo / kDtCell) - 1);
+            c1 = xhi >= 1e29 ? a.gw - 1 : (int)fmax(0.0, fmin((double)(a.gw - 1), floor(xhi / kDtCell) + 1));
+            c0 = max(0, c0);
+        }
+        const int s0 = any && c0 <= c1 ? S.cell_start[cy * a.gw + c0] : 0;
+        const int e0 = any && c0 <= c1 ? S.cell_start[cy * a.gw + c1 + 1] : 0;
+        r_start[cy] = s0;
+        r_pre[cy] = e0 - s0;  // length for now
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int cy = 0; cy < a.gh; ++cy) {
+            const int l = r_pre[cy];
+            r_pre[cy] = acc;
+            acc += l;
+        }
+        r_pre[a.gh] = acc;
+    }
+    __syncthreads();
+    const int total = r_pre[a.gh];
+    int4 best = bc;
+    DtKey<int64_t> bk = bc.w ? dt_key<int64_t>(p, cur, bc, side) : DtKey<int64_t>{0, 1};
+    for (int j = tid; j < total; j += nth) {
+        int lo = 0, hi = a.gh - 1;  // last row whose prefix is <= j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (r_pre[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int4 q = S.pts[r_start[lo] + (j - r_pre[lo])];
+        if (!q.w || q.z == cur.z || q.z == p.z) continue;
+        const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
+        if (qk.D <= 0) continue;
+        if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
+            best = q;
+            bk = qk;
+        }
+    }
+    return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
+}
+
+// Exact star of p, CTA-wide.  cand/k: cache of the points within kDtRadius2
+// (k > kDtCandCap2: unusable).  Writes the owned triangles to the slots or,
+// with out != NULL, to out.  Returns 1, or -1 if it exceeded kDtMaxStar, or
+// 0 if cached_only and a step needed every point.
+__device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4 &p, int n, const int4 *cand, int k,
+                             int *written, int32_t *out, DtBlockShared &sh, bool cached_only, int *r_start,
+                             int *r_pre) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
+    const bool cached = cand && k <= kDtCandCap2;
+    // nearest neighbour over every point (cheap: one pass)
+    unsigned long long key = ~0ull;
+    for (int j = tid; j < n; j += nth) {
+        const int4 q = S.pts[j];
+        if (q.w && q.z != p.z) {
+            const unsigned long long kk = dt_nn_key(p, q);
+            key = kk < key ? kk : key;
+        }
+    }
+    key = warp_min64(key);
+    __syncthreads();
+    if (lane == 0) sh.key[warp] = key;
+    __syncthreads();
+    key = lane < (nth >> 5) ? sh.key[lane] : ~0ull;
+    key = warp_min64(key);
+    *written = 0;
+    if (key == ~0ull) return 1;  // p is the only point
+    const int4 first = S.pts[S.slot[(int)(unsigned)(key & 0xFFFFFFFFu)]];
+    int wr = 0;
+    auto emit = [&](const int4 &u, const int4 &v) {  // triangle (p, u, v), ccw
+        if (p.z < u.z && p.z < v.z) {
+            if (tid == 0) {
+                if (out) {
+                    out[3 * wr] = p.z;
+                    out[3 * wr + 1] = u.z;
+                    out[3 * wr + 2] = v.z;
+                } else if (wr < kDtSlots) {
+                    int32_t *slot = S.slots + ((size_t)i * kDtSlots + wr) * 2;
+                    slot[0] = u.z;
+                    slot[1] = v.z;
+                }
+            }
+            ++wr;
+        }
+    };
+    bool bail = false;  // cached_only: a step needed every point
+    auto next = [&](const int4 &cur, int side) {
+        int4 b = make_int4(0, 0, 0, 0);
+        if (cached) {
+            b = dt_block_step(S, p, cur, side, cand, k, n, sh);
+            const bool small = b.w && (side > 0 ? dt_small_circle(p, cur, b, kDtRadius2)
+                                                : dt_small_circle(p, b, cur, kDtRadius2));
+            if (small) return b;
+        }
+        if (cached_only) {
+            bail = true;
+            return make_int4(0, 0, 0, 0);
+        }
+        if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_pre);
+        return dt_block_step(S, p, cur, side, nullptr, 0, n, sh);
+    };
+    int4 cur = first;
+    bool closed = false;
+    int step = 0;
+    for (; step < kDtMaxStar; ++step) {  // counter-clockwise
+        const int4 best = next(cur, +1);
+        if (bail) return 0;
+        if (!best.w) break;  // hull edge
+        emit(cur, best);
+        if (best.z == first.z) {
+            closed = true;
+            break;
+        }
+        cur = best;
+    }
+    if (step >= kDtMaxStar) return -1;
+    if (!closed) {  // clockwise from the first edge
+        cur = first;
+        for (step = 0; step < kDtMaxStar; ++step) {
+            const int4 best = next(cur, -1);
+            if (bail) return 0;
+            if (!best.w) break;
+            emit(best, cur);
+            cur = best;
+        }
+        if (step >= kDtMaxStar) return -1;
+    }
+    *written = wr;
+    return 1;
+}
+
+// Gathers the points within R of p into the shared cache; returns their
+// number (more than kDtCandCap2 means the cache overflowed).  The cell rows'
+// ranges are fetched at once, the candidates read as one flat index space,
+// and each warp places its hits with one atomic.
+__device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, int R, int4 *cand,
+                               DtBlockShared &sh) {
+    const int tid = threadIdx.x, lane = tid & 31, nth = blockDim.x;
+    const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, max(0, p.x + R) / kDtCell);
+    const int cy0 = max(0, p.y - R) / kDtCell, cy1 = min(a.gh - 1, max(0, p.y + R) / kDtCell);
+    const int nrows = min(kDtMaxRows, cy1 - cy0 + 1);
+    __syncthreads();
+    if (tid < nrows) {
+        const int r0 = S.cell_start[(cy0 + tid) * a.gw + cx0], r1 = S.cell_start[(cy0 + tid) * a.gw + cx1 + 1];
+        sh.rs[tid] = r0;
+        sh.rlen[tid] = r1 - r0;
+    }
+    if (tid == 0) sh.cnt = 0;
+    __syncthreads();
+    if (tid == 0) {  // exclusive prefix of the row lengths, in place
+        int acc = 0;
+        for (int r = 0; r < nrows; ++r) {
+            const int l = sh.rlen[r];
+            sh.rlen[r] = acc;
+            acc += l;
+        }
+        sh.rlen[nrows] = acc;
+    }
+    __syncthreads();
+    const int total = sh.rlen[nrows];
+    const int64_t R2 = (int64_t)R * R;
+    for (int j0 = 0; j0 < total; j0 += nth) {
+        const int j = j0 + tid;
+        bool take = false;
+        int4 q = make_int4(0, 0, 0, 0);
+        if (j < total) {
+            int lo = 0, hi = nrows - 1;  // last row whose prefix is <= j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sh.rlen[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            q = S.pts[sh.rs[lo] + (j - sh.rlen[lo])];
+            const int64_t dx = q.x - p.x, dy = q.y - p.y;
+            take = q.w && q.z != p.z && dx * dx + dy * dy <= R2;
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&sh.cnt, __popc(m));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        if (take && pos < kDtCandCap2) cand[pos] = q;
+    }
+    __syncthreads();
+    return sh.cnt;
+}
+
+// mode 2: cached steps only, a star that needs more is queued again; mode 3:
+// exact, over that second queue; mode 4: exact, over the first queue.
+__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a, int mode) {
+    extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows (mode 3)
+    __shared__ DtBlockShared sh;
+    int *r_start = mode >= 3 ? reinterpret_cast<int *>(s_cand + kDtCandCap2) : nullptr;
+    int *r_pre = mode >= 3 ? r_start + a.gh : nullptr;
     const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int np = *S.npending;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
-    for (int q0 = blockIdx.x; q0 < np; q0 += gridDim.x) {
-        const int i = S.pending[q0];
+    const int32_t *queue = mode == 3 ? S.pending2 : S.pending;
+    const int nq = mode == 3 ? *S.npending2 : *S.npending;
+    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) {
+        const int i = queue[q0];
         const int4 p = S.pts[S.slot[i]];
-        // nearest neighbour over all points
-        unsigned long long key = ~0ull;
-        for (int j = tid; j < n; j += nth) {
-            const int4 q = S.pts[j];
-            if (q.w && q.z != p.z) {
-                const unsigned long long kk = dt_nn_key(p, q);
-                key = kk < key ? kk : key;
-            }
-        }
-        key = warp_min64(key);
-        __syncthreads();
-        if (lane == 0) s_key[warp] = key;
-        __syncthreads();
-        key = lane < (nth >> 5) ? s_key[lane] : ~0ull;
-        key = warp_min64(key);
+        const int k = dt_block_gather(a, S, p, kDtRadius2, s_cand, sh);
         int written = 0;
-        bool ok = true;
-        if (key != ~0ull) {
-            const int4 first = S.pts[S.slot[(int)(unsigned)(key & 0xFFFFFFFFu)]];
-            int4 cur = first;
-            bool closed = false;
-            int step = 0;
-            for (; step < kDtMaxStar; ++step) {  // counter-clockwise
-                int4 best = make_int4(0, 0, 0, 0);
-                for (int j = tid; j < n; j += nth) {
-                    const int4 q = S.pts[j];
-                    if (q.w && q.z != p.z && q.z != cur.z && dt_orient(p.x, p.y, cur.x, cur.y, q.x, q.y) > 0)
-                        best = dt_better(best, q, p, cur, true);
-                }
-                best = dt_block_best(best, p, cur, true, s_red);
-                if (!best.w) break;  // hull edge
-                dt_record(S, i, written, p, cur, best, tid == 0);
-                if (best.z == first.z) {
-                    closed = true;
-                    break;
-                }
-                cur = best;
-            }
-            if (step >= kDtMaxStar) ok = false;
-            if (!closed && ok) {  // clockwise from the first edge
-                cur = first;
-                for (step = 0; step < kDtMaxStar; ++step) {
-                    int4 best = make_int4(0, 0, 0, 0);
-                    for (int j = tid; j < n; j += nth) {
-                        const int4 q = S.pts[j];
-                        if (q.w && q.z != p.z && q.z != cur.z && dt_orient(p.x, p.y, cur.x, cur.y, q.x, q.y) < 0)
-                            best = dt_better(best, q, p, cur, false);
-                    }
-                    best = dt_block_best(best, p, cur, false, s_red);
-                    if (!best.w) break;
-                    dt_record(S, i, written, p, best, cur, tid == 0);
-                    cur = best;
-                }
-                if (step >= kDtMaxStar) ok = false;
-            }
-        }
-        if (tid == 0) {
-            if (ok) {
+        const int r = dt_block_star(a, S, i, p, n, s_cand, k, &written, nullptr, sh, mode == 2, r_start, r_pre);
+        if (threadIdx.x == 0) {
+            if (r == 1) {
                 S.status[i] = 2;
                 S.owned[i] = written;
                 if (written > kDtSlots) atomicOr(S.err, 4);
+            } else if (r == 0) {
+                S.pending2[atomicAdd(S.npending2, 1)] = i;
             } else {
                 atomicOr(S.err, 1);
             }
@@ -480,81 +932,18 @@ __global__ void dt_emit_kernel(DtArgs a) {
 }
 
 // Points that own more than kDtSlots triangles (fan apexes): one CTA each
-// rebuilds its star over all points and writes the owned triangles in order.
-__global__ void __launch_bounds__(32 * kDtWarps) dt_emit_big_kernel(DtArgs a) {
-    __shared__ int4 s_red[kDtWarps];
-    __shared__ unsigned long long s_key[kDtWarps];
+// rebuilds its star over every point and writes the owned triangles in order.
+__global__ void __launch_bounds__(256) dt_emit_big_kernel(DtArgs a) {
+    __shared__ DtBlockShared sh;
     const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     if (*S.ntri < 0 || !(*S.err & 4)) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         if (S.owned[i] <= kDtSlots) continue;
         const int4 p = S.pts[S.slot[i]];
-        int32_t *out = S.tri + 3 * (size_t)S.offset[i];
-        unsigned long long key = ~0ull;
-        for (int j = tid; j < n; j += nth) {
-            const int4 q = S.pts[j];
-            if (q.w && q.z != p.z) {
-                const unsigned long long kk = dt_nn_key(p, q);
-                key = kk < key ? kk : key;
-            }
-        }
-        key = warp_min64(key);
-        __syncthreads();
-        if (lane == 0) s_key[warp] = key;
-        __syncthreads();
-        key = lane < (nth >> 5) ? s_key[lane] : ~0ull;
-        key = warp_min64(key);
-        const int4 first = S.pts[S.slot[(int)(unsigned)(key & 0xFFFFFFFFu)]];
         int written = 0;
-        int4 cur = first;
-        bool closed = false;
-        for (int step = 0; step < kDtMaxStar; ++step) {
-            int4 best = make_int4(0, 0, 0, 0);
-            for (int j = tid; j < n; j += nth) {
-                const int4 q = S.pts[j];
-                if (q.w && q.z != p.z && q.z != cur.z && dt_orient(p.x, p.y, cur.x, cur.y, q.x, q.y) > 0)
-                    best = dt_better(best, q, p, cur, true);
-            }
-            best = dt_block_best(best, p, cur, true, s_red);
-            if (!best.w) break;
-            if (p.z < cur.z && p.z < best.z) {
-                if (tid == 0) {
-                    out[3 * written] = i;
-                    out[3 * written + 1] = cur.z;
-                    out[3 * written + 2] = best.z;
-                }
-                ++written;
-            }
-            if (best.z == first.z) {
-                closed = true;
-                break;
-            }
-            cur = best;
-        }
-        if (!closed) {
-            cur = first;
-            for (int step = 0; step < kDtMaxStar; ++step) {
-                int4 best = make_int4(0, 0, 0, 0);
-                for (int j = tid; j < n; j += nth) {
-                    const int4 q = S.pts[j];
-                    if (q.w && q.z != p.z && q.z != cur.z && dt_orient(p.x, p.y, cur.x, cur.y, q.x, q.y) < 0)
-                        best = dt_better(best, q, p, cur, false);
-                }
-                best = dt_block_best(best, p, cur, false, s_red);
-                if (!best.w) break;
-                if (p.z < cur.z && p.z < best.z) {
-                    if (tid == 0) {
-                        out[3 * written] = i;
-                        out[3 * written + 1] = best.z;
-                        out[3 * written + 2] = cur.z;
-                    }
-                    ++written;
-                }
-                cur = best;
-            }
-        }
+        dt_block_star(a, S, i, p, n, nullptr, 0, &written, S.tri + 3 * (size_t)S.offset[i], sh, false, nullptr,
+                      nullptr);
         __syncthreads();
     }
 }
@@ -574,7 +963,8 @@ size_t dt_side_bytes(int cap, int w, int h) {
     const size_t c = (size_t)(cap > 0 ? cap : 1);
     const size_t cells = (size_t)gw * gh + 1;
     return 2 * align_up(c * 4, 256) + align_up(c * 16, 256) + align_up(c * 4, 256) + 3 * align_up(cells * 4, 256) +
-           3 * align_up(c * 4, 256) + align_up(c * kDtSlots * 8, 256) + align_up(c * 4, 256) + align_up(16, 256);
+           3 * align_up(c * 4, 256) + align_up(c * kDtSlots * 8, 256) + 2 * align_up(c * 4, 256) +
+           2 * align_up((size_t)h * 4, 256) + align_up(16, 256);
 }
 
 static DtSide dt_carve(void *ws, int cap, int w, int h) {
@@ -601,9 +991,13 @@ static DtSide dt_carve(void *ws, int cap, int w, int h) {
     s.offset = reinterpret_cast<int32_t *>(take(c * 4));
     s.slots = reinterpret_cast<int32_t *>(take(c * kDtSlots * 8));
     s.pending = reinterpret_cast<int32_t *>(take(c * 4));
+    s.pending2 = reinterpret_cast<int32_t *>(take(c * 4));
+    s.rowmin = reinterpret_cast<int32_t *>(take((size_t)h * 4));
+    s.rowmax = reinterpret_cast<int32_t *>(take((size_t)h * 4));
     int32_t *small = reinterpret_cast<int32_t *>(take(16));
     s.err = small;
     s.npending = small + 1;
+    s.npending2 = small + 2;
     return s;
 }
 
@@ -627,7 +1021,9 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
         a.s[i].ntri = ntri[i];
         const size_t cells = (size_t)a.gw * a.gh + 1;
         if (cudaMemsetAsync(a.s[i].cell_cnt, 0, cells * 4, st) != cudaSuccess ||
-            cudaMemsetAsync(a.s[i].err, 0, 16, st) != cudaSuccess)
+            cudaMemsetAsync(a.s[i].err, 0, 16, st) != cudaSuccess ||
+            cudaMemsetAsync(a.s[i].rowmin, 0x7F, (size_t)h * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(a.s[i].rowmax, 0x80, (size_t)h * 4, st) != cudaSuccess)
             return launch_status("triangulation memsets");
     }
     const int tb = 256;
@@ -637,11 +1033,18 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     dt_cell_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_scatter_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_dedup_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
-    dt_pass1_kernel<<<dim3(wblocks, nsides), 32 * kDtWarps, 0, st>>>(a);
-    dt_pass2_kernel<<<dim3(152 * 4, nsides), 32 * kDtWarps, 0, st>>>(a);
+    const int gblocks = max(1, min((cap + kDtGroupThreads / kDtGroup - 1) / (kDtGroupThreads / kDtGroup), 152 * 8));
+    dt_pass1_kernel<<<dim3(gblocks, nsides), kDtGroupThreads, 0, st>>>(a);
+    const int smem2 = kDtCandCap2 * (int)sizeof(int4);
+    const int smem3 = smem2 + (2 * a.gh + 1) * (int)sizeof(int);
+    if (smem3 > 227 * 1024) return fail(ELAS_ERR_INVALID_ARG, "image too tall for the triangulation grid");
+    if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
+        return launch_status("dt_pass_block_kernel shared memory attribute");
+    (void)smem2;
+    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a, 4);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
-    dt_emit_big_kernel<<<dim3(152, nsides), 32 * kDtWarps, 0, st>>>(a);
+    dt_emit_big_kernel<<<dim3(152, nsides), 256, 0, st>>>(a);
     return launch_status("triangulation kernels");
 }
 
