@@ -292,11 +292,14 @@ elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, const elas_
                              elas_stream stream);
 
 /*
- * Pipeline handle: owns device buffers, pinned staging and host worker
- * threads for one image size, and runs the whole path per pair.
+ * Pipeline handle: owns device buffers, pinned staging and a host worker
+ * thread for one image size, and runs the whole path per pair, one launch
+ * per kernel for that pair (the plain per-pair path).
  * elas_pipeline_run: device images in, device maps out (dR, post may be
- * NULL); the stream is synchronised once in the middle (support list to the
- * host for triangulation) and the call returns with the rest enqueued.
+ * NULL); with triangulation on the GPU (the default) nothing in the step
+ * waits for the host and the call returns with everything enqueued; with
+ * host triangulation the stream is synchronised once in the middle (support
+ * list to the host).
  * elas_pipeline_run_host: host buffers in and out, copies included; returns
  * when the outputs are on the host.
  */
@@ -323,6 +326,57 @@ elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu);
 /* Counts of the last pair; waits for the pipeline's last stream. */
 elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st);
 void elas_pipeline_destroy(elas_pipeline *pl);
+
+/*
+ * Batch handle: many stereo pairs, of any mix of sizes and disparity
+ * ranges, run through the whole path together.  Each pair keeps its own
+ * resident state on the device (a "slot"); every kernel of the path is
+ * launched once for the whole batch, its grid covering the tiles of every
+ * pair (per-pair block ranges, so small and large pairs share one launch),
+ * and the triangulation's CTA pass takes its work from one queue over all
+ * pairs.  With use_graph the launch sequence is captured once into a CUDA
+ * graph and replayed.  Results are identical to the per-pair path.
+ *
+ * elas_batch_create: n pairs (1 <= n <= 256), pair i of w[i] x h[i] with
+ *   params[i] (w, h >= candidate_stepsize).  Allocates every slot.
+ * elas_batch_run: device pointers, arrays of n entries.  imgL/imgR [h][pitch]
+ *   uint8 (pitch NULL = widths); dL int16 [h][w] (required); dR NULL or
+ *   entries NULL = internal buffers; post NULL or entries NULL = no
+ *   post-processing for that pair.  Asynchronous on `stream`; the handle
+ *   must not be run on two streams at once.  Changing pointers between runs
+ *   costs one small table upload.
+ * elas_batch_run_host: host pointers (pinned for speed); copies in, runs,
+ *   copies out and returns when the outputs are on the host.
+ * elas_batch_stats: per-pair counts of the last run (waits for it).
+ * elas_batch_tune: times each tile-shape knob on the given inputs (device
+ *   pointers as in elas_batch_run, dL required) and keeps the fastest;
+ *   *chosen (may be NULL) receives the result.  Results are cached per
+ *   process by the batch's shape list.
+ */
+typedef struct elas_batch elas_batch;
+typedef struct {
+    int32_t desc_tile_rows;          /* descriptor tile height: 4, 8, 16      */
+    int32_t support_warps;           /* candidates per support CTA: 4, 8, 16  */
+    int32_t dense_threads_per_pixel; /* dense argmin threads per pixel: 1, 2, 4 */
+    int32_t use_graph;               /* capture and replay a CUDA graph       */
+} elas_batch_config;
+
+elas_status elas_batch_create(int32_t n, const int32_t *w, const int32_t *h, const elas_params *params,
+                              elas_batch **out);
+elas_status elas_batch_get_config(const elas_batch *b, elas_batch_config *cfg);
+elas_status elas_batch_set_config(elas_batch *b, const elas_batch_config *cfg);
+elas_status elas_batch_run(elas_batch *b, const uint8_t *const *imgL, const uint8_t *const *imgR,
+                           const int32_t *pitch, int16_t *const *dL, int16_t *const *dR, float *const *post,
+                           elas_stream stream);
+elas_status elas_batch_run_host(elas_batch *b, const uint8_t *const *imgL, const uint8_t *const *imgR,
+                                int16_t *const *dL, int16_t *const *dR, float *const *post, elas_stream stream);
+elas_status elas_batch_stats(elas_batch *b, int32_t *n_support, int32_t *n_tri_left, int32_t *n_tri_right);
+elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL, const uint8_t *const *imgR,
+                            const int32_t *pitch, int16_t *const *dL, elas_stream stream,
+                            elas_batch_config *chosen);
+/* Device bytes the batch holds (slots, tables and scratch). */
+size_t elas_batch_device_bytes(const elas_batch *b);
+void elas_batch_destroy(elas_batch *b);
 
 #ifdef __cplusplus
 }

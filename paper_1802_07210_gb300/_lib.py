@@ -50,6 +50,11 @@ class PipelineStats(C.Structure):
                 ("n_tri_right", C.c_int32), ("triangulate_ms", C.c_double)]
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("desc_tile_rows", C.c_int32), ("support_warps", C.c_int32),
+                ("dense_threads_per_pixel", C.c_int32), ("use_graph", C.c_int32)]
+
+
 _P, _I, _Z = C.c_void_p, C.c_int32, C.c_size_t
 
 # name -> (restype, argtypes), exactly the declarations of include/*.h
@@ -79,6 +84,15 @@ SIGNATURES = {
     "elas_pipeline_set_triangulation": (C.c_int, [_P, _I]),
     "elas_pipeline_stats_get": (C.c_int, [_P, _P]),
     "elas_pipeline_destroy": (None, [_P]),
+    "elas_batch_create": (C.c_int, [_I, _P, _P, _P, _P]),
+    "elas_batch_get_config": (C.c_int, [_P, _P]),
+    "elas_batch_set_config": (C.c_int, [_P, _P]),
+    "elas_batch_run": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "elas_batch_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "elas_batch_stats": (C.c_int, [_P, _P, _P, _P]),
+    "elas_batch_tune": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "elas_batch_device_bytes": (_Z, [_P]),
+    "elas_batch_destroy": (None, [_P]),
     "elas_probe_sad16": (C.c_int, [_I, _I, _I, _I, _P, _P]),
 }
 

@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import ElasError, Params, PipelineStats, as_params, check, lib, np_ptr, params  # noqa: F401
+from ._lib import BatchConfig, ElasError, Params, PipelineStats, as_params, check, lib, np_ptr, params  # noqa: F401
 
 
 def _stream(stream=None):
@@ -217,6 +217,116 @@ class Pipeline:
     def close(self):
         if self._h:
             lib().elas_pipeline_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(ptrs):
+    arr = (C.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+class Batch:
+    """Owner of an ``elas_batch`` handle: many pairs, any mix of sizes and
+    parameters, run together through batched launches (one launch per
+    kernel for the whole batch)."""
+
+    def __init__(self, shapes, prms):
+        """shapes: list of (w, h); prms: one parameter block (shared) or a
+        list with one per pair."""
+        n = len(shapes)
+        if not isinstance(prms, (list, tuple)):
+            prms = [prms] * n
+        if len(prms) != n:
+            raise ValueError("%d shapes but %d parameter blocks" % (n, len(prms)))
+        self.shapes = [(int(w), int(h)) for w, h in shapes]
+        self.prms = [as_params(p) for p in prms]
+        ws = (C.c_int32 * n)(*[w for w, _ in self.shapes])
+        hs = (C.c_int32 * n)(*[h for _, h in self.shapes])
+        parr = (Params * n)(*self.prms)
+        self._h = C.c_void_p()
+        check(lib().elas_batch_create(n, ws, hs, parr, C.byref(self._h)))
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def config(self):
+        cfg = BatchConfig()
+        check(lib().elas_batch_get_config(self._h, C.byref(cfg)))
+        return dict(desc_tile_rows=cfg.desc_tile_rows, support_warps=cfg.support_warps,
+                    dense_threads_per_pixel=cfg.dense_threads_per_pixel, use_graph=cfg.use_graph)
+
+    def set_config(self, **kw):
+        cur = self.config()
+        cur.update(kw)
+        cfg = BatchConfig(cur["desc_tile_rows"], cur["support_warps"], cur["dense_threads_per_pixel"],
+                          cur["use_graph"])
+        check(lib().elas_batch_set_config(self._h, C.byref(cfg)))
+
+    def _dev_arrays(self, imgL, imgR, dL, dR, post):
+        n = len(self)
+        if len(imgL) != n or len(imgR) != n or len(dL) != n:
+            raise ValueError("expected %d pairs" % n)
+        pl, pr, pd, pdr, pp = [], [], [], [], []
+        for i, (w, h) in enumerate(self.shapes):
+            pl.append(_dev(imgL[i], torch.uint8, "imgL[%d]" % i, (h, w)))
+            pr.append(_dev(imgR[i], torch.uint8, "imgR[%d]" % i, (h, w)))
+            pd.append(_dev(dL[i], torch.int16, "dL[%d]" % i, (h, w)))
+            pdr.append(None if dR is None or dR[i] is None else _dev(dR[i], torch.int16, "dR[%d]" % i, (h, w)))
+            pp.append(None if post is None or post[i] is None else _dev(post[i], torch.float32, "post[%d]" % i, (h, w)))
+        return _ptr_array(pl), _ptr_array(pr), _ptr_array(pd), _ptr_array(pdr), _ptr_array(pp)
+
+    def run(self, imgL, imgR, dL, dR=None, post=None, stream=None):
+        """Lists of device tensors (dR/post may be None or hold None)."""
+        aL, aR, aD, aDR, aP = self._dev_arrays(imgL, imgR, dL, dR, post)
+        check(lib().elas_batch_run(self._h, aL, aR, None, aD, aDR, aP, _stream(stream)))
+
+    def run_host(self, imgL, imgR, dL, dR=None, post=None, stream=None):
+        """Lists of host (ideally pinned) tensors; returns when done."""
+        def hp(t, dtype, name, shape):
+            if t is None:
+                return None
+            if t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise TypeError("%s must be a contiguous host %s tensor of shape %s" % (name, dtype, shape))
+            return C.c_void_p(t.data_ptr())
+        n = len(self)
+        pl, pr, pd, pdr, pp = [], [], [], [], []
+        for i, (w, h) in enumerate(self.shapes):
+            pl.append(hp(imgL[i], torch.uint8, "imgL[%d]" % i, (h, w)))
+            pr.append(hp(imgR[i], torch.uint8, "imgR[%d]" % i, (h, w)))
+            pd.append(hp(dL[i], torch.int16, "dL[%d]" % i, (h, w)))
+            pdr.append(None if dR is None else hp(dR[i], torch.int16, "dR[%d]" % i, (h, w)))
+            pp.append(None if post is None else hp(post[i], torch.float32, "post[%d]" % i, (h, w)))
+        assert len(pl) == n
+        check(lib().elas_batch_run_host(self._h, _ptr_array(pl), _ptr_array(pr), _ptr_array(pd), _ptr_array(pdr),
+                                        _ptr_array(pp), _stream(stream)))
+
+    def stats(self):
+        n = len(self)
+        a, b, c = (C.c_int32 * n)(), (C.c_int32 * n)(), (C.c_int32 * n)()
+        check(lib().elas_batch_stats(self._h, a, b, c))
+        return dict(n_support=list(a), n_tri_left=list(b), n_tri_right=list(c))
+
+    def tune(self, imgL, imgR, dL, stream=None):
+        aL, aR, aD, _, _ = self._dev_arrays(imgL, imgR, dL, None, None)
+        cfg = BatchConfig()
+        check(lib().elas_batch_tune(self._h, aL, aR, None, aD, _stream(stream), C.byref(cfg)))
+        return dict(desc_tile_rows=cfg.desc_tile_rows, support_warps=cfg.support_warps,
+                    dense_threads_per_pixel=cfg.dense_threads_per_pixel, use_graph=cfg.use_graph)
+
+    def device_bytes(self):
+        return int(lib().elas_batch_device_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            lib().elas_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -33,37 +33,6 @@ namespace elas {
 constexpr int kDtCell = 16;
 constexpr int kDtMaxStar = 4096;  // wrap steps per star
 
-struct DtSide {
-    int right;
-    int32_t *X, *Y;        // [cap] coordinates per list index
-    int4 *pts;             // [cap] (x, y, index, alive) sorted by grid cell
-    int32_t *slot;         // [cap] position of each point in pts
-    int32_t *cell_cnt;     // [ncell + 1]
-    int32_t *cell_start;   // [ncell + 1]
-    int32_t *cell_fill;    // [ncell + 1]
-    int32_t *status;       // [cap] 0 pending, k: star done in pass k, -1 duplicate
-    int32_t *owned;        // [cap] triangles owned (lowest-index vertex)
-    int32_t *offset;       // [cap] exclusive scan of owned
-    int32_t *slots;        // [cap][kDtSlots][2] owned triangles (the other two vertices)
-    int32_t *pending;      // [cap] points queued for pass 2
-    int32_t *npending;     // queue length
-    int32_t *pending2;     // [cap] points queued for pass 3
-    int32_t *npending2;
-    int32_t *rowmin, *rowmax;  // [h] extreme x of the points of each image row
-    int32_t *tri;          // output [cap_tri][3]
-    int32_t *ntri;         // output count
-    int32_t *err;          // bit 0: a star failed, bit 1: capacity, bit 2: slots overflowed
-};
-
-struct DtArgs {
-    const int16_t *list;
-    const int32_t *count;  // number of support points (device)
-    int cap;               // capacity in points
-    int cap_tri;
-    int w, h, gw, gh;
-    DtSide s[2];
-};
-
 __device__ __forceinline__ int dt_ncell(const DtArgs &a) { return a.gw * a.gh; }
 
 __device__ __forceinline__ int dt_cell(const DtArgs &a, int x, int y) {
@@ -107,10 +76,10 @@ __device__ __forceinline__ int dt_incircle(const int4 &P, const int4 &A, const i
 // Grid build
 // -------------------------------------------------------------------------
 
-__global__ void dt_points_kernel(DtArgs a) {
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+__device__ __forceinline__ void dt_points_body(const DtArgs &a, const VB &vb) {
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = vb.x * blockDim.x + threadIdx.x; i < n; i += vb.gx * blockDim.x) {
         const int u = a.list[3 * i], v = a.list[3 * i + 1], d = a.list[3 * i + 2];
         const int x = S.right ? u - d : u;
         S.X[i] = x;
@@ -125,11 +94,17 @@ __global__ void dt_points_kernel(DtArgs a) {
     }
 }
 
+__global__ void dt_points_kernel(DtArgs a) { dt_points_body(a, vb_single()); }
+__global__ void dt_points_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_points_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
 // One CTA per side: exclusive scan of the cell counts.
-__global__ void __launch_bounds__(1024) dt_cell_scan_kernel(DtArgs a) {
+__device__ __forceinline__ void dt_cell_scan_body(const DtArgs &a, const VB &vb) {
     __shared__ int s_w[32];
     __shared__ int s_carry;
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int ncell = dt_ncell(a);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) s_carry = 0;
@@ -164,10 +139,16 @@ __global__ void __launch_bounds__(1024) dt_cell_scan_kernel(DtArgs a) {
     }
 }
 
-__global__ void dt_scatter_kernel(DtArgs a) {
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+__global__ void __launch_bounds__(1024) dt_cell_scan_kernel(DtArgs a) { dt_cell_scan_body(a, vb_single()); }
+__global__ void __launch_bounds__(1024) dt_cell_scan_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_cell_scan_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+__device__ __forceinline__ void dt_scatter_body(const DtArgs &a, const VB &vb) {
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = vb.x * blockDim.x + threadIdx.x; i < n; i += vb.gx * blockDim.x) {
         const int x = S.X[i], y = S.Y[i];
         const int k = atomicAdd(S.cell_fill + dt_cell(a, x, y), 1);
         S.pts[k] = make_int4(x, y, i, 1);
@@ -175,11 +156,17 @@ __global__ void dt_scatter_kernel(DtArgs a) {
     }
 }
 
+__global__ void dt_scatter_kernel(DtArgs a) { dt_scatter_body(a, vb_single()); }
+__global__ void dt_scatter_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_scatter_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
 // Coincident points (right coordinates only) keep the lowest list index.
-__global__ void dt_dedup_kernel(DtArgs a) {
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+__device__ __forceinline__ void dt_dedup_body(const DtArgs &a, const VB &vb) {
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = vb.x * blockDim.x + threadIdx.x; i < n; i += vb.gx * blockDim.x) {
         const int x = S.X[i], y = S.Y[i];
         const int c = dt_cell(a, x, y);
         bool dup = false;
@@ -192,6 +179,12 @@ __global__ void dt_dedup_kernel(DtArgs a) {
             S.pts[S.slot[i]].w = 0;
         }
     }
+}
+
+__global__ void dt_dedup_kernel(DtArgs a) { dt_dedup_body(a, vb_single()); }
+__global__ void dt_dedup_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_dedup_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // -------------------------------------------------------------------------
@@ -374,16 +367,16 @@ __device__ __forceinline__ int4 dt_group_best(unsigned m, int4 best, DtKey<int> 
     return best;
 }
 
-__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel(DtArgs a) {
+__device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
     __shared__ int s_list[kDtGroupThreads / kDtGroup][kDtListCap];
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     const int lane = threadIdx.x & 31, gl = lane & (kDtGroup - 1), gbase = lane & ~(kDtGroup - 1);
     const unsigned gm = ((1u << kDtGroup) - 1u) << gbase;
     int *list = s_list[threadIdx.x / kDtGroup];
     const int R = kDtRadius;
-    const int groups = gridDim.x * (kDtGroupThreads / kDtGroup);
-    for (int j = blockIdx.x * (kDtGroupThreads / kDtGroup) + threadIdx.x / kDtGroup; j < n; j += groups) {
+    const int groups = vb.gx * (kDtGroupThreads / kDtGroup);
+    for (int j = vb.x * (kDtGroupThreads / kDtGroup) + threadIdx.x / kDtGroup; j < n; j += groups) {
         const int4 p = S.pts[j];
         if (!p.w || S.status[p.z] != 0) continue;
         // candidates: lanes fetch the cell rows' ranges, then stride over them
@@ -526,6 +519,12 @@ __global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel(DtArgs a) {
         }
         __syncwarp(gm);
     }
+}
+
+__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel(DtArgs a) { dt_pass1_body(a, vb_single()); }
+__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_pass1_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // Pass 2: one CTA per queued point.  The points within kDtRadius2 are cached
@@ -843,43 +842,106 @@ __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, 
     return sh.cnt;
 }
 
-// mode 2: cached steps only, a star that needs more is queued again; mode 3:
-// exact, over that second queue; mode 4: exact, over the first queue.
-__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a, int mode) {
-    extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows (mode 3)
+// One queued star rebuilt by the whole CTA (exact): cached steps among the
+// points within kDtRadius2, full scans restricted to the rows a step's
+// circle can reach otherwise.
+__device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, int i, int n, int4 *s_cand,
+                                              DtBlockShared &sh, int *r_start, int *r_pre) {
+    const int4 p = S.pts[S.slot[i]];
+    const int k = dt_block_gather(a, S, p, kDtRadius2, s_cand, sh);
+    int written = 0;
+    const int r = dt_block_star(a, S, i, p, n, s_cand, k, &written, nullptr, sh, false, r_start, r_pre);
+    if (threadIdx.x == 0) {
+        if (r == 1) {
+            S.status[i] = 2;
+            S.owned[i] = written;
+            if (written > kDtSlots) atomicOr(S.err, 4);
+        } else {
+            atomicOr(S.err, 1);
+        }
+    }
+    __syncthreads();
+}
+
+// One pair: the CTAs of side blockIdx.y stride over that side's queue.
+__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a) {
+    extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows
     __shared__ DtBlockShared sh;
-    int *r_start = mode >= 3 ? reinterpret_cast<int *>(s_cand + kDtCandCap2) : nullptr;
-    int *r_pre = mode >= 3 ? r_start + a.gh : nullptr;
+    int *r_start = reinterpret_cast<int *>(s_cand + kDtCandCap2);
+    int *r_pre = r_start + a.gh;
     const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int32_t *queue = mode == 3 ? S.pending2 : S.pending;
-    const int nq = mode == 3 ? *S.npending2 : *S.npending;
-    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) {
-        const int i = queue[q0];
-        const int4 p = S.pts[S.slot[i]];
-        const int k = dt_block_gather(a, S, p, kDtRadius2, s_cand, sh);
-        int written = 0;
-        const int r = dt_block_star(a, S, i, p, n, s_cand, k, &written, nullptr, sh, mode == 2, r_start, r_pre);
-        if (threadIdx.x == 0) {
-            if (r == 1) {
-                S.status[i] = 2;
-                S.owned[i] = written;
-                if (written > kDtSlots) atomicOr(S.err, 4);
-            } else if (r == 0) {
-                S.pending2[atomicAdd(S.npending2, 1)] = i;
-            } else {
-                atomicOr(S.err, 1);
-            }
+    const int nq = *S.npending;
+    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, S.pending[q0], n, s_cand, sh, r_start, r_pre);
+}
+
+// Many pairs, persistent: the queues of every (pair, side) of the launch are
+// concatenated in launch order and the CTAs take their entries one at a
+// time from one atomic counter (zeroed by dt_init_kernel_b), so the long
+// stars of one pair overlap the work of all the others.
+__global__ void __launch_bounds__(1024) dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides,
+                                                               int32_t *counter) {
+    extern __shared__ int4 s_cand[];
+    __shared__ DtBlockShared sh;
+    __shared__ int s_pre[2 * kMaxBatch + 1];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nq_all = vm.n * nsides;
+    // exclusive prefix of the queue lengths (warp 0; nq_all <= 2 * kMaxBatch)
+    if (tid < 32) {
+        constexpr int kPer = (2 * kMaxBatch + 31) / 32;
+        int v[kPer], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int q = lane * kPer + j;
+            v[j] = 0;
+            if (q < nq_all) v[j] = max(0, *slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides].npending);
+            sum += v[j];
         }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int q = lane * kPer + j;
+            if (q <= nq_all) s_pre[q] = run;
+            run += v[j];
+        }
+        if (lane == 31 && nq_all == 32 * kPer) s_pre[nq_all] = incl;
+    }
+    __syncthreads();
+    const int total = s_pre[nq_all];
+    int *r_start = reinterpret_cast<int *>(s_cand + kDtCandCap2);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        // last queue whose start is <= item
+        int lo = 0, hi = nq_all - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const DtArgs &a = slot_entry(tab, vm.stride, vm.slot[lo / nsides]);
+        const DtSide &S = a.s[lo % nsides];
+        const int n = min(max(*a.count, 0), a.cap);
+        dt_block_item(a, S, S.pending[item - s_pre[lo]], n, s_cand, sh, r_start, r_start + a.gh);
     }
 }
 
 // One CTA per side: exclusive scan of the owned counts, total = ntri.
-__global__ void __launch_bounds__(1024) dt_tri_scan_kernel(DtArgs a) {
+__device__ __forceinline__ void dt_tri_scan_body(const DtArgs &a, const VB &vb) {
     __shared__ int s_w[32];
     __shared__ int s_carry;
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) s_carry = 0;
@@ -914,12 +976,18 @@ __global__ void __launch_bounds__(1024) dt_tri_scan_kernel(DtArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(1024) dt_tri_scan_kernel(DtArgs a) { dt_tri_scan_body(a, vb_single()); }
+__global__ void __launch_bounds__(1024) dt_tri_scan_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_tri_scan_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
 // One thread per point: copy the owned triangles to their offset.
-__global__ void dt_emit_kernel(DtArgs a) {
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+__device__ __forceinline__ void dt_emit_body(const DtArgs &a, const VB &vb) {
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     if (*S.ntri < 0) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = vb.x * blockDim.x + threadIdx.x; i < n; i += vb.gx * blockDim.x) {
         const int m = min(S.owned[i], kDtSlots);
         int32_t *out = S.tri + 3 * (size_t)S.offset[i];
         const int32_t *sl = S.slots + (size_t)i * kDtSlots * 2;
@@ -931,14 +999,20 @@ __global__ void dt_emit_kernel(DtArgs a) {
     }
 }
 
+__global__ void dt_emit_kernel(DtArgs a) { dt_emit_body(a, vb_single()); }
+__global__ void dt_emit_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_emit_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
 // Points that own more than kDtSlots triangles (fan apexes): one CTA each
 // rebuilds its star over every point and writes the owned triangles in order.
-__global__ void __launch_bounds__(256) dt_emit_big_kernel(DtArgs a) {
+__device__ __forceinline__ void dt_emit_big_body(const DtArgs &a, const VB &vb) {
     __shared__ DtBlockShared sh;
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
+    const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     if (*S.ntri < 0 || !(*S.err & 4)) return;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int i = vb.x; i < n; i += vb.gx) {
         if (S.owned[i] <= kDtSlots) continue;
         const int4 p = S.pts[S.slot[i]];
         int written = 0;
@@ -946,6 +1020,12 @@ __global__ void __launch_bounds__(256) dt_emit_big_kernel(DtArgs a) {
                       nullptr);
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(256) dt_emit_big_kernel(DtArgs a) { dt_emit_big_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) dt_emit_big_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_emit_big_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // -------------------------------------------------------------------------
@@ -1041,11 +1121,107 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel shared memory attribute");
     (void)smem2;
-    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a, 4);
+    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_emit_big_kernel<<<dim3(152, nsides), 256, 0, st>>>(a);
     return launch_status("triangulation kernels");
+}
+
+// Batched launches keep no memsets: this kernel clears the counters and the
+// row extremes of every (pair, side), and the CTA pass's queue counter.
+__device__ __forceinline__ void dt_init_body(const DtArgs &a, const VB &vb, int32_t *counter) {
+    const DtSide &S = a.s[vb.y];
+    const int ncell1 = a.gw * a.gh + 1;
+    const int nall = ncell1 + 2 * a.h + 4;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    for (int k = vb.x * blockDim.x + threadIdx.x; k < nall; k += vb.gx * blockDim.x) {
+        if (k < ncell1)
+            S.cell_cnt[k] = 0;
+        else if (k < ncell1 + a.h)
+            S.rowmin[k - ncell1] = 0x7F7F7F7F;
+        else if (k < ncell1 + 2 * a.h)
+            S.rowmax[k - ncell1 - a.h] = (int32_t)0x80808080u;
+        else
+            S.err[k - ncell1 - 2 * a.h] = 0;  // err, npending, npending2 and one spare word
+    }
+}
+
+__global__ void __launch_bounds__(256) dt_init_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int32_t *counter) {
+    const VB vb = vb_batch(vm);
+    dt_init_body(slot_entry(tab, vm.stride, vb.slot), vb, counter);
+}
+
+static int dt_point_blocks(int cap, int threads, int npairs) {
+    // grid-stride kernels: about a third of the capacity per sweep in a
+    // batch (the support list holds a fraction of the lattice), capped
+    const int full = (cap + threads - 1) / threads;
+    if (npairs <= 1) return max(1, min(full, 152 * 8));
+    return max(1, min((full + 2) / 3, 152 * 8));
+}
+
+elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VMap &pairs, int nsides,
+                                 int32_t *counter, cudaStream_t st) {
+    if (pairs.n == 0) return ELAS_OK;
+    if (nsides < 1 || nsides > 2) return fail(ELAS_ERR_INVALID_ARG, "nsides %d", nsides);
+    VMap m_init, m_pts, m_scan, m_grp, m_big;
+    vmap_clear(m_init, pairs.stride);
+    vmap_clear(m_pts, pairs.stride);
+    vmap_clear(m_scan, pairs.stride);
+    vmap_clear(m_grp, pairs.stride);
+    vmap_clear(m_big, pairs.stride);
+    int max_gh = 1;
+    for (int i = 0; i < pairs.n; ++i) {
+        const int slot = pairs.slot[i];
+        const DtArgs &a = slot_entry(host, pairs.stride, slot);
+        const int nall = a.gw * a.gh + 1 + 2 * a.h + 4;
+        vmap_add(m_init, slot, dim3((nall + 255) / 256, nsides));
+        vmap_add(m_pts, slot, dim3(dt_point_blocks(a.cap, 256, pairs.n), nsides));
+        vmap_add(m_scan, slot, dim3(1, nsides));
+        const int gthreads = kDtGroupThreads / kDtGroup;
+        vmap_add(m_grp, slot, dim3(dt_point_blocks(a.cap, gthreads, pairs.n), nsides));
+        vmap_add(m_big, slot, dim3(64, nsides));
+        max_gh = max(max_gh, a.gh);
+    }
+    const int smem3 = kDtCandCap2 * (int)sizeof(int4) + (2 * max_gh + 1) * (int)sizeof(int);
+    if (smem3 > 200 * 1024) return fail(ELAS_ERR_INVALID_ARG, "image too tall for the triangulation grid");
+    if (cudaFuncSetAttribute(dt_pass_block_kernel_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
+        return launch_status("dt_pass_block_kernel_b shared memory attribute");
+    dt_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(tab, m_init, counter);
+    dt_points_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
+    dt_cell_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
+    dt_scatter_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
+    dt_dedup_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
+    dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    dt_pass_block_kernel_b<<<nsm * 4, 256, smem3, st>>>(tab, pairs, nsides, counter);
+    dt_tri_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
+    dt_emit_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
+    dt_emit_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(tab, m_big);
+    return launch_status("batched triangulation kernels");
+}
+
+// Argument block of one pair's triangulation (both sides), for the tables
+// of batched launches.
+DtArgs triangulate_args(const int16_t *list, const int32_t *count, int cap, int w, int h, int32_t *const *tri,
+                        int32_t *const *ntri, int cap_tri, void *ws) {
+    DtArgs a{};
+    a.list = list;
+    a.count = count;
+    a.cap = cap;
+    a.cap_tri = cap_tri;
+    a.w = w;
+    a.h = h;
+    dt_geom(w, h, a.gw, a.gh);
+    const size_t side_bytes = dt_side_bytes(cap, w, h);
+    for (int i = 0; i < 2; ++i) {
+        a.s[i] = dt_carve(reinterpret_cast<char *>(ws) + i * side_bytes, cap, w, h);
+        a.s[i].right = i;
+        a.s[i].tri = tri[i];
+        a.s[i].ntri = ntri[i];
+    }
+    return a;
 }
 
 size_t triangulate_device_workspace(int cap, int w, int h, int nsides) { return nsides * dt_side_bytes(cap, w, h); }

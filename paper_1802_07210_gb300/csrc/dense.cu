@@ -57,24 +57,11 @@ __device__ __forceinline__ void edge_span(int px, int py, int qx, int qy, int ow
         hi = lo - 1;
 }
 
-struct RasterSide {
-    const int32_t *tri;
-    int ntri, right;            // ntri: used when ntri_dev is NULL
-    int16_t *dplane;
-    const int32_t *ntri_dev;    // device triangle count (negative = none)
-};
 
 __device__ __forceinline__ int side_ntri(const RasterSide &S) {
     return S.ntri_dev ? max(0, *S.ntri_dev) : S.ntri;
 }
 
-struct RasterArgs {
-    const int16_t *list;
-    RasterSide s[2];
-    int32_t *big;     // (side << 30) | triangle, for triangles left to plane_raster_big_kernel
-    int32_t *nbig;    // count of big (zeroed before the launch)
-    int w, h, dmin, dmax;
-};
 
 constexpr int kBigArea = 1024;  // bounding-box pixels above which a triangle is "big"
 
@@ -154,13 +141,13 @@ __device__ __forceinline__ void raster_row(const TriGeom &g, int y, int first, i
     }
 }
 
-__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
-    const int side = blockIdx.y;
+__device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb) {
+    const int side = vb.y;
     const RasterSide S = side ? a.s[1] : a.s[0];
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int ntri = side_ntri(S);
-    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntri; t += gridDim.x * wpb) {
+    for (int t = vb.x * wpb + (threadIdx.x >> 5); t < ntri; t += vb.gx * wpb) {
         const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
         if (g.empty) continue;
         const int rows = g.ymax - g.ymin + 1;
@@ -172,12 +159,18 @@ __global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) { plane_raster_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    plane_raster_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
 // Big triangles, one CTA each (grid-stride over the list): the CTA's warps
 // take the rows in turn and their lanes stride across x.
-__global__ void __launch_bounds__(256) plane_raster_big_kernel(RasterArgs a) {
+__device__ __forceinline__ void plane_raster_big_body(const RasterArgs &a, const VB &vb) {
     const int n = *a.nbig;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    for (int k = vb.x; k < n; k += vb.gx) {
         const int e = a.big[k];
         const int side = e >> 30, t = e & ((1 << 30) - 1);
         const RasterSide S = side ? a.s[1] : a.s[0];
@@ -187,43 +180,48 @@ __global__ void __launch_bounds__(256) plane_raster_big_kernel(RasterArgs a) {
     }
 }
 
-struct CellSide {
-    const uint4 *ref, *oth;
-    const uint32_t *grid;   // [gh][gw][nw]
-    const int16_t *dplane;  // prior map (may be NULL with full range)
-    int16_t *out;
-    int dir;
-};
+__global__ void __launch_bounds__(256) plane_raster_big_kernel(RasterArgs a) { plane_raster_big_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) plane_raster_big_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    plane_raster_big_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 
-struct CellArgs {
-    CellSide s[2];
-    int w, h, G, gw, nw, dmin, dmax, sradius, match_texture, full, prior_off;
-    int P[kMaxSradius + 1];
-};
 
-__global__ void __launch_bounds__(512) cell_kernel(CellArgs a) {
-    __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + 4];
+
+constexpr int kListPad = 16;  // the candidate list is padded to a multiple of this
+
+// TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
+// every TPP-th candidate of its list and of its plane window and merge their
+// keys with shuffles (min is order free, so every TPP gives the same result).
+template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
+    __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + kListPad];
     __shared__ int s_P[kMaxSradius + 1];
     __shared__ int s_nlist;
 
-    const CellSide S = blockIdx.z ? a.s[1] : a.s[0];
-    const int cx = blockIdx.x, cy = blockIdx.y;
-    const int x0 = cx * a.G, y0 = cy * a.G;
-    const int cw = min(a.G, a.w - x0), ch = min(a.G, a.h - y0);
+    const CellSide &S = a.s[vb.z];
+    const int W = a.w, H = a.h, G = a.G;
+    const int dmin = a.dmin, dmax = a.dmax, sradius = a.sradius, full = a.full;
+    const int cx = vb.x, cy = vb.y;
+    const int x0 = cx * G, y0 = cy * G;
+    const int cw = min(G, W - x0), ch = min(G, H - y0);
     const int npx = cw * ch;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cell = cy * a.gw + cx;
+    const uint4 *__restrict__ ref = S.ref;
+    const uint4 *__restrict__ oth = S.oth;
+    const int dir = S.dir;
 
     // ---- candidate list of the cell, ascending ---------------------------------
     if (tid <= kMaxSradius) s_P[tid] = a.P[tid];
-    if (!a.full && warp == 0) {
-        const uint32_t *g = S.grid + (size_t)cell * a.nw;
+    if (!full && warp == 0) {
+        const int nw = a.nw;
+        const uint32_t *g = S.grid + (size_t)cell * nw;
         int base = 0;
-        for (int w0 = 0; w0 < a.nw; w0 += 32) {
+        for (int w0 = 0; w0 < nw; w0 += 32) {
             const int wi = w0 + lane;
-            uint32_t m = wi < a.nw ? __ldg(g + wi) : 0u;
+            uint32_t m = wi < nw ? __ldg(g + wi) : 0u;
             // keep the bits inside [dmin, dmax]
-            const int lo = a.dmin - 32 * wi, hi = a.dmax - 32 * wi;
+            const int lo = dmin - 32 * wi, hi = dmax - 32 * wi;
             if (lo > 0) m &= lo >= 32 ? 0u : (0xFFFFFFFFu << lo);
             if (hi < 31) m &= hi < 0 ? 0u : (0xFFFFFFFFu >> (31 - hi));
             const int c = __popc(m);
@@ -240,54 +238,75 @@ __global__ void __launch_bounds__(512) cell_kernel(CellArgs a) {
             }
             base += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
-        // pad to a multiple of 4 with a disparity above every dmax
-        if (lane < 4) s_list[base + lane] = (uint16_t)2047;
+        // pad with a disparity above every dmax
+        if (lane < kListPad) s_list[base + lane] = (uint16_t)2047;
         if (lane == 0) s_nlist = base;
     }
     __syncthreads();
-    const int nlist4 = a.full ? 0 : (s_nlist + 3) & ~3;
+    constexpr int kStep = 4 * TPP;  // list entries per unrolled round of a pixel group
+    const int nlist = full ? 0 : (s_nlist + kStep - 1) / kStep * kStep;
+    const int sub = TPP > 1 ? (tid & (TPP - 1)) : 0;
 
     // ---- per-pixel argmin -------------------------------------------------------
-    for (int p = tid; p < npx; p += blockDim.x) {
-        const int x = x0 + p % cw, y = y0 + p / cw;
-        const size_t row = (size_t)y * a.w;
-        int res = -1;
-        if (x >= 2 && x <= a.w - 3 && y >= 2 && y <= a.h - 3) {
-            const uint4 r = __ldg(S.ref + row + x);
-            const int dp = a.full ? -1 : (int)__ldg(S.dplane + row + x);
-            if ((int)texture16(r) >= a.match_texture && (a.full || dp >= 0)) {
-                // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
-                // (the lower bound of the first condition is <= 0; the list's
-                // padding value 2047 exceeds every dmax)
-                const int dlim = min(a.dmax, S.dir < 0 ? x - 2 : a.w - 3 - x);
-                const uint4 *orow = S.oth + row + x;
-                int best = 0x7FFFFFFF;
-                if (a.full) {
-                    for (int d = a.dmin; d <= dlim; ++d) {  // no plane, so no prior term
-                        const int c = (int)sad16(r, __ldg(orow + S.dir * d));
-                        best = min(best, ((c + kKeyBias) << 11) | d);
-                    }
-                } else {
+    const int ppb = blockDim.x / TPP;  // pixels per pass of the CTA
+    for (int pb = 0; pb < npx; pb += ppb) {
+        const int p = pb + tid / TPP;
+        int best = 0x7FFFFFFF;
+        bool live = false;
+        size_t row = 0;
+        int x = 0;
+        if (p < npx) {
+            x = x0 + p % cw;
+            const int y = y0 + p / cw;
+            row = (size_t)y * W;
+            live = true;
+            if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
+                const uint4 r = __ldg(ref + row + x);
+                const int dp = full ? -1 : (int)__ldg(S.dplane + row + x);
+                if ((int)texture16(r) >= a.match_texture && (full || dp >= 0)) {
+                    // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
+                    // (the lower bound of the first condition is <= 0; the list's
+                    // padding value 2047 exceeds every dmax)
+                    const int dlim = min(dmax, dir < 0 ? x - 2 : W - 3 - x);
+                    const uint4 *orow = oth + row + x;
+                    if (full) {
+                        for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
+                            const int c = (int)sad16(r, __ldg(orow + dir * d));
+                            best = min(best, ((c + kKeyBias) << 11) | d);
+                        }
+                    } else {
 #pragma unroll 4
-                    for (int k = 0; k < nlist4; ++k) {
-                        const int d = s_list[k];
-                        if (d <= dlim) {
-                            const int c = (int)sad16(r, __ldg(orow + S.dir * d));
+                        for (int k = sub; k < nlist; k += TPP) {
+                            const int d = s_list[k];
+                            if (d <= dlim) {
+                                const int c = (int)sad16(r, __ldg(orow + dir * d));
+                                best = min(best, ((c + kKeyBias) << 11) | d);
+                            }
+                        }
+                        const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
+                        for (int d = lo + sub; d <= hi; d += TPP) {
+                            int c = (int)sad16(r, __ldg(orow + dir * d));
+                            if (!a.prior_off) c += s_P[abs(d - dp)];
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     }
-                    const int lo = max(a.dmin, dp - a.sradius), hi = min(dlim, dp + a.sradius);
-                    for (int d = lo; d <= hi; ++d) {
-                        int c = (int)sad16(r, __ldg(orow + S.dir * d));
-                        if (!a.prior_off) c += s_P[abs(d - dp)];
-                        best = min(best, ((c + kKeyBias) << 11) | d);
-                    }
                 }
-                if (best != 0x7FFFFFFF) res = best & 2047;
             }
         }
-        S.out[row + x] = (int16_t)res;
+        if (TPP > 1) {
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+        }
+        if (live && sub == 0) S.out[row + x] = (int16_t)(best != 0x7FFFFFFF ? (best & 2047) : -1);
     }
+}
+
+__global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) { cell_body<1>(a, vb_single()); }
+
+template <int TPP>
+__global__ void __launch_bounds__(1024) cell_kernel_b(const CellArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    cell_body<TPP>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,31 +331,58 @@ size_t raster_scratch_bytes(int ntri_total) {
     return align_up(sizeof(int32_t) * 4, 256) + align_up(sizeof(int32_t) * (size_t)(ntri_total > 0 ? ntri_total : 1), 256);
 }
 
-// Prior maps of one or two meshes.  With two, the maps must be contiguous
-// (dplane1 == dplane0 + w*h) so that one memset clears both.
-static elas_status raster_meshes(const int16_t *list, const RasterSide *sides, int nsides, int w, int h,
-                                 const elas_params *p, void *scratch, cudaStream_t st) {
-    const size_t bytes = (size_t)w * h * sizeof(int16_t) * nsides;
-    if (cudaMemsetAsync(sides[0].dplane, 0xFF, bytes, st) != cudaSuccess) return launch_status("memset d_plane");
+// Batched launches keep no memsets: this kernel fills the prior maps of a
+// pair (both sides, contiguous) with -1 and clears its big-triangle count.
+__device__ __forceinline__ void raster_init_body(const RasterArgs &a, const VB &vb) {
+    const size_t n = (size_t)a.nsides * a.w * a.h;  // int16 entries
+    int16_t *d = a.s[0].dplane;
+    const size_t n8 = n / 8;
+    uint4 *d8 = reinterpret_cast<uint4 *>(d);
+    const size_t stride = (size_t)vb.gx * blockDim.x;
+    const size_t t = (size_t)vb.x * blockDim.x + threadIdx.x;
+    for (size_t i = t; i < n8; i += stride) d8[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    if (t < n - 8 * n8) d[8 * n8 + t] = -1;
+    if (t == 0) *a.nbig = 0;
+}
+
+__global__ void __launch_bounds__(256) raster_init_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    raster_init_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+static RasterArgs raster_args(const int16_t *list, const RasterSide *sides, int nsides, int w, int h,
+                              const elas_params *p, void *scratch) {
     RasterArgs a{};
     a.list = list;
+    a.nsides = nsides;
     a.nbig = reinterpret_cast<int32_t *>(scratch);
     a.big = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scratch) + align_up(sizeof(int32_t) * 4, 256));
     a.w = w;
     a.h = h;
     a.dmin = p->disp_min;
     a.dmax = p->disp_max;
+    for (int i = 0; i < nsides; ++i) a.s[i] = sides[i];
+    return a;
+}
+
+static int raster_max_ntri(const RasterArgs &a) {
     int maxt = 0;
-    for (int i = 0; i < nsides; ++i) {
-        a.s[i] = sides[i];
-        maxt = max(maxt, sides[i].ntri);
-    }
+    for (int i = 0; i < a.nsides; ++i) maxt = max(maxt, a.s[i].ntri);
+    return maxt;
+}
+
+// Prior maps of one or two meshes.  With two, the maps must be contiguous
+// (dplane1 == dplane0 + w*h) so that one memset clears both.
+static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
+    const size_t bytes = (size_t)a.w * a.h * sizeof(int16_t) * a.nsides;
+    if (cudaMemsetAsync(a.s[0].dplane, 0xFF, bytes, st) != cudaSuccess) return launch_status("memset d_plane");
+    const int maxt = raster_max_ntri(a);
     if (maxt == 0) return ELAS_OK;
     if (cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) return launch_status("memset big count");
     const int wpb = 8;
     int blocks = (maxt + wpb - 1) / wpb;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    plane_raster_kernel<<<dim3(blocks, nsides), 32 * wpb, 0, st>>>(a);
+    plane_raster_kernel<<<dim3(blocks, a.nsides), 32 * wpb, 0, st>>>(a);
     elas_status s = launch_status("plane_raster_kernel");
     if (s != ELAS_OK) return s;
     plane_raster_big_kernel<<<2 * 152, 256, 0, st>>>(a);
@@ -361,18 +407,25 @@ static CellArgs cell_args(int w, int h, const elas_params *p, const int *P) {
     return a;
 }
 
-static elas_status launch_cells(const CellArgs &a, int nsides, int w, int h, const elas_params *p, cudaStream_t st) {
-    const GridGeom g = grid_geom(w, h, p);
-    // one warp per 32 pixels of the cell, at most 16 warps
-    const int warps = min(16, max(1, (p->grid_size * p->grid_size + 31) / 32));
-    cell_kernel<<<dim3(g.gw, g.gh, nsides), 32 * warps, 0, st>>>(a);
+// Threads of a cell CTA: TPP per pixel of a G x G cell, at most 1024.
+int cell_threads(int G, int tpp) {
+    const int t = (G * G * tpp + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
+dim3 cell_grid(const CellArgs &a, int nsides) {
+    return dim3((a.w + a.G - 1) / a.G, (a.h + a.G - 1) / a.G, nsides);
+}
+
+static elas_status launch_cells(const CellArgs &a, int nsides, cudaStream_t st) {
+    cell_kernel<<<cell_grid(a, nsides), cell_threads(a.G, 1), 0, st>>>(a);
     return launch_status("cell_kernel");
 }
 
 elas_status launch_plane_prior(const int16_t *list, const int32_t *tri, int ntri, int right, int w, int h,
                                const elas_params *p, int16_t *dplane, void *scratch, cudaStream_t st) {
     RasterSide side{tri, ntri, right ? 1 : 0, dplane, nullptr};
-    return raster_meshes(list, &side, 1, w, h, p, scratch, st);
+    return raster_meshes(raster_args(list, &side, 1, w, h, p, scratch), st);
 }
 
 elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
@@ -388,29 +441,29 @@ elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int 
     cs.dplane = dplane;
     cs.out = out;
     cs.dir = right ? +1 : -1;
-    return launch_cells(a, 1, w, h, p, st);
+    return launch_cells(a, 1, st);
 }
 
 size_t dense_workspace(int w, int h, const elas_params *p) {
     return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(2 * max_triangles(w, h, p));
 }
 
-elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
-                              const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
-                              const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
-                              cudaStream_t st, const int32_t *ntri_dev) {
+elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                       const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
+                       const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
+                       const int32_t *ntri_dev, DenseStage *o) {
     int16_t *dpL = reinterpret_cast<int16_t *>(ws);
     int16_t *dpR = dpL + (size_t)w * h;
     const RasterSide sides[2] = {{triL, ntriL, 0, dpL, ntri_dev ? ntri_dev : nullptr},
                                  {triR, ntriR, 1, dpR, ntri_dev ? ntri_dev + 1 : nullptr}};
     void *scratch = reinterpret_cast<char *>(ws) + align_up(2 * (size_t)w * h * sizeof(int16_t), 256);
-    elas_status s = raster_meshes(list, sides, 2, w, h, p, scratch, st);
-    if (s != ELAS_OK) return s;
+    o->raster = raster_args(list, sides, 2, w, h, p, scratch);
     int P[kMaxSradius + 1];
-    if ((s = fill_prior_table(p, P)) != ELAS_OK) return s;
-    CellArgs a = cell_args(w, h, p, P);
+    elas_status s = fill_prior_table(p, P);
+    if (s != ELAS_OK) return s;
+    o->cell = cell_args(w, h, p, P);
     for (int i = 0; i < 2; ++i) {
-        CellSide &cs = a.s[i];
+        CellSide &cs = o->cell.s[i];
         cs.ref = reinterpret_cast<const uint4 *>(i ? descR : descL);
         cs.oth = reinterpret_cast<const uint4 *>(i ? descL : descR);
         cs.grid = i ? gridR : gridL;
@@ -418,7 +471,61 @@ elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w,
         cs.out = i ? dR : dL;
         cs.dir = i ? +1 : -1;
     }
-    return launch_cells(a, 2, w, h, p, st);
+    return ELAS_OK;
+}
+
+elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                              const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
+                              const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
+                              cudaStream_t st, const int32_t *ntri_dev) {
+    DenseStage d;
+    elas_status s = dense_args(descL, descR, w, h, p, list, triL, ntriL, triR, ntriR, gridL, gridR, dL, dR, ws,
+                               ntri_dev, &d);
+    if (s != ELAS_OK) return s;
+    if ((s = raster_meshes(d.raster, st)) != ELAS_OK) return s;
+    return launch_cells(d.cell, 2, st);
+}
+
+// Batched plane prior and dense matching over the pairs of `pairs`; host
+// is the host copy of the table.
+elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp,
+                           cudaStream_t st) {
+    if (pairs.n == 0) return ELAS_OK;
+    if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
+    VMap m_init, m_tri, m_big, m_cell;
+    vmap_clear(m_init, pairs.stride);
+    vmap_clear(m_tri, pairs.stride);
+    vmap_clear(m_big, pairs.stride);
+    vmap_clear(m_cell, pairs.stride);
+    int threads = 32;
+    for (int i = 0; i < pairs.n; ++i) {
+        const int slot = pairs.slot[i];
+        const DenseStage &d = slot_entry(host, pairs.stride, slot);
+        const size_t n8 = ((size_t)d.raster.nsides * d.raster.w * d.raster.h + 7) / 8;
+        vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)152 * 4)));
+        const int maxt = raster_max_ntri(d.raster);
+        const int wpb = 8;
+        int blocks = (maxt + wpb - 1) / wpb;
+        if (pairs.n > 1) blocks = (blocks + 2) / 3;
+        blocks = max(1, min(blocks, 152 * 16));
+        vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
+        vmap_add(m_big, slot, dim3(32));
+        vmap_add(m_cell, slot, cell_grid(d.cell, 2));
+        threads = max(threads, cell_threads(d.cell.G, tpp));
+    }
+    raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
+    plane_raster_kernel_b<<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri);
+    plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
+    elas_status s = launch_status("batched plane prior");
+    if (s != ELAS_OK) return s;
+    const int total = vmap_total(m_cell);
+    if (tpp == 1)
+        cell_kernel_b<1><<<total, threads, 0, st>>>(t.cell, m_cell);
+    else if (tpp == 2)
+        cell_kernel_b<2><<<total, threads, 0, st>>>(t.cell, m_cell);
+    else
+        cell_kernel_b<4><<<total, threads, 0, st>>>(t.cell, m_cell);
+    return launch_status("cell_kernel_b");
 }
 
 }  // namespace elas

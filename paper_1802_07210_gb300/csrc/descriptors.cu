@@ -1,38 +1,39 @@
 // Descriptors: Sobel gradient images quantised to uint8 and sampled into a
 // 16-byte descriptor per pixel (Sec. III.A, Fig. 1(b-d); Sec. VI.A).
 //
-// One CTA produces a 32x8 tile of descriptors.  The image tile with a 3-pixel
-// halo is staged in shared memory, the quantised du/dv planes of the tile
-// with a 2-pixel halo are computed once into shared memory, and every thread
-// assembles its pixel's 16 bytes and writes them as one 16-byte store
-// (a warp writes 512 contiguous bytes).
+// One CTA produces a 32xTH tile of descriptors (TH = 8 for the one-pair
+// launch; 4, 8 or 16 in batched launches, chosen by the tuner).  The image
+// tile with a 3-pixel halo is staged in shared memory, the quantised du/dv
+// planes of the tile with a 2-pixel halo are computed once into shared
+// memory, and every thread assembles its pixel's 16 bytes and writes them as
+// one 16-byte store (a warp writes 512 contiguous bytes).
 #include "launch.cuh"
 
 namespace elas {
 
 constexpr int kDescTW = 32;
-constexpr int kDescTH = 8;
 
 __device__ __forceinline__ int quantise(int s) {
     int q = 128 + s / 4;  // truncation toward zero
     return q < 1 ? 1 : (q > 255 ? 255 : q);
 }
 
-__global__ void __launch_bounds__(kDescTW *kDescTH)
-descriptor_kernel(const uint8_t *__restrict__ imgL, const uint8_t *__restrict__ imgR, int w, int h,
-                  int pitch, uint4 *__restrict__ descL, uint4 *__restrict__ descR) {
-    const uint8_t *img = blockIdx.z ? imgR : imgL;
-    uint4 *desc = blockIdx.z ? descR : descL;
+// TH = tile height (image rows per CTA): one of 4, 8, 16.
+template <int TH>
+__device__ __forceinline__ void descriptor_body(const DescArgs &a, const VB &vb) {
+    const uint8_t *img = vb.z ? a.imgR : a.imgL;
+    uint4 *desc = vb.z ? a.descR : a.descL;
+    const int w = a.w, h = a.h, pitch = a.pitch;
 
-    constexpr int IW = kDescTW + 6, IH = kDescTH + 6;  // image tile with halo 3
-    constexpr int QW = kDescTW + 4, QH = kDescTH + 4;  // gradient tile with halo 2
+    constexpr int IW = kDescTW + 6, IH = TH + 6;  // image tile with halo 3
+    constexpr int QW = kDescTW + 4, QH = TH + 4;  // gradient tile with halo 2
     __shared__ int16_t s_img[IH][IW];
     __shared__ uint8_t s_du[QH][QW];
     __shared__ uint8_t s_dv[QH][QW];
 
-    const int x0 = blockIdx.x * kDescTW, y0 = blockIdx.y * kDescTH;
+    const int x0 = vb.x * kDescTW, y0 = vb.y * TH;
     const int tid = threadIdx.y * kDescTW + threadIdx.x;
-    constexpr int NT = kDescTW * kDescTH;
+    constexpr int NT = kDescTW * TH;
 
     for (int i = tid; i < IW * IH; i += NT) {
         const int ix = i % IW, iy = i / IW;
@@ -49,11 +50,11 @@ descriptor_kernel(const uint8_t *__restrict__ imgL, const uint8_t *__restrict__ 
         int qdu = 128, qdv = 128;
         if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
             const int ix = qx + 1, iy = qy + 1;  // image-tile coordinates of (x, y)
-            const int a = s_img[iy - 1][ix - 1], b = s_img[iy - 1][ix], c = s_img[iy - 1][ix + 1];
+            const int a0 = s_img[iy - 1][ix - 1], b = s_img[iy - 1][ix], c = s_img[iy - 1][ix + 1];
             const int d = s_img[iy][ix - 1], f = s_img[iy][ix + 1];
             const int g = s_img[iy + 1][ix - 1], hh = s_img[iy + 1][ix], k = s_img[iy + 1][ix + 1];
-            const int gx = (c + 2 * f + k) - (a + 2 * d + g);
-            const int gy = (g + 2 * hh + k) - (a + 2 * b + c);
+            const int gx = (c + 2 * f + k) - (a0 + 2 * d + g);
+            const int gy = (g + 2 * hh + k) - (a0 + 2 * b + c);
             qdu = quantise(gx);
             qdv = quantise(gy);
         }
@@ -77,13 +78,48 @@ descriptor_kernel(const uint8_t *__restrict__ imgL, const uint8_t *__restrict__ 
     desc[(size_t)y * w + x] = o;
 }
 
+template <int TH> __global__ void __launch_bounds__(kDescTW *TH) descriptor_kernel(DescArgs a) {
+    descriptor_body<TH>(a, vb_single());
+}
+
+template <int TH>
+__global__ void __launch_bounds__(kDescTW *TH) descriptor_kernel_b(const DescArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    descriptor_body<TH>(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+dim3 descriptor_grid(int w, int h, int two, int tile_rows) {
+    return dim3((w + kDescTW - 1) / kDescTW, (h + tile_rows - 1) / tile_rows, two ? 2 : 1);
+}
+
+static bool valid_tile_rows(int th) { return th == 4 || th == 8 || th == 16; }
+
 elas_status launch_descriptors(const uint8_t *imgL, const uint8_t *imgR, int w, int h, int pitch,
                                uint8_t *descL, uint8_t *descR, cudaStream_t st) {
-    dim3 block(kDescTW, kDescTH, 1);
-    dim3 grid((w + kDescTW - 1) / kDescTW, (h + kDescTH - 1) / kDescTH, imgR ? 2 : 1);
-    descriptor_kernel<<<grid, block, 0, st>>>(imgL, imgR, w, h, pitch, reinterpret_cast<uint4 *>(descL),
-                                              reinterpret_cast<uint4 *>(descR));
+    DescArgs a{imgL, imgR, w, h, pitch, reinterpret_cast<uint4 *>(descL), reinterpret_cast<uint4 *>(descR)};
+    descriptor_kernel<8><<<descriptor_grid(w, h, imgR != nullptr, 8), dim3(kDescTW, 8), 0, st>>>(a);
     return launch_status("descriptor_kernel");
+}
+
+elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, const VMap &pairs, int tile_rows,
+                                 cudaStream_t st) {
+    if (!valid_tile_rows(tile_rows)) return fail(ELAS_ERR_INVALID_ARG, "descriptor tile rows %d", tile_rows);
+    VMap m;
+    vmap_clear(m, pairs.stride);
+    for (int i = 0; i < pairs.n; ++i) {
+        const DescArgs &d = slot_entry(host, pairs.stride, pairs.slot[i]);
+        vmap_add(m, pairs.slot[i], descriptor_grid(d.w, d.h, d.imgR != nullptr, tile_rows));
+    }
+    const int total = vmap_total(m);
+    if (total == 0) return ELAS_OK;
+    const dim3 block(kDescTW, tile_rows);
+    if (tile_rows == 4)
+        descriptor_kernel_b<4><<<total, block, 0, st>>>(tab, m);
+    else if (tile_rows == 8)
+        descriptor_kernel_b<8><<<total, block, 0, st>>>(tab, m);
+    else
+        descriptor_kernel_b<16><<<total, block, 0, st>>>(tab, m);
+    return launch_status("descriptor_kernel_b");
 }
 
 }  // namespace elas

@@ -3,21 +3,24 @@
 // lr_check_kernel   one CTA per image row; both rows are staged in shared
 //                   memory before any write, so the in-place update reads
 //                   only unmodified values (rows are independent).
-// gap_kernel        gap interpolation along rows or columns, one thread per
-//                   pixel: the maximal invalid run through a pixel is found
-//                   by scanning at most ipol_gap_width steps each way.
-// mean_kernel       adaptive mean along rows or columns, one thread per
-//                   pixel, taps in ascending offset order, FP32 without
-//                   contraction.
+// post_pass_kernel  one pass per launch, one thread per pixel: gap
+//                   interpolation along rows or columns (the maximal invalid
+//                   run through a pixel is found by scanning at most
+//                   ipol_gap_width steps each way), the adaptive mean along
+//                   rows or columns (taps in ascending offset order, FP32
+//                   without contraction), or the copy to float.
 #include "launch.cuh"
 
 namespace elas {
 
-__global__ void lr_check_kernel(int16_t *__restrict__ dL, int16_t *__restrict__ dR, int w, int thr,
-                                uint8_t *__restrict__ maskL, uint8_t *__restrict__ maskR) {
+__device__ __forceinline__ void lr_check_body(const LrArgs &a, const VB &vb) {
     extern __shared__ int16_t s_rows[];
+    const int w = a.w, thr = a.thr;
     int16_t *sL = s_rows, *sR = s_rows + w;
-    const size_t row = (size_t)blockIdx.x * w;
+    int16_t *__restrict__ dL = a.dL;
+    int16_t *__restrict__ dR = a.dR;
+    uint8_t *maskL = a.maskL, *maskR = a.maskR;
+    const size_t row = (size_t)vb.x * w;
     for (int u = threadIdx.x; u < w; u += blockDim.x) {
         sL[u] = dL[row + u];
         sR[u] = dR[row + u];
@@ -42,21 +45,15 @@ __global__ void lr_check_kernel(int16_t *__restrict__ dL, int16_t *__restrict__ 
     }
 }
 
-// Value of element k along a line: from the int16 map or the float buffer.
-struct LineIn {
-    const int16_t *i16;
-    const float *f32;
-    __device__ __forceinline__ float at(size_t idx) const { return i16 ? (float)i16[idx] : f32[idx]; }
-};
+__global__ void __launch_bounds__(256) lr_check_kernel(LrArgs a) { lr_check_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) lr_check_kernel_b(const LrArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    lr_check_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 
-__global__ void gap_kernel(LineIn in, float *__restrict__ out, int w, int h, int vertical, int gap) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
-    if (u >= w || v >= h) return;
-    const int len = vertical ? h : w;
-    const int k = vertical ? v : u;
-    const size_t base = vertical ? (size_t)u : (size_t)v * w;
-    const size_t es = vertical ? (size_t)w : 1;
+// Gap interpolation along a row or a column at element k of a line of
+// length len (stride es from base).
+__device__ __forceinline__ float gap_at(const LineIn &in, size_t base, size_t es, int k, int len, int gap) {
     const float x = in.at(base + (size_t)k * es);
     float res = x;
     if (x < 0.0f) {
@@ -71,19 +68,14 @@ __global__ void gap_kernel(LineIn in, float *__restrict__ out, int w, int h, int
             res = fabsf(__fsub_rn(d1, d2)) < 3.0f ? __fmul_rn(__fadd_rn(d1, d2), 0.5f) : fminf(d1, d2);
         }
     }
-    out[(size_t)v * w + u] = res;
+    return res;
 }
 
 constexpr int kMeanRadius = 3;
 
-__global__ void mean_kernel(LineIn in, float *__restrict__ out, int w, int h, int vertical) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
-    if (u >= w || v >= h) return;
-    const int len = vertical ? h : w;
-    const int k = vertical ? v : u;
-    const size_t base = vertical ? (size_t)u : (size_t)v * w;
-    const size_t es = vertical ? (size_t)w : 1;
+// Adaptive mean along a line: taps in ascending offset order, FP32 without
+// contraction.
+__device__ __forceinline__ float mean_at(const LineIn &in, size_t base, size_t es, int k, int len) {
     const float d0 = in.at(base + (size_t)k * es);
     float res = d0;
     if (d0 >= 0.0f) {
@@ -102,52 +94,125 @@ __global__ void mean_kernel(LineIn in, float *__restrict__ out, int w, int h, in
         }
         res = __fdiv_rn(swd, sw);
     }
-    out[(size_t)v * w + u] = res;
+    return res;
 }
 
-__global__ void to_float_kernel(const int16_t *__restrict__ in, float *__restrict__ out, size_t n) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
+// One pass of post-processing over a 32x8 pixel tile: gap interpolation or
+// adaptive mean along rows or columns, or the int16 -> float copy.
+__device__ __forceinline__ void post_pass_body(const PostArgs &a, const VB &vb) {
+    const int w = a.w, h = a.h;
+    const int u = vb.x * blockDim.x + threadIdx.x;
+    const int v = vb.y * blockDim.y + threadIdx.y;
+    if (u >= w || v >= h) return;
+    const int kind = a.kind;
+    float res;
+    if (kind == kPostCopy) {
+        res = a.in.at((size_t)v * w + u);
+    } else {
+        const int vertical = kind == kPostGapCols || kind == kPostMeanCols;
+        const int len = vertical ? h : w;
+        const int k = vertical ? v : u;
+        const size_t base = vertical ? (size_t)u : (size_t)v * w;
+        const size_t es = vertical ? (size_t)w : 1;
+        res = kind <= kPostGapCols ? gap_at(a.in, base, es, k, len, a.gap) : mean_at(a.in, base, es, k, len);
+    }
+    a.out[(size_t)v * w + u] = res;
+}
+
+__global__ void __launch_bounds__(256) post_pass_kernel(PostArgs a) { post_pass_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    post_pass_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 size_t post_workspace(int w, int h) { return 2 * align_up((size_t)w * h * sizeof(float), 256); }
 
+size_t lr_smem(int w) { return 2 * (size_t)w * sizeof(int16_t); }
+
+static elas_status lr_smem_attr(const void *fn, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return launch_status("lr_check smem attribute");
+    return ELAS_OK;
+}
+
 elas_status launch_lr_check(int16_t *dL, int16_t *dR, int w, int h, int thr, uint8_t *maskL, uint8_t *maskR,
                             cudaStream_t st) {
-    const size_t smem = 2 * (size_t)w * sizeof(int16_t);
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(lr_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return launch_status("lr_check smem attribute");
-    }
-    lr_check_kernel<<<h, 256, smem, st>>>(dL, dR, w, thr, maskL, maskR);
+    const size_t smem = lr_smem(w);
+    elas_status s = lr_smem_attr((const void *)lr_check_kernel, smem);
+    if (s != ELAS_OK) return s;
+    lr_check_kernel<<<h, 256, smem, st>>>(LrArgs{dL, dR, w, h, thr, maskL, maskR});
     return launch_status("lr_check_kernel");
 }
 
-elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, cudaStream_t st) {
+// The ordered passes of post-processing for one map: gap interpolation
+// (rows, then columns) and the adaptive mean (rows, then columns); the last
+// pass writes `out`, the others alternate between the two scratch maps.  With
+// no pass enabled the one pass is the copy to float.
+int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, PostArgs *passes) {
     float *A = reinterpret_cast<float *>(ws);
     float *B = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + align_up((size_t)w * h * sizeof(float), 256));
-    dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8);
-    // ordered list of passes; the last one writes `out`
-    int passes[4], np = 0;
-    if (p->ipol_gap_width > 0) { passes[np++] = 0; passes[np++] = 1; }
-    if (p->filter_adaptive_mean) { passes[np++] = 2; passes[np++] = 3; }
-    if (np == 0) {
-        const size_t n = (size_t)w * h;
-        to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, out, n);
-        return launch_status("to_float_kernel");
+    int kinds[4], np = 0;
+    if (p->ipol_gap_width > 0) {
+        kinds[np++] = kPostGapRows;
+        kinds[np++] = kPostGapCols;
     }
+    if (p->filter_adaptive_mean) {
+        kinds[np++] = kPostMeanRows;
+        kinds[np++] = kPostMeanCols;
+    }
+    if (np == 0) kinds[np++] = kPostCopy;
     LineIn in{d, nullptr};
     for (int i = 0; i < np; ++i) {
         float *dst = (i == np - 1) ? out : ((i & 1) ? B : A);
-        const int kind = passes[i];
-        if (kind < 2)
-            gap_kernel<<<grd, blk, 0, st>>>(in, dst, w, h, kind == 1, p->ipol_gap_width);
-        else
-            mean_kernel<<<grd, blk, 0, st>>>(in, dst, w, h, kind == 3);
-        elas_status s = launch_status(kind < 2 ? "gap_kernel" : "mean_kernel");
-        if (s != ELAS_OK) return s;
+        passes[i] = PostArgs{in, dst, w, h, kinds[i], p->ipol_gap_width};
         in = LineIn{nullptr, dst};
+    }
+    return np;
+}
+
+dim3 post_grid(int w, int h) { return dim3((w + 31) / 32, (h + 7) / 8); }
+
+elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, cudaStream_t st) {
+    PostArgs passes[4];
+    const int np = post_passes(d, w, h, p, out, ws, passes);
+    for (int i = 0; i < np; ++i) {
+        post_pass_kernel<<<post_grid(w, h), dim3(32, 8), 0, st>>>(passes[i]);
+        elas_status s = launch_status("post_pass_kernel");
+        if (s != ELAS_OK) return s;
+    }
+    return ELAS_OK;
+}
+
+// Batched LR check and post-processing.  post_tab[k] is the table of pass k
+// and npass_of(slot) the number of passes of a slot (0: no post-processing).
+elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const PostArgs *const *post_tab,
+                             const int *npass, const VMap &pairs, cudaStream_t st) {
+    if (pairs.n == 0) return ELAS_OK;
+    VMap m_lr;
+    vmap_clear(m_lr, pairs.stride);
+    int maxw = 1, maxp = 0;
+    for (int i = 0; i < pairs.n; ++i) {
+        const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
+        vmap_add(m_lr, pairs.slot[i], dim3(l.h));
+        maxw = max(maxw, l.w);
+        maxp = max(maxp, npass[i]);
+    }
+    const size_t smem = lr_smem(maxw);
+    elas_status s = lr_smem_attr((const void *)lr_check_kernel_b, smem);
+    if (s != ELAS_OK) return s;
+    lr_check_kernel_b<<<vmap_total(m_lr), 256, smem, st>>>(lr_tab, m_lr);
+    if ((s = launch_status("lr_check_kernel_b")) != ELAS_OK) return s;
+    for (int k = 0; k < maxp && k < 4; ++k) {
+        VMap m;
+        vmap_clear(m, pairs.stride);
+        for (int i = 0; i < pairs.n; ++i) {
+            const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
+            vmap_add(m, pairs.slot[i], k < npass[i] ? post_grid(l.w, l.h) : dim3(0));
+        }
+        if (vmap_total(m) == 0) continue;
+        post_pass_kernel_b<<<vmap_total(m), dim3(32, 8), 0, st>>>(post_tab[k], m);
+        if ((s = launch_status("post_pass_kernel_b")) != ELAS_OK) return s;
     }
     return ELAS_OK;
 }

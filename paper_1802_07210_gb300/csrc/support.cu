@@ -21,12 +21,6 @@
 
 namespace elas {
 
-struct SupportArgs {
-    int w, h, step, wc, hc;
-    int dmin, dmax;
-    float thr;
-    int support_texture, lr_threshold;
-};
 
 // Best disparity of the window (a0..a3 at (u+-2, v+-2)) against `oth`,
 // searching other position uo = u + dir*d with 4 <= uo <= w-5.  Warp
@@ -74,22 +68,24 @@ __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth
     return (__uint2float_rn(gm1) <= __fmul_rn(thr, __uint2float_rn(gm2))) ? gd1 : -1;
 }
 
-__global__ void __launch_bounds__(256)
-support_match_kernel(const uint4 *__restrict__ dL, const uint4 *__restrict__ dR, SupportArgs a,
-                     int16_t *__restrict__ raw) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB &vb) {
+    const SupportArgs &a = m.a;
+    const uint4 *__restrict__ dL = m.dL;
+    const uint4 *__restrict__ dR = m.dR;
+    const int warp = (vb.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= a.wc * a.hc) return;
-    const int ic = warp / a.wc, jc = warp - ic * a.wc;
+    const int w = a.w, wc = a.wc;
+    if (warp >= wc * a.hc) return;
+    const int ic = warp / wc, jc = warp - ic * wc;
     const int u = jc * a.step, v = ic * a.step;
     int out = -1;
-    if (u >= 4 && u <= a.w - 5 && v >= 4 && v <= a.h - 5) {
-        const size_t rt = (size_t)(v - 2) * a.w, rb = (size_t)(v + 2) * a.w;
+    if (u >= 4 && u <= w - 5 && v >= 4 && v <= a.h - 5) {
+        const size_t rt = (size_t)(v - 2) * w, rb = (size_t)(v + 2) * w;
         const uint4 l0 = __ldg(dL + rt + u - 2), l1 = __ldg(dL + rt + u + 2);
         const uint4 l2 = __ldg(dL + rb + u - 2), l3 = __ldg(dL + rb + u + 2);
         const uint32_t texL = texture16(l0) + texture16(l1) + texture16(l2) + texture16(l3);
         if ((int)texL >= a.support_texture) {
-            const int d1 = warp_best_disparity(dR, a.w, l0, l1, l2, l3, u, v, -1, a.dmin, a.dmax, a.thr, lane);
+            const int d1 = warp_best_disparity(dR, w, l0, l1, l2, l3, u, v, -1, a.dmin, a.dmax, a.thr, lane);
             if (d1 >= 0) {
                 const int ur = u - d1;
                 const uint4 r0 = __ldg(dR + rt + ur - 2), r1 = __ldg(dR + rt + ur + 2);
@@ -97,13 +93,19 @@ support_match_kernel(const uint4 *__restrict__ dL, const uint4 *__restrict__ dR,
                 const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
                 if ((int)texR >= a.support_texture) {
                     const int d2 =
-                        warp_best_disparity(dL, a.w, r0, r1, r2, r3, ur, v, +1, a.dmin, a.dmax, a.thr, lane);
+                        warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, a.dmin, a.dmax, a.thr, lane);
                     if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
                 }
             }
         }
     }
-    if (lane == 0) raw[warp] = (int16_t)out;
+    if (lane == 0) m.raw[warp] = (int16_t)out;
+}
+
+__global__ void __launch_bounds__(512) support_match_kernel(MatchArgs m) { support_match_body(m, vb_single()); }
+__global__ void __launch_bounds__(512) support_match_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    support_match_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // Consistency filter on a 32x8 tile of candidates staged with its halo in
@@ -111,42 +113,51 @@ support_match_kernel(const uint4 *__restrict__ dL, const uint4 *__restrict__ dR,
 // next kernel can OR into them.
 constexpr int kConsTX = 32, kConsTY = 8;
 
-__global__ void __launch_bounds__(kConsTX *kConsTY)
-consistency_kernel(const int16_t *__restrict__ in, int wc, int hc, int r, int thr, int min_support,
-                   int16_t *__restrict__ out, uint32_t *__restrict__ gL, uint32_t *__restrict__ gR, int gwords) {
+__device__ __forceinline__ void consistency_body(const ConsArgs &c, const VB &vb) {
     extern __shared__ int16_t s_g[];
+    const int r = c.r, wc = c.wc, hc = c.hc;
     const int SW = kConsTX + 2 * r, SH = kConsTY + 2 * r;
-    const int j0 = blockIdx.x * kConsTX - r, i0 = blockIdx.y * kConsTY - r;
+    const int j0 = vb.x * kConsTX - r, i0 = vb.y * kConsTY - r;
     const int tid = threadIdx.y * kConsTX + threadIdx.x;
     constexpr int NT = kConsTX * kConsTY;
     for (int k = tid; k < SW * SH; k += NT) {
         const int gi = i0 + k / SW, gj = j0 + k % SW;
-        s_g[k] = (gi >= 0 && gi < hc && gj >= 0 && gj < wc) ? in[gi * wc + gj] : (int16_t)-1;
+        s_g[k] = (gi >= 0 && gi < hc && gj >= 0 && gj < wc) ? c.in[gi * wc + gj] : (int16_t)-1;
     }
-    const int nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-    for (int k = bid * NT + tid; k < gwords; k += nblk * NT) {
+    const int nblk = vb.gx * vb.gy, bid = vb.y * vb.gx + vb.x;
+    uint32_t *gL = c.gL, *gR = c.gR;
+    for (int k = bid * NT + tid; k < c.gwords; k += nblk * NT) {
         if (gL) gL[k] = 0u;
         if (gR) gR[k] = 0u;
     }
     __syncthreads();
-    const int jc = blockIdx.x * kConsTX + threadIdx.x, ic = blockIdx.y * kConsTY + threadIdx.y;
+    const int jc = vb.x * kConsTX + threadIdx.x, ic = vb.y * kConsTY + threadIdx.y;
     if (jc >= wc || ic >= hc) return;
-    const int16_t *c = s_g + (threadIdx.y + r) * SW + threadIdx.x + r;
-    const int d = c[0];
+    const int16_t *cp = s_g + (threadIdx.y + r) * SW + threadIdx.x + r;
+    const int d = cp[0];
+    const int thr = c.thr;
     int res = -1;
     if (d >= 0) {
         int cnt = 0;
         for (int di = -r; di <= r; ++di) {
-            const int16_t *rowp = c + di * SW;
+            const int16_t *rowp = cp + di * SW;
             for (int dj = -r; dj <= r; ++dj) {
                 const int v = rowp[dj];
                 cnt += (v >= 0) & (abs(v - d) <= thr);
             }
         }
         cnt -= (thr >= 0);  // the point itself
-        if (cnt >= min_support) res = d;
+        if (cnt >= c.min_support) res = d;
     }
-    out[ic * wc + jc] = (int16_t)res;
+    c.out[ic * wc + jc] = (int16_t)res;
+}
+
+__global__ void __launch_bounds__(kConsTX *kConsTY) consistency_kernel(ConsArgs c) {
+    consistency_body(c, vb_single());
+}
+__global__ void __launch_bounds__(kConsTX *kConsTY) consistency_kernel_b(const ConsArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    consistency_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 __device__ __forceinline__ void or_bits(uint32_t *cell, int d, int dmin, int dmax) {
@@ -154,23 +165,20 @@ __device__ __forceinline__ void or_bits(uint32_t *cell, int d, int dmin, int dma
         if (dd >= dmin && dd <= dmax) atomicOr(cell + (dd >> 5), 1u << (dd & 31));
 }
 
-struct GridArgs {
-    int step, G, gw, gh, nw, dmin, dmax;
-};
 
 // Redundancy filter for one lattice row per CTA, the grid-vector bits of the
 // surviving points (atomicOr: order free) and the row's point count.
-__global__ void __launch_bounds__(128)
-redundancy_grid_kernel(const int16_t *__restrict__ con, int wc, int hc, int maxd, int enabled, GridArgs g,
-                       int16_t *__restrict__ dcan, uint32_t *__restrict__ gridL, uint32_t *__restrict__ gridR,
-                       int32_t *__restrict__ rowcount) {
+__device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB &vb) {
     __shared__ int s_cnt[4];
-    const int ic = blockIdx.x;
+    const int16_t *__restrict__ con = ra.con;
+    const int wc = ra.wc, hc = ra.hc, maxd = ra.maxd;
+    const GridArgs g = ra.g;
+    const int ic = vb.x;
     int mine = 0;
     for (int jc = threadIdx.x; jc < wc; jc += blockDim.x) {
         const int d = con[ic * wc + jc];
         int res = d;
-        if (d >= 0 && enabled) {
+        if (d >= 0 && ra.enabled) {
             const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
             bool redundant = true;
             for (int k = 0; k < 4 && redundant; ++k) {
@@ -187,13 +195,13 @@ redundancy_grid_kernel(const int16_t *__restrict__ con, int wc, int hc, int maxd
             }
             if (redundant) res = -1;
         }
-        dcan[ic * wc + jc] = (int16_t)res;
+        ra.dcan[ic * wc + jc] = (int16_t)res;
         if (res >= 0) {
             ++mine;
             const int u = jc * g.step, v = ic * g.step;
             const int cy = v / g.G;
             for (int side = 0; side < 2; ++side) {
-                uint32_t *grid = side ? gridR : gridL;
+                uint32_t *grid = side ? ra.gridR : ra.gridL;
                 if (!grid) continue;
                 const int cx = (side ? u - res : u) / g.G;
                 for (int y = max(0, cy - 1); y <= min(g.gh - 1, cy + 1); ++y)
@@ -205,26 +213,32 @@ redundancy_grid_kernel(const int16_t *__restrict__ con, int wc, int hc, int maxd
     mine = __reduce_add_sync(0xFFFFFFFFu, mine);
     if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = mine;
     __syncthreads();
-    if (threadIdx.x == 0) rowcount[ic] = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+    if (threadIdx.x == 0) ra.rowcount[ic] = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+}
+
+__global__ void __launch_bounds__(128) redundancy_grid_kernel(RedArgs ra) { redundancy_grid_body(ra, vb_single()); }
+__global__ void __launch_bounds__(128) redundancy_grid_kernel_b(const RedArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    redundancy_grid_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // Raster-order compaction, one lattice row per CTA: the row's offset is the
 // sum of the counts of the rows above; entries are placed with warp ballots.
-__global__ void __launch_bounds__(128)
-compact_rows_kernel(const int16_t *__restrict__ dcan, int wc, int hc, int step, const int32_t *__restrict__ rowcount,
-                    int16_t *__restrict__ list, int32_t *__restrict__ count) {
+__device__ __forceinline__ void compact_rows_body(const CompactArgs &ca, const VB &vb) {
     __shared__ int s_w[4];
-    const int ic = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wc = ca.wc, hc = ca.hc, step = ca.step;
+    const int ic = vb.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int part = 0;
-    for (int k = tid; k < ic; k += 128) part += rowcount[k];
+    for (int k = tid; k < ic; k += 128) part += ca.rowcount[k];
     part = __reduce_add_sync(0xFFFFFFFFu, part);
     if (lane == 0) s_w[warp] = part;
     __syncthreads();
     int base = s_w[0] + s_w[1] + s_w[2] + s_w[3];
     __syncthreads();
+    int16_t *list = ca.list;
     for (int j0 = 0; j0 < wc; j0 += 128) {
         const int jc = j0 + tid;
-        const int d = jc < wc ? dcan[ic * wc + jc] : -1;
+        const int d = jc < wc ? ca.dcan[ic * wc + jc] : -1;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, d >= 0);
         if (lane == 0) s_w[warp] = __popc(bal);
         __syncthreads();
@@ -238,7 +252,13 @@ compact_rows_kernel(const int16_t *__restrict__ dcan, int wc, int hc, int step, 
         base += s_w[0] + s_w[1] + s_w[2] + s_w[3];
         __syncthreads();
     }
-    if (ic == hc - 1 && tid == 0) *count = base;
+    if (ic == hc - 1 && tid == 0) *ca.count = base;
+}
+
+__global__ void __launch_bounds__(128) compact_rows_kernel(CompactArgs ca) { compact_rows_body(ca, vb_single()); }
+__global__ void __launch_bounds__(128) compact_rows_kernel_b(const CompactArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    compact_rows_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 size_t support_workspace(int w, int h, const elas_params *p) {
@@ -249,9 +269,11 @@ size_t support_workspace(int w, int h, const elas_params *p) {
 
 constexpr int kMaxConsistencyWindow = 64;
 
-elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
-                           int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
-                           void *ws, cudaStream_t st) {
+elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                         int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
+                         void *ws, SupportStage *o) {
+    if (p->incon_window_size > kMaxConsistencyWindow)
+        return fail(ELAS_ERR_INVALID_ARG, "incon_window_size %d above %d", p->incon_window_size, kMaxConsistencyWindow);
     SupportArgs a;
     a.w = w;
     a.h = h;
@@ -265,41 +287,96 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     a.lr_threshold = p->lr_threshold;
     const int nc = a.wc * a.hc;
     const GridGeom g = grid_geom(w, h, p);
-    const int gwords = g.gw * g.gh * g.nw;
-    if (p->incon_window_size > kMaxConsistencyWindow)
-        return fail(ELAS_ERR_INVALID_ARG, "incon_window_size %d above %d", p->incon_window_size, kMaxConsistencyWindow);
+    const size_t grid_bytes = align_up((size_t)nc * sizeof(int16_t) + 16, 256);
+    int16_t *raw = reinterpret_cast<int16_t *>(ws);
+    int16_t *con = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(ws) + grid_bytes);
+    int32_t *rowcount = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(ws) + 2 * grid_bytes);
+    o->match = MatchArgs{reinterpret_cast<const uint4 *>(descL), reinterpret_cast<const uint4 *>(descR), a, raw};
+    o->cons = ConsArgs{raw, a.wc, a.hc, p->incon_window_size, p->incon_threshold, p->incon_min_support, con,
+                       grid_L, grid_R, g.gw * g.gh * g.nw};
+    o->red = RedArgs{con, a.wc, a.hc, p->redun_max_dist, (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1,
+                     GridArgs{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax}, d_can, grid_L, grid_R,
+                     rowcount};
+    o->compact = CompactArgs{d_can, a.wc, a.hc, a.step, rowcount, list, count};
+    return ELAS_OK;
+}
+
+size_t consistency_smem(int r) { return (size_t)(kConsTX + 2 * r) * (kConsTY + 2 * r) * sizeof(int16_t); }
+
+static elas_status consistency_smem_attr(const void *fn, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return launch_status("consistency_kernel shared memory attribute");
+    return ELAS_OK;
+}
+
+dim3 support_match_grid(const MatchArgs &m, int warps) {
+    const int nc = m.a.wc * m.a.hc;
+    return dim3((nc + warps - 1) / warps);
+}
+dim3 consistency_grid(const ConsArgs &c) { return dim3((c.wc + kConsTX - 1) / kConsTX, (c.hc + kConsTY - 1) / kConsTY); }
+dim3 lattice_row_grid(int hc) { return dim3(hc); }
+
+elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
+                           int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
+                           void *ws, cudaStream_t st) {
+    SupportStage sa;
+    elas_status s = support_args(descL, descR, w, h, p, d_can, list, count, grid_L, grid_R, ws, &sa);
+    if (s != ELAS_OK) return s;
+    const int nc = sa.match.a.wc * sa.match.a.hc;
     if (nc == 0) {
-        if ((grid_L && cudaMemsetAsync(grid_L, 0, (size_t)gwords * 4, st) != cudaSuccess) ||
-            (grid_R && cudaMemsetAsync(grid_R, 0, (size_t)gwords * 4, st) != cudaSuccess) ||
+        const size_t gbytes = (size_t)sa.cons.gwords * 4;
+        if ((grid_L && cudaMemsetAsync(grid_L, 0, gbytes, st) != cudaSuccess) ||
+            (grid_R && cudaMemsetAsync(grid_R, 0, gbytes, st) != cudaSuccess) ||
             cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess)
             return launch_status("memset empty support");
         return ELAS_OK;
     }
-    int16_t *raw = reinterpret_cast<int16_t *>(ws);
-    int16_t *con = reinterpret_cast<int16_t *>(reinterpret_cast<char *>(ws) + align_up(nc * sizeof(int16_t) + 16, 256));
-    int32_t *rowcount =
-        reinterpret_cast<int32_t *>(reinterpret_cast<char *>(ws) + 2 * align_up(nc * sizeof(int16_t) + 16, 256));
     const int warps_per_block = 8;
-    support_match_kernel<<<(nc + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        reinterpret_cast<const uint4 *>(descL), reinterpret_cast<const uint4 *>(descR), a, raw);
-    elas_status s = launch_status("support_match_kernel");
-    if (s != ELAS_OK) return s;
-    const int r = p->incon_window_size;
-    const size_t smem = (size_t)(kConsTX + 2 * r) * (kConsTY + 2 * r) * sizeof(int16_t);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(consistency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return launch_status("consistency_kernel shared memory attribute");
-    consistency_kernel<<<dim3((a.wc + kConsTX - 1) / kConsTX, (a.hc + kConsTY - 1) / kConsTY), dim3(kConsTX, kConsTY),
-                         smem, st>>>(raw, a.wc, a.hc, r, p->incon_threshold, p->incon_min_support, con, grid_L,
-                                     grid_R, gwords);
+    support_match_kernel<<<support_match_grid(sa.match, warps_per_block), 32 * warps_per_block, 0, st>>>(sa.match);
+    if ((s = launch_status("support_match_kernel")) != ELAS_OK) return s;
+    const size_t smem = consistency_smem(sa.cons.r);
+    if ((s = consistency_smem_attr((const void *)consistency_kernel, smem)) != ELAS_OK) return s;
+    consistency_kernel<<<consistency_grid(sa.cons), dim3(kConsTX, kConsTY), smem, st>>>(sa.cons);
     if ((s = launch_status("consistency_kernel")) != ELAS_OK) return s;
-    GridArgs ga{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax};
-    redundancy_grid_kernel<<<a.hc, 128, 0, st>>>(con, a.wc, a.hc, p->redun_max_dist,
-                                                 (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1, ga, d_can,
-                                                 grid_L, grid_R, rowcount);
+    redundancy_grid_kernel<<<lattice_row_grid(sa.red.hc), 128, 0, st>>>(sa.red);
     if ((s = launch_status("redundancy_grid_kernel")) != ELAS_OK) return s;
-    compact_rows_kernel<<<a.hc, 128, 0, st>>>(d_can, a.wc, a.hc, a.step, rowcount, list, count);
+    compact_rows_kernel<<<lattice_row_grid(sa.compact.hc), 128, 0, st>>>(sa.compact);
     return launch_status("compact_rows_kernel");
+}
+
+// Batched support stage: every pair of the launch must have at least one
+// lattice candidate (w, h >= candidate_stepsize).
+elas_status launch_support_b(const SupportTables &t, const SupportStage *host, const VMap &pairs, int match_warps,
+                             cudaStream_t st) {
+    if (match_warps != 4 && match_warps != 8 && match_warps != 16)
+        return fail(ELAS_ERR_INVALID_ARG, "support warps per CTA %d", match_warps);
+    VMap m_match, m_cons, m_rows;
+    vmap_clear(m_match, pairs.stride);
+    vmap_clear(m_cons, pairs.stride);
+    vmap_clear(m_rows, pairs.stride);
+    size_t cons_smem = 0;
+    for (int i = 0; i < pairs.n; ++i) {
+        const int slot = pairs.slot[i];
+        const SupportStage &h = slot_entry(host, pairs.stride, slot);
+        if (h.match.a.wc * h.match.a.hc == 0)
+            return fail(ELAS_ERR_INVALID_ARG, "pair %d has no lattice candidate", i);
+        vmap_add(m_match, slot, support_match_grid(h.match, match_warps));
+        vmap_add(m_cons, slot, consistency_grid(h.cons));
+        vmap_add(m_rows, slot, lattice_row_grid(h.red.hc));
+        cons_smem = cons_smem > consistency_smem(h.cons.r) ? cons_smem : consistency_smem(h.cons.r);
+    }
+    if (pairs.n == 0) return ELAS_OK;
+    elas_status s;
+    support_match_kernel_b<<<vmap_total(m_match), 32 * match_warps, 0, st>>>(t.match, m_match);
+    if ((s = launch_status("support_match_kernel_b")) != ELAS_OK) return s;
+    if ((s = consistency_smem_attr((const void *)consistency_kernel_b, cons_smem)) != ELAS_OK) return s;
+    consistency_kernel_b<<<vmap_total(m_cons), dim3(kConsTX, kConsTY), cons_smem, st>>>(t.cons, m_cons);
+    if ((s = launch_status("consistency_kernel_b")) != ELAS_OK) return s;
+    redundancy_grid_kernel_b<<<vmap_total(m_rows), 128, 0, st>>>(t.red, m_rows);
+    if ((s = launch_status("redundancy_grid_kernel_b")) != ELAS_OK) return s;
+    compact_rows_kernel_b<<<vmap_total(m_rows), 128, 0, st>>>(t.compact, m_rows);
+    return launch_status("compact_rows_kernel_b");
 }
 
 }  // namespace elas
