@@ -20,12 +20,15 @@
 // (4 r^2 <= 32^2 in exact arithmetic, so no farther point can matter) and,
 // where the star stays open (p on the hull), nothing lies beyond either open
 // edge (checked against the extreme points of every image row).  The other
-// stars are rebuilt by one CTA per point: each step takes the best of the
-// points within 192 pixels when its circle fits that radius (pass 2, 256
-// threads); stars with a step whose circle does not fit are rebuilt by 1024
-// threads that scan every point for such steps (pass 3), which is exact.  Each triangle is emitted
-// once, by its lowest-index vertex, at an offset from an exclusive scan of
-// the per-point counts, so the output order is deterministic.
+// stars go through the same group pass once more with one warp per star and
+// the points within 64 pixels (circles up to radius 32).  The rest are
+// rebuilt by one CTA (256 threads) per point: each step takes the best of
+// the points within 192 pixels when its circle fits that disc, else scans
+// the grid cells its circle (or, with no candidate, its half-plane) meets,
+// which is exact.  Each triangle
+// is emitted once, by its lowest-index vertex, at an offset from an
+// exclusive scan of the per-point counts, so the output order is
+// deterministic.
 #include "launch.cuh"
 
 namespace elas {
@@ -315,10 +318,12 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
 // star is accepted when every triangle's circumdisc lies inside the radius
 // (4 r^2 <= R^2, exact) and, for an open star (p on the hull), nothing lies
 // beyond either open edge (checked against the extreme points of every image
-// row).  Other stars are queued for pass 2.
+// row).  Other stars are queued for the next pass.
 constexpr int kDtGroup = 8;
 constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (the radius-32 disc holds at most ~120 lattice points)
+constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
+constexpr int kDtListCapB = 640; // the radius-64 disc holds at most ~520 lattice points
 
 __device__ __forceinline__ bool dt_small_circle_exact(const int4 &p, const int4 &a, const int4 &b, int R) {
     const int64_t pa = (int64_t)(a.x - p.x) * (a.x - p.x) + (int64_t)(a.y - p.y) * (a.y - p.y);
@@ -334,10 +339,11 @@ __device__ __forceinline__ int4 gshfl4(unsigned m, const int4 &v, int src) {
 }
 
 // Group reduction of (best, key) under the pencil order of edge (p, e).
+template <int G>
 __device__ __forceinline__ int4 dt_group_best(unsigned m, int4 best, DtKey<int> bk, const int4 &p, const int4 &e,
                                               int side) {
 #pragma unroll
-    for (int o = kDtGroup / 2; o > 0; o >>= 1) {
+    for (int o = G / 2; o > 0; o >>= 1) {
         int4 ob;
         ob.x = __shfl_xor_sync(m, best.x, o);
         ob.y = __shfl_xor_sync(m, best.y, o);
@@ -367,22 +373,28 @@ __device__ __forceinline__ int4 dt_group_best(unsigned m, int4 best, DtKey<int> 
     return best;
 }
 
-__device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
-    __shared__ int s_list[kDtGroupThreads / kDtGroup][kDtListCap];
+// G lanes per star, candidates within R (list capacity CAP).  QUEUE: the
+// stars of the first queue (left by the R = 32 pass), failures go to the
+// second queue; else every point, failures to the first queue.
+template <int G, int R, int CAP, bool QUEUE>
+__device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb) {
+    static_assert(2 * R / kDtCell + 2 <= G, "the group's lanes fetch the cell rows of the disc");
+    static_assert(R <= 64, "32-bit pencil keys are exact for coordinates within 64 of p");
+    __shared__ int s_list[kDtGroupThreads / G][CAP];
     const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int lane = threadIdx.x & 31, gl = lane & (kDtGroup - 1), gbase = lane & ~(kDtGroup - 1);
-    const unsigned gm = ((1u << kDtGroup) - 1u) << gbase;
-    int *list = s_list[threadIdx.x / kDtGroup];
-    const int R = kDtRadius;
-    const int groups = vb.gx * (kDtGroupThreads / kDtGroup);
-    for (int j = vb.x * (kDtGroupThreads / kDtGroup) + threadIdx.x / kDtGroup; j < n; j += groups) {
-        const int4 p = S.pts[j];
-        if (!p.w || S.status[p.z] != 0) continue;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), gbase = lane & ~(G - 1);
+    const unsigned gm = G == 32 ? 0xFFFFFFFFu : ((1u << (G & 31)) - 1u) << gbase;
+    int *list = s_list[threadIdx.x / G];
+    const int groups = vb.gx * (kDtGroupThreads / G);
+    const int njobs = QUEUE ? *S.npending : n;
+    for (int j = vb.x * (kDtGroupThreads / G) + threadIdx.x / G; j < njobs; j += groups) {
+        const int4 p = QUEUE ? S.pts[S.slot[S.pending[j]]] : S.pts[j];
+        if (!p.w || (!QUEUE && S.status[p.z] != 0)) continue;
         // candidates: lanes fetch the cell rows' ranges, then stride over them
         const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, max(0, p.x + R) / kDtCell);
         const int cy0 = max(0, p.y - R) / kDtCell, cy1 = min(a.gh - 1, max(0, p.y + R) / kDtCell);
-        const int nrows = cy1 - cy0 + 1;  // at most 5
+        const int nrows = cy1 - cy0 + 1;  // at most 2R/16 + 2
         int rs = 0, re = 0;
         if (gl < nrows) {
             rs = S.cell_start[(cy0 + gl) * a.gw + cx0];
@@ -393,7 +405,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
         int nn = -1;
         for (int r = 0; r < nrows; ++r) {
             const int s0 = __shfl_sync(gm, rs, gbase + r), e0 = __shfl_sync(gm, re, gbase + r);
-            for (int c = s0; c < e0; c += kDtGroup) {
+            for (int c = s0; c < e0; c += G) {
                 bool take = false;
                 if (c + gl < e0) {
                     const int4 q = S.pts[c + gl];
@@ -409,12 +421,12 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                 }
                 const unsigned b = __ballot_sync(gm, take) >> gbase;
                 const int pos = k + __popc(b & ((1u << gl) - 1u));
-                if (take && pos < kDtListCap) list[pos] = c + gl;
+                if (take && pos < CAP) list[pos] = c + gl;
                 k += __popc(b);
             }
         }
         __syncwarp(gm);
-        bool certified = k > 0 && k <= kDtListCap;
+        bool certified = k > 0 && k <= CAP;
         int written = 0;
         bool open_l = false, open_r = false;
         int4 e_l = p, e_r = p;
@@ -422,7 +434,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
             // nearest neighbour of the group
             unsigned long long kmin = key;
 #pragma unroll
-            for (int o = kDtGroup / 2; o > 0; o >>= 1) {
+            for (int o = G / 2; o > 0; o >>= 1) {
                 const unsigned long long other = __shfl_xor_sync(gm, kmin, o);
                 kmin = other < kmin ? other : kmin;
             }
@@ -434,7 +446,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
             for (int step = 0; step <= k && certified; ++step) {  // counter-clockwise
                 int4 best = make_int4(0, 0, 0, 0);
                 DtKey<int> bk{0, 1};
-                for (int c = gl; c < k; c += kDtGroup) {
+                for (int c = gl; c < k; c += G) {
                     const int4 q = S.pts[list[c]];
                     if (q.z == cur.z) continue;
                     const DtKey<int> qk = dt_key<int>(p, cur, q, +1);
@@ -444,7 +456,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                         bk = qk;
                     }
                 }
-                best = dt_group_best(gm, best, bk, p, cur, +1);
+                best = dt_group_best<G>(gm, best, bk, p, cur, +1);
                 if (!best.w) {
                     open_l = true;
                     e_l = cur;
@@ -467,7 +479,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                 for (int step = 0; step <= k && certified; ++step) {  // clockwise
                     int4 best = make_int4(0, 0, 0, 0);
                     DtKey<int> bk{0, 1};
-                    for (int c = gl; c < k; c += kDtGroup) {
+                    for (int c = gl; c < k; c += G) {
                         const int4 q = S.pts[list[c]];
                         if (q.z == cur.z) continue;
                         const DtKey<int> qk = dt_key<int>(p, cur, q, -1);
@@ -477,7 +489,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                             bk = qk;
                         }
                     }
-                    best = dt_group_best(gm, best, bk, p, cur, -1);
+                    best = dt_group_best<G>(gm, best, bk, p, cur, -1);
                     if (!best.w) {
                         open_r = true;
                         e_r = cur;
@@ -498,7 +510,7 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                 if (!open) continue;
                 const int4 e = side ? e_r : e_l;
                 bool bad = false;
-                for (int y = gl; y < a.h && !bad; y += kDtGroup) {
+                for (int y = gl; y < a.h && !bad; y += G) {
                     const int x0 = S.rowmin[y], x1 = S.rowmax[y];
                     if (x0 > x1) continue;
                     const int64_t o0 = dt_orient(p.x, p.y, e.x, e.y, x0, y);
@@ -513,6 +525,8 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
                 S.status[p.z] = 1;
                 S.owned[p.z] = written;
                 if (written > kDtSlots) atomicOr(S.err, 4);
+            } else if (QUEUE) {
+                S.pending2[atomicAdd(S.npending2, 1)] = p.z;
             } else {
                 S.pending[atomicAdd(S.npending, 1)] = p.z;
             }
@@ -521,22 +535,37 @@ __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
     }
 }
 
-__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel(DtArgs a) { dt_pass1_body(a, vb_single()); }
-__global__ void __launch_bounds__(kDtGroupThreads) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+
+__device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
+    dt_group_pass_body<kDtGroup, kDtRadius, kDtListCap, false>(a, vb);
+}
+__device__ __forceinline__ void dt_pass1b_body(const DtArgs &a, const VB &vb) {
+    dt_group_pass_body<32, kDtRadiusB, kDtListCapB, true>(a, vb);
+}
+
+__global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel(DtArgs a) { dt_pass1b_body(a, vb_single()); }
+__global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_pass1b_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) { dt_pass1_body(a, vb_single()); }
+__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     dt_pass1_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-// Pass 2: one CTA per queued point.  The points within kDtRadius2 are cached
-// in shared memory; every wrap step first takes the best cached candidate and
-// keeps it when its circumdisc lies inside that radius (then no other point
-// can beat it); otherwise (large circle, no cached candidate on that side, or
-// the cache overflowed) the step scans every point, which is exact.  So
+// CTA pass: one CTA per star left by both group passes.  The points within
+// kDtRadius2 are cached in shared memory; every wrap step first takes the
+// best cached candidate and keeps it when its circumdisc lies inside the
+// cached disc (then no other point can beat it); a step that does not fit
+// (large circle, no cached candidate on that side, or the cache overflowed)
+// scans the grid cells its disc or half-plane meets, which is exact.  So
 // every queued star comes out exact.
-constexpr int kDtRadius2 = 192;
-constexpr int kDtCandCap2 = 3072;  // pass-2 candidates cached per CTA (48 KB)
+constexpr int kDtRadius2 = 192;    // cache radius of the CTA pass
+constexpr int kDtCandCap2 = 3072;  // candidates cached per CTA (48 KB)
 constexpr int kDtMaxRows = 64;     // cell rows a radius-192 disc spans, with margin
-static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "pass-2 disc must fit the row table");
+static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "the CTA pass's disc must fit the row table");
 
 // CTA reduction of the threads' (best, key) under the pencil order: each
 // warp reduces with shuffles, warp 0 reduces the warps' results, and every
@@ -697,19 +726,28 @@ __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int
     return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
 }
 
-// Exact star of p, CTA-wide.  cand/k: cache of the points within kDtRadius2
-// (k > kDtCandCap2: unusable).  Writes the owned triangles to the slots or,
-// with out != NULL, to out.  Returns 1, or -1 if it exceeded kDtMaxStar, or
-// 0 if cached_only and a step needed every point.
-__device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4 &p, int n, const int4 *cand, int k,
-                             int *written, int32_t *out, DtBlockShared &sh, bool cached_only, int *r_start,
-                             int *r_pre) {
+__device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, int R, int4 *cand,
+                               DtBlockShared &sh);
+
+// Exact star of p, CTA-wide.  cand: shared cache (capacity kDtCandCap2)
+// holding the k points within R of p (k > kDtCandCap2: unusable), or NULL.
+// A step is taken from the cache when the winner's circle lies inside the
+// disc of radius R (2r <= R: no point outside the cache can be inside it);
+// otherwise the cache is refilled once at kDtRadius2 and, if that still does
+// not hold the circle, the step scans the cells its disc or half-plane meets
+// (every point without the region tables).  Writes the owned triangles to the
+// slots or, with out != NULL, to out.  Returns 1, or -1 if it exceeded
+// kDtMaxStar.
+__device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4 &p, int n, int4 *cand, int R, int k,
+                             int *written, int32_t *out, DtBlockShared &sh, int *r_start, int *r_pre) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
-    const bool cached = cand && k <= kDtCandCap2;
-    // nearest neighbour over every point (cheap: one pass)
+    // nearest neighbour: a cached point is nearer than every point outside
+    // the cache, so a non-empty cache holds it; else one pass over all points
     unsigned long long key = ~0ull;
-    for (int j = tid; j < n; j += nth) {
-        const int4 q = S.pts[j];
+    const bool nn_cached = cand && k > 0 && k <= kDtCandCap2;
+    const int nn_n = nn_cached ? k : n;
+    for (int j = tid; j < nn_n; j += nth) {
+        const int4 q = nn_cached ? cand[j] : S.pts[j];
         if (q.w && q.z != p.z) {
             const unsigned long long kk = dt_nn_key(p, q);
             key = kk < key ? kk : key;
@@ -741,18 +779,17 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
             ++wr;
         }
     };
-    bool bail = false;  // cached_only: a step needed every point
     auto next = [&](const int4 &cur, int side) {
         int4 b = make_int4(0, 0, 0, 0);
-        if (cached) {
+        for (;;) {
+            if (!cand || k > kDtCandCap2) break;
             b = dt_block_step(S, p, cur, side, cand, k, n, sh);
-            const bool small = b.w && (side > 0 ? dt_small_circle(p, cur, b, kDtRadius2)
-                                                : dt_small_circle(p, b, cur, kDtRadius2));
+            const bool small =
+                b.w && (side > 0 ? dt_small_circle(p, cur, b, R) : dt_small_circle(p, b, cur, R));
             if (small) return b;
-        }
-        if (cached_only) {
-            bail = true;
-            return make_int4(0, 0, 0, 0);
+            if (R >= kDtRadius2) break;
+            R = kDtRadius2;  // refill the cache once with the larger disc
+            k = dt_block_gather(a, S, p, R, cand, sh);
         }
         if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_pre);
         return dt_block_step(S, p, cur, side, nullptr, 0, n, sh);
@@ -762,7 +799,6 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
     int step = 0;
     for (; step < kDtMaxStar; ++step) {  // counter-clockwise
         const int4 best = next(cur, +1);
-        if (bail) return 0;
         if (!best.w) break;  // hull edge
         emit(cur, best);
         if (best.z == first.z) {
@@ -776,7 +812,6 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
         cur = first;
         for (step = 0; step < kDtMaxStar; ++step) {
             const int4 best = next(cur, -1);
-            if (bail) return 0;
             if (!best.w) break;
             emit(best, cur);
             cur = best;
@@ -843,14 +878,13 @@ __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, 
 }
 
 // One queued star rebuilt by the whole CTA (exact): cached steps among the
-// points within kDtRadius2, full scans restricted to the rows a step's
-// circle can reach otherwise.
+// points within kDtRadius2, region scans otherwise.
 __device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, int i, int n, int4 *s_cand,
                                               DtBlockShared &sh, int *r_start, int *r_pre) {
     const int4 p = S.pts[S.slot[i]];
     const int k = dt_block_gather(a, S, p, kDtRadius2, s_cand, sh);
     int written = 0;
-    const int r = dt_block_star(a, S, i, p, n, s_cand, k, &written, nullptr, sh, false, r_start, r_pre);
+    const int r = dt_block_star(a, S, i, p, n, s_cand, kDtRadius2, k, &written, nullptr, sh, r_start, r_pre);
     if (threadIdx.x == 0) {
         if (r == 1) {
             S.status[i] = 2;
@@ -871,8 +905,8 @@ __global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a) {
     int *r_pre = r_start + a.gh;
     const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int nq = *S.npending;
-    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, S.pending[q0], n, s_cand, sh, r_start, r_pre);
+    const int nq = *S.npending2;
+    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, S.pending2[q0], n, s_cand, sh, r_start, r_pre);
 }
 
 // Many pairs, persistent: the queues of every (pair, side) of the launch are
@@ -895,7 +929,7 @@ __global__ void __launch_bounds__(1024) dt_pass_block_kernel_b(const DtArgs *__r
         for (int j = 0; j < kPer; ++j) {
             const int q = lane * kPer + j;
             v[j] = 0;
-            if (q < nq_all) v[j] = max(0, *slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides].npending);
+            if (q < nq_all) v[j] = max(0, *slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides].npending2);
             sum += v[j];
         }
         int incl = sum;
@@ -933,7 +967,7 @@ __global__ void __launch_bounds__(1024) dt_pass_block_kernel_b(const DtArgs *__r
         const DtArgs &a = slot_entry(tab, vm.stride, vm.slot[lo / nsides]);
         const DtSide &S = a.s[lo % nsides];
         const int n = min(max(*a.count, 0), a.cap);
-        dt_block_item(a, S, S.pending[item - s_pre[lo]], n, s_cand, sh, r_start, r_start + a.gh);
+        dt_block_item(a, S, S.pending2[item - s_pre[lo]], n, s_cand, sh, r_start, r_start + a.gh);
     }
 }
 
@@ -1016,7 +1050,7 @@ __device__ __forceinline__ void dt_emit_big_body(const DtArgs &a, const VB &vb) 
         if (S.owned[i] <= kDtSlots) continue;
         const int4 p = S.pts[S.slot[i]];
         int written = 0;
-        dt_block_star(a, S, i, p, n, nullptr, 0, &written, S.tri + 3 * (size_t)S.offset[i], sh, false, nullptr,
+        dt_block_star(a, S, i, p, n, nullptr, 0, 0, &written, S.tri + 3 * (size_t)S.offset[i], sh, nullptr,
                       nullptr);
         __syncthreads();
     }
@@ -1115,6 +1149,7 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     dt_dedup_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     const int gblocks = max(1, min((cap + kDtGroupThreads / kDtGroup - 1) / (kDtGroupThreads / kDtGroup), 152 * 8));
     dt_pass1_kernel<<<dim3(gblocks, nsides), kDtGroupThreads, 0, st>>>(a);
+    dt_pass1b_kernel<<<dim3(152, nsides), kDtGroupThreads, 0, st>>>(a);
     const int smem2 = kDtCandCap2 * (int)sizeof(int4);
     const int smem3 = smem2 + (2 * a.gh + 1) * (int)sizeof(int);
     if (smem3 > 227 * 1024) return fail(ELAS_ERR_INVALID_ARG, "image too tall for the triangulation grid");
@@ -1164,11 +1199,12 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
                                  int32_t *counter, cudaStream_t st) {
     if (pairs.n == 0) return ELAS_OK;
     if (nsides < 1 || nsides > 2) return fail(ELAS_ERR_INVALID_ARG, "nsides %d", nsides);
-    VMap m_init, m_pts, m_scan, m_grp, m_big;
+    VMap m_init, m_pts, m_scan, m_grp, m_grp2, m_big;
     vmap_clear(m_init, pairs.stride);
     vmap_clear(m_pts, pairs.stride);
     vmap_clear(m_scan, pairs.stride);
     vmap_clear(m_grp, pairs.stride);
+    vmap_clear(m_grp2, pairs.stride);
     vmap_clear(m_big, pairs.stride);
     int max_gh = 1;
     for (int i = 0; i < pairs.n; ++i) {
@@ -1180,6 +1216,9 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         vmap_add(m_scan, slot, dim3(1, nsides));
         const int gthreads = kDtGroupThreads / kDtGroup;
         vmap_add(m_grp, slot, dim3(dt_point_blocks(a.cap, gthreads, pairs.n), nsides));
+        // the second group pass gets a warp per star of a queue of a few
+        // percent of the points
+        vmap_add(m_grp2, slot, dim3(max(1, min(152, a.cap / 256)), nsides));
         vmap_add(m_big, slot, dim3(64, nsides));
         max_gh = max(max_gh, a.gh);
     }
@@ -1193,6 +1232,7 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
     dt_scatter_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_dedup_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
+    dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     dt_pass_block_kernel_b<<<nsm * 4, 256, smem3, st>>>(tab, pairs, nsides, counter);
