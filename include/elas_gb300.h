@@ -378,6 +378,71 @@ elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL, const uin
 size_t elas_batch_device_bytes(const elas_batch *b);
 void elas_batch_destroy(elas_batch *b);
 
+/*
+ * Server: a request loop over resident pair state with continuous batching.
+ * Requests (host images in, host maps out) are queued by elas_server_submit
+ * and handled by a scheduler thread of the library:
+ *  - admission: a request takes an idle slot of its shape (w, h, params) or
+ *    a new one while the slots' device bytes stay within the HBM budget
+ *    (idle slots of other shapes are released to make room); requests are
+ *    admitted in arrival order;
+ *  - waves: admitted requests are launched together as one wave of batched
+ *    launches (images to the device, the whole path, maps to the host) on
+ *    one of `lanes` streams; a new wave starts whenever a lane is free, so
+ *    pairs that arrive while others are on the GPU join the next wave and
+ *    overlap with the running ones;
+ *  - plain = 1 instead runs one request at a time through the per-pair path
+ *    (an elas_pipeline per shape), in arrival order: the comparison.
+ * Results are bit-identical to the per-pair path.  Host buffers passed to
+ * elas_server_submit must stay valid until the request's result has been
+ * polled; pinned memory makes the copies faster.  Times are milliseconds on
+ * the server's steady clock (elas_server_now_ms).
+ */
+typedef struct elas_server elas_server;
+typedef struct {
+    int32_t  lanes;              /* waves in flight at once, 1..8 (plain: 1)      */
+    int32_t  max_wave;           /* requests per wave at most, 1..256             */
+    int32_t  max_slots;          /* resident pair states at most, 1..1024         */
+    int32_t  plain;              /* 1: per-pair path, one request at a time       */
+    uint64_t hbm_budget_bytes;   /* device bytes for slots; 0 = free memory at
+                                    creation minus hbm_reserve_bytes            */
+    uint64_t hbm_reserve_bytes;  /* left free with hbm_budget_bytes = 0          */
+} elas_server_config;
+
+typedef struct {
+    uint64_t id;          /* the id given to elas_server_submit              */
+    int32_t  status;      /* elas_status of the request                      */
+    int32_t  n_support;   /* support points of the pair                      */
+    int32_t  wave_size;   /* requests in the wave it ran in (plain: 1)       */
+    int32_t  pad;
+    double   t_submit_ms; /* submitted                                        */
+    double   t_start_ms;  /* its wave launched                                */
+    double   t_done_ms;   /* its outputs on the host, seen by the scheduler   */
+} elas_server_result;
+
+typedef struct {
+    int64_t  submitted, completed, waves, slots_created, slots_released;
+    int32_t  slots_in_use, max_wave_seen;
+    uint64_t slot_bytes, hbm_budget_bytes;
+} elas_server_stats;
+
+elas_status elas_server_config_default(elas_server_config *cfg);
+/* Device bytes of one resident pair state (slot) of this shape; 0 if the
+ * shape or parameters are invalid. */
+size_t elas_slot_device_bytes(int32_t w, int32_t h, const elas_params *p);
+elas_status elas_server_create(const elas_server_config *cfg, elas_server **out);
+/* Queues one pair: imgL/imgR host uint8 [h][w]; dL host int16 [h][w];
+ * post host float [h][w] or NULL (post-processing off). */
+elas_status elas_server_submit(elas_server *s, uint64_t id, int32_t w, int32_t h, const elas_params *p,
+                               const uint8_t *imgL, const uint8_t *imgR, int16_t *dL, float *post);
+/* Up to max finished results (oldest first); waits up to timeout_ms for the
+ * first one.  Returns the number written, or -1 on a NULL argument. */
+int32_t elas_server_poll(elas_server *s, elas_server_result *out, int32_t max, int32_t timeout_ms);
+double elas_server_now_ms(const elas_server *s);
+elas_status elas_server_stats_get(elas_server *s, elas_server_stats *st);
+/* Waits for every queued request, then stops the scheduler and frees all. */
+void elas_server_destroy(elas_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,23 @@ class BatchConfig(C.Structure):
                 ("dense_threads_per_pixel", C.c_int32), ("use_graph", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("max_wave", C.c_int32), ("max_slots", C.c_int32), ("plain", C.c_int32),
+                ("hbm_budget_bytes", C.c_uint64), ("hbm_reserve_bytes", C.c_uint64)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("n_support", C.c_int32), ("wave_size", C.c_int32),
+                ("pad", C.c_int32), ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double),
+                ("t_done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("waves", C.c_int64),
+                ("slots_created", C.c_int64), ("slots_released", C.c_int64), ("slots_in_use", C.c_int32),
+                ("max_wave_seen", C.c_int32), ("slot_bytes", C.c_uint64), ("hbm_budget_bytes", C.c_uint64)]
+
+
 _P, _I, _Z = C.c_void_p, C.c_int32, C.c_size_t
 
 # name -> (restype, argtypes), exactly the declarations of include/*.h
@@ -93,6 +110,14 @@ SIGNATURES = {
     "elas_batch_tune": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "elas_batch_device_bytes": (_Z, [_P]),
     "elas_batch_destroy": (None, [_P]),
+    "elas_server_config_default": (C.c_int, [_P]),
+    "elas_slot_device_bytes": (_Z, [_I, _I, _P]),
+    "elas_server_create": (C.c_int, [_P, _P]),
+    "elas_server_submit": (C.c_int, [_P, C.c_uint64, _I, _I, _P, _P, _P, _P, _P]),
+    "elas_server_poll": (C.c_int32, [_P, _P, _I, _I]),
+    "elas_server_now_ms": (C.c_double, [_P]),
+    "elas_server_stats_get": (C.c_int, [_P, _P]),
+    "elas_server_destroy": (None, [_P]),
     "elas_probe_sad16": (C.c_int, [_I, _I, _I, _I, _P, _P]),
 }
 

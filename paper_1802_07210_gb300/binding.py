@@ -12,7 +12,8 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import BatchConfig, ElasError, Params, PipelineStats, as_params, check, lib, np_ptr, params  # noqa: F401
+from ._lib import (BatchConfig, ElasError, Params, PipelineStats, ServerConfig, ServerResult, ServerStats,  # noqa: F401
+                   as_params, check, lib, np_ptr, params)
 
 
 def _stream(stream=None):
@@ -328,6 +329,74 @@ class Batch:
         if self._h:
             lib().elas_batch_destroy(self._h)
             self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owner of an ``elas_server`` handle: requests with host buffers are
+    queued with ``submit`` and their results collected with ``poll``."""
+
+    def __init__(self, lanes=None, max_wave=None, max_slots=None, plain=False, hbm_budget_bytes=None,
+                 hbm_reserve_bytes=None):
+        cfg = ServerConfig()
+        check(lib().elas_server_config_default(C.byref(cfg)))
+        for k, v in dict(lanes=lanes, max_wave=max_wave, max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes,
+                         hbm_reserve_bytes=hbm_reserve_bytes).items():
+            if v is not None:
+                setattr(cfg, k, int(v))
+        cfg.plain = 1 if plain else 0
+        self._h = C.c_void_p()
+        self._keep = {}  # request id -> buffers that must outlive the request
+        check(lib().elas_server_create(C.byref(cfg), C.byref(self._h)))
+
+    def submit(self, rid, imgL, imgR, dL, prm=None, post=None):
+        """imgL/imgR: host uint8 tensors [h, w]; dL: host int16 [h, w];
+        post: host float32 [h, w] or None.  Pinned tensors copy fastest."""
+        prm = as_params(prm)
+        h, w = imgL.shape
+        for t, dt, name in ((imgL, torch.uint8, "imgL"), (imgR, torch.uint8, "imgR"), (dL, torch.int16, "dL"),
+                            (post, torch.float32, "post")):
+            if t is None:
+                continue
+            if t.is_cuda or t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != (h, w):
+                raise TypeError("%s must be a contiguous host %s tensor [%d, %d]" % (name, dt, h, w))
+        check(lib().elas_server_submit(self._h, int(rid), w, h, C.byref(prm), C.c_void_p(imgL.data_ptr()),
+                                       C.c_void_p(imgR.data_ptr()), C.c_void_p(dL.data_ptr()),
+                                       None if post is None else C.c_void_p(post.data_ptr())))
+        self._keep[int(rid)] = (imgL, imgR, dL, post)
+
+    def poll(self, max_results=256, timeout_ms=0):
+        buf = (ServerResult * max_results)()
+        k = lib().elas_server_poll(self._h, buf, max_results, int(timeout_ms))
+        if k < 0:
+            raise ElasError(1, "poll")
+        out = []
+        for i in range(k):
+            r = buf[i]
+            self._keep.pop(int(r.id), None)
+            out.append(dict(id=int(r.id), status=int(r.status), n_support=int(r.n_support),
+                            wave_size=int(r.wave_size), t_submit_ms=r.t_submit_ms, t_start_ms=r.t_start_ms,
+                            t_done_ms=r.t_done_ms))
+        return out
+
+    def now_ms(self):
+        return float(lib().elas_server_now_ms(self._h))
+
+    def stats(self):
+        st = ServerStats()
+        check(lib().elas_server_stats_get(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().elas_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -100,7 +100,7 @@ elas_status SlotPool::wait_mirror() {
     return ELAS_OK;
 }
 
-elas_status SlotPool::add(int w, int h, const elas_params *p, int *id) {
+elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStream_t alloc_stream) {
     elas_status s = check_params(p, w, h);
     if (s != ELAS_OK) return s;
     if (w < p->candidate_stepsize || h < p->candidate_stepsize)
@@ -121,7 +121,10 @@ elas_status SlotPool::add(int w, int h, const elas_params *p, int *id) {
     sl.nc = (w / p->candidate_stepsize) * (h / p->candidate_stepsize);
     sl.tri_cap = 2 * sl.nc + 8;
     const Layout need = layout(nullptr, w, h, p);
-    if (cudaMalloc(reinterpret_cast<void **>(&sl.mem), need.bytes) != cudaSuccess) {
+    sl.async_mem = alloc_stream != nullptr;
+    const cudaError_t ae = alloc_stream ? cudaMallocAsync(reinterpret_cast<void **>(&sl.mem), need.bytes, alloc_stream)
+                                        : cudaMalloc(reinterpret_cast<void **>(&sl.mem), need.bytes);
+    if (ae != cudaSuccess) {
         cudaGetLastError();
         sl.mem = nullptr;
         return fail(ELAS_ERR_NO_MEMORY, "slot of %zu bytes for %dx%d", need.bytes, w, h);
@@ -161,11 +164,14 @@ elas_status SlotPool::add(int w, int h, const elas_params *p, int *id) {
     return ELAS_OK;
 }
 
-void SlotPool::remove(int id) {
+void SlotPool::remove(int id, cudaStream_t free_stream) {
     if (id < 0 || id >= (int)slots_.size() || !slots_[id].used) return;
     Slot &sl = slots_[id];
     // the caller guarantees that no launch on this slot is still running
-    cudaFree(sl.mem);
+    if (sl.async_mem && free_stream)
+        cudaFreeAsync(sl.mem, free_stream);
+    else
+        cudaFree(sl.mem);
     bytes_in_use_ -= sl.bytes;
     sl = Slot();
 }
@@ -272,9 +278,9 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     return ELAS_OK;
 }
 
-elas_status SlotPool::fetch_counters(cudaStream_t st) {
-    if (cudaMemcpyAsync(h_counters_, dev_counters_, sizeof(int32_t) * 4 * slots_.size(), cudaMemcpyDeviceToHost,
-                        st) != cudaSuccess)
+elas_status SlotPool::fetch_counters(cudaStream_t st, int32_t *dst) {
+    if (cudaMemcpyAsync(dst ? dst : h_counters_, dev_counters_, sizeof(int32_t) * 4 * slots_.size(),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return launch_status("counters to host");
     return ELAS_OK;
 }

@@ -53,6 +53,7 @@ struct Slot {
     int16_t *io_dL = nullptr, *io_dR = nullptr;
     float *io_post = nullptr;
     bool post_on = false;
+    bool async_mem = false;  // memory from the stream-ordered allocator
 };
 
 // Per-stage event marks of a wave (for the tuner); NULL entries are skipped.
@@ -70,8 +71,11 @@ class SlotPool {
     elas_status init(int max_slots);
     // Device bytes a slot of this shape takes.
     static size_t slot_bytes(int w, int h, const elas_params *p);
-    elas_status add(int w, int h, const elas_params *p, int *id);
-    void remove(int id);
+    // alloc_stream != NULL: the slot's memory comes from the stream-ordered
+    // allocator on that stream (no device-wide synchronisation), and remove
+    // returns it on free_stream the same way.
+    elas_status add(int w, int h, const elas_params *p, int *id, cudaStream_t alloc_stream = nullptr);
+    void remove(int id, cudaStream_t free_stream = nullptr);
     // Points the slot's records at these inputs and outputs; NULL images or
     // dL select the internal buffers, NULL dR the internal right map;
     // post_on with a NULL post selects the internal float map.
@@ -82,8 +86,9 @@ class SlotPool {
     // The whole path for the slots ids[0..n-1]; counter = one device int.
     elas_status launch(const int *ids, int n, const Knobs &k, cudaStream_t st, int32_t *counter,
                        const StageMarks *marks = nullptr);
-    // Counters of every slot to pinned host memory (after launch, same stream).
-    elas_status fetch_counters(cudaStream_t st);
+    // Counters of every slot to pinned host memory (after launch, same
+    // stream): to the pool's array, or to dst (capacity() * 4 ints, pinned).
+    elas_status fetch_counters(cudaStream_t st, int32_t *dst = nullptr);
     const int32_t *host_counters(int id) const { return h_counters_ + 4 * id; }
 
     Slot &operator[](int id) { return slots_[id]; }

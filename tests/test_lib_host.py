@@ -50,6 +50,36 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.elas_triangulate(None, -1, 0, None, 0, C.byref(nt)) == 1
 
 
+def test_batch_and_server_configs_are_checked_on_the_host():
+    """Shape and configuration errors are reported before any device call."""
+    L = _lib.lib()
+    out = C.c_void_p()
+    w = (C.c_int32 * 1)(64)
+    h = (C.c_int32 * 1)(48)
+    prm = (_lib.Params * 1)(_lib.params())
+    assert L.elas_batch_create(0, w, h, prm, C.byref(out)) == 1 and not out.value
+    assert L.elas_batch_create(300, w, h, prm, C.byref(out)) == 1
+    assert L.elas_batch_create(1, None, h, prm, C.byref(out)) == 1
+    cfg = _lib.ServerConfig()
+    assert L.elas_server_config_default(C.byref(cfg)) == 0
+    assert 1 <= cfg.lanes <= 8 and 1 <= cfg.max_wave <= 256 and cfg.plain == 0
+    for field, bad in (("lanes", 0), ("lanes", 9), ("max_wave", 0), ("max_wave", 257), ("max_slots", 0)):
+        c = _lib.ServerConfig()
+        L.elas_server_config_default(C.byref(c))
+        setattr(c, field, bad)
+        assert L.elas_server_create(C.byref(c), C.byref(out)) == 1, field
+        assert field.encode() in L.elas_last_error()
+    # slot sizes: grow with the image and the disparity range; 0 when invalid
+    p64, p256 = _lib.params(disp_max=63), _lib.params(disp_max=255)
+    s1 = L.elas_slot_device_bytes(320, 240, C.byref(p64))
+    s2 = L.elas_slot_device_bytes(640, 480, C.byref(p64))
+    s3 = L.elas_slot_device_bytes(640, 480, C.byref(p256))
+    assert 0 < s1 < s2 < s3
+    assert s2 >= 640 * 480 * 36  # two descriptor planes alone are 32 bytes a pixel
+    assert L.elas_slot_device_bytes(3, 3, C.byref(p64)) == 0
+    assert L.elas_slot_device_bytes(640, 480, C.byref(_lib.params(disp_max=5000))) == 0
+
+
 def _canon(t):
     return sorted(tuple(int(v) for v in np.roll(r, -int(np.argmin(r)))) for r in np.asarray(t).reshape(-1, 3))
 
