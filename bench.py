@@ -1,13 +1,29 @@
-"""Throughput of the ELAS path on GB300: Mpix/s and pairs/s at 640x480 with
-256 disparities (one stereo pair per step, the whole path: descriptors,
-support points, host triangulation, plane prior, dense matching, LR check,
-post-processing).
+"""Throughput and latency of the ELAS path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  N > 1 runs N independent replicas, one per
-GPU (pairs are independent; there is no collective on the data path).
-``--impl reference`` times the CPU oracle on the host cores instead.
+The JSON line's value is Mpix/s of the plain one-pair path on 640x480 pairs
+with 256 disparities: one pair per step, the whole path on the GPU
+(descriptors, support points, triangulation, plane prior, dense matching,
+LR check, post-processing), inputs resident in HBM, L2 flushed before every
+step.  The same line carries:
+  e2e          the same metric through the host-buffer call (copies timed);
+  roofline     the dense argmin kernel (one launch covers both reference
+               images) against the measured SAD16 ceiling, timed by events
+               inside the timed steps;
+  batch        64 pairs of 1242x375 with 256 disparities in one batched wave
+               (one launch per kernel for all pairs, CUDA graph, tuned tile
+               shapes) against 64 runs of the plain path, with the batched
+               dense kernel's roofline;
+  mixed_batch  128 pairs of mixed sizes and disparity ranges in one wave
+               against 128 plain runs;
+  serving      8 simulated cameras with Poisson arrivals (600 pairs/s in
+               total): the continuous-batching server against the plain
+               per-pair loop, p50/p99 latency and pairs/s;
+  cpu_baseline the oracle on the host cores.
+N > 1 runs N independent replicas, one per GPU (pairs are independent; no
+collective on the data path); the extra sections run on rank 0.
+``--impl reference`` times the CPU oracle instead.
 """
 import argparse
 import json
@@ -27,7 +43,16 @@ from paper_1802_07210_gb300 import synth  # noqa: E402
 METRIC = "Mpix/s & pairs/s at 640x480 D=256; p50/p99 served latency vs per-pair path"
 WORKLOADS = {"vga_640": (synth.VGA_640, 2), "small_320": (synth.SMALL_320, 1),
              "kitti_1242": (synth.KITTI_1242, 3)}
-KERNELS_PER_STEP = 11  # descriptor 1, support 4, prior binning 1, dense 1, LR 1, post 4
+# kernels of one plain step: descriptors 1; support 4 (match, consistency,
+# redundancy + grids, compaction); triangulation 10 (points, cell scan,
+# scatter, dedup, group pass, warp pass, CTA pass, triangle scan, emit, emit
+# big); plane prior 2 (raster, big triangles); dense 1; LR 1; post-processing
+# 4 (gap rows, gap columns, mean rows, mean columns) or 1 (copy)
+KERNELS_PER_STEP = {True: 23, False: 20}
+STAGES = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")
+# bytes a dense launch must move at least: both descriptor images read once
+# (32 B/px), the two prior maps read (4 B/px), the two maps written (4 B/px)
+DENSE_MIN_BYTES_PER_PX = 40
 
 
 def _peaks():
@@ -148,6 +173,187 @@ def run_reference(args, wl, cfg):
     print(json.dumps(line), flush=True)
 
 
+def _timed(torch, stream, flush, fn, steps):
+    """Device ms of each of `steps` calls of fn(i), L2 flushed before each."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        fn(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def pair_dense_evals(B, torch, wl, L, R, dev):
+    """Algorithmic candidate evaluations of the dense step for one pair (the
+    intermediates come from the library's own calls; host triangulation)."""
+    prm = B.as_params(wl.params)
+    tL, tR = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
+    descL, descR = B.elas_descriptors(tL, tR)
+    sp = B.elas_support_points(descL, descR, prm)
+    torch.cuda.synchronize()
+    n = int(sp["count"].item())
+    lst_h = sp["list"][:n].cpu().numpy()
+    triL = torch.from_numpy(B.elas_triangulate(lst_h, False)).to(dev)
+    triR = torch.from_numpy(B.elas_triangulate(lst_h, True)).to(dev)
+    lst = sp["list"][:max(n, 1)].contiguous()
+    h, w = L.shape
+    dpL = B.elas_plane_prior(lst, triL, w, h, prm, False)
+    dpR = B.elas_plane_prior(lst, triR, w, h, prm, True)
+    work = dict(descL=descL.cpu().numpy(), descR=descR.cpu().numpy(), dpL=dpL.cpu().numpy(),
+                dpR=dpR.cpu().numpy(), gridL=sp["grid_L"].cpu().numpy(), gridR=sp["grid_R"].cpu().numpy())
+    return dense_work(work, prm, w, h)
+
+
+def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad):
+    """64 x 1242x375 D=256 through one batched wave vs the plain path."""
+    wl, cfg = synth.KITTI_1242, 3
+    w, h = wl.spec.w, wl.spec.h
+    pool = [synth.workload_pair(wl, 500 + i, cfg)[:2] for i in range(distinct)]
+    imgL = [torch.from_numpy(pool[i % distinct][0]).to(dev) for i in range(npairs)]
+    imgR = [torch.from_numpy(pool[i % distinct][1]).to(dev) for i in range(npairs)]
+    dL = [torch.empty((h, w), dtype=torch.int16, device=dev) for _ in range(npairs)]
+    dR = [torch.empty_like(t) for t in dL]
+    b = B.Batch([(w, h)] * npairs, wl.params)
+    tuned = b.tune(imgL, imgR, dL)
+    for _ in range(3):
+        b.run(imgL, imgR, dL, dR)
+    ms = _timed(torch, stream, flush, lambda i: b.run(imgL, imgR, dL, dR), steps)
+    prof = [b.profile() for _ in range(3)]
+    stage = {k: float(np.median([p[k] for p in prof])) for k in prof[0]}
+    nsup = b.stats()["n_support"]
+    b.close()
+    pl = B.Pipeline(w, h, wl.params)
+    for i in range(npairs):
+        pl.run(imgL[i], imgR[i], dL[i], dR[i])
+    ms_plain = _timed(torch, stream, flush, lambda i: [pl.run(imgL[k], imgR[k], dL[k], dR[k]) for k in range(npairs)],
+                      max(3, steps // 3))
+    pl.close()
+    evals = sum(pair_dense_evals(B, torch, wl, L, R, dev) for L, R in pool) * (npairs // distinct)
+    evals += sum(pair_dense_evals(B, torch, wl, *pool[i], dev) for i in range(npairs % distinct))
+    t_b, t_p = float(np.mean(ms)), float(np.mean(ms_plain))
+    ach = evals / (stage["dense_argmin"] * 1e-3) / 1e9
+    return {"workload": "%d x %s" % (npairs, wl.name), "pairs": npairs, "distinct_pairs": distinct,
+            "ms_per_batch": t_b, "pairs_per_s": npairs / (t_b * 1e-3), "mpix_per_s": npairs * w * h / (t_b * 1e-3) / 1e6,
+            "plain_ms_per_batch": t_p, "plain_pairs_per_s": npairs / (t_p * 1e-3),
+            "speedup_vs_plain": t_p / t_b, "tuned": tuned, "stages_ms": stage, "support_points_first": nsup[:4],
+            "launches_per_batch": 21, "graph": True,
+            "l2": "flushed before every timed batch",
+            "roofline_dense": {"kernel": "cell_kernel_b (dense argmin, every pair and both reference images in one launch)",
+                               "bound": "alu", "achieved": ach, "peak": peak_gsad, "unit": "G SAD16/s",
+                               "frac": ach / peak_gsad, "algorithmic_evals": evals,
+                               "time_source": "CUDA events around the launch in an eager run of the same batch"}}
+
+
+def run_mixed_section(B, torch, dev, stream, flush, steps, npairs):
+    """128 pairs of mixed sizes and disparity ranges: one wave vs plain runs."""
+    spec = synth.mixed_batch(npairs, 4)
+    distinct = {}
+    for wl, _ in spec:
+        distinct.setdefault(wl.name, wl)
+    pool = {name: synth.workload_pair(wl, 700, 4)[:2] for name, wl in distinct.items()}
+    imgL = [torch.from_numpy(pool[wl.name][0]).to(dev) for wl, _ in spec]
+    imgR = [torch.from_numpy(pool[wl.name][1]).to(dev) for wl, _ in spec]
+    dL = [torch.empty(t.shape, dtype=torch.int16, device=dev) for t in imgL]
+    dR = [torch.empty_like(t) for t in dL]
+    shapes = [(wl.spec.w, wl.spec.h) for wl, _ in spec]
+    b = B.Batch(shapes, [wl.params for wl, _ in spec])
+    tuned = b.tune(imgL, imgR, dL)
+    for _ in range(3):
+        b.run(imgL, imgR, dL, dR)
+    ms = _timed(torch, stream, flush, lambda i: b.run(imgL, imgR, dL, dR), steps)
+    b.close()
+    pls = {name: B.Pipeline(wl.spec.w, wl.spec.h, wl.params) for name, wl in distinct.items()}
+    names = [wl.name for wl, _ in spec]
+
+    def plain(_):
+        for k in range(npairs):
+            pls[names[k]].run(imgL[k], imgR[k], dL[k], dR[k])
+    plain(0)
+    ms_plain = _timed(torch, stream, flush, plain, max(3, steps // 3))
+    for p in pls.values():
+        p.close()
+    px = sum(w * h for w, h in shapes)
+    t_b, t_p = float(np.mean(ms)), float(np.mean(ms_plain))
+    return {"workload": "%d mixed pairs (sizes %s, D in %s)" % (npairs, synth.MIXED_SIZES, synth.MIXED_D),
+            "distinct_pairs": len(pool), "megapixels": px / 1e6, "ms_per_batch": t_b,
+            "pairs_per_s": npairs / (t_b * 1e-3), "mpix_per_s": px / (t_b * 1e-3) / 1e6,
+            "plain_ms_per_batch": t_p, "plain_pairs_per_s": npairs / (t_p * 1e-3), "speedup_vs_plain": t_p / t_b,
+            "tuned": tuned, "l2": "flushed before every timed batch"}
+
+
+def run_serve_section(B, torch, seconds, rate_per_camera=75.0, seed=5):
+    """8 cameras (2 x 640x480 D=128, 4 x 1242x375 D=256, 2 x 1920x1080 D=256),
+    Poisson arrivals, host buffers in and out: the continuous-batching server
+    against the plain per-pair loop on the same arrival schedule."""
+    cams = [synth.scaled_workload(640, 480, 128)] * 2 + [synth.KITTI_1242] * 4 + \
+        [synth.scaled_workload(1920, 1080, 256)] * 2
+    pool = {}
+    for wl in cams:
+        if wl.name not in pool:
+            pool[wl.name] = [tuple(torch.from_numpy(x).pin_memory() for x in synth.workload_pair(wl, k, 5)[:2])
+                             for k in range(2)]
+    rng = np.random.default_rng(seed)
+    arr = []
+    for ci in range(len(cams)):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / rate_per_camera)
+            if t >= seconds:
+                break
+            arr.append((t, ci))
+    arr.sort()
+
+    def run(plain):
+        srv = B.Server(plain=plain, lanes=3, max_wave=64)
+        ring = {ci: [torch.empty(pool[wl.name][0][0].shape, dtype=torch.int16).pin_memory() for _ in range(256)]
+                for ci, wl in enumerate(cams)}
+        for ci, wl in enumerate(cams):  # warm-up: creates the slots
+            srv.submit(10 ** 9 + ci, pool[wl.name][0][0], pool[wl.name][0][1], ring[ci][0], wl.params)
+        got = 0
+        while got < len(cams):
+            got += len(srv.poll(64, 100))
+        lat, done = [], 0
+        t0 = time.perf_counter()
+        for i, (ta, ci) in enumerate(arr):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= ta:
+                    break
+                for r in srv.poll(256, 0):
+                    lat.append(r["t_done_ms"] - r["t_submit_ms"])
+                    done += 1
+                if ta - now > 0.0005:
+                    time.sleep(min(ta - now - 0.0003, 0.002))
+            wl = cams[ci]
+            L, R = pool[wl.name][i % 2]
+            srv.submit(i, L, R, ring[ci][i % 256], wl.params)
+        while done < len(arr):
+            for r in srv.poll(256, 200):
+                lat.append(r["t_done_ms"] - r["t_submit_ms"])
+                done += 1
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        return {"pairs": int(len(lat)), "pairs_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "waves": int(st["waves"]),
+                "max_wave": int(st["max_wave_seen"]), "slots": int(st["slots_in_use"]),
+                "slot_gb": st["slot_bytes"] / 1e9}
+
+    out = {"cameras": "2x640x480 D=128, 4x1242x375 D=256, 2x1920x1080 D=256",
+           "arrivals": "Poisson, %.0f pairs/s per camera, %.0f pairs/s in total, seeded" % (rate_per_camera,
+                                                                                          rate_per_camera * len(cams)),
+           "seconds": seconds, "requests": len(arr),
+           "latency": "submit to outputs on the host (host copies included)",
+           "continuous_batching": run(False), "plain_per_pair": run(True)}
+    cb, pp = out["continuous_batching"], out["plain_per_pair"]
+    out["p50_ratio_plain_over_batched"] = pp["p50_ms"] / cb["p50_ms"]
+    out["p99_ratio_plain_over_batched"] = pp["p99_ms"] / cb["p99_ms"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -157,6 +363,11 @@ def main():
     ap.add_argument("--workload", default="vga_640", choices=sorted(WORKLOADS))
     ap.add_argument("--pool", type=int, default=4, help="distinct pairs cycled through")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=64)
+    ap.add_argument("--batch-distinct", type=int, default=8)
+    ap.add_argument("--mixed-pairs", type=int, default=128)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-extra", action="store_true", help="only the plain-path line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl, cfg = WORKLOADS[args.workload]
@@ -177,6 +388,7 @@ def main():
     pool = [synth.workload_pair(wl, rank * 1000 + i, cfg) for i in range(args.pool)]
     imgs = [(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)) for L, R, _ in pool]
     pl = B.Pipeline(w, h, wl.params)
+    pl.set_profiling(True)
     dL = torch.empty((h, w), dtype=torch.int16, device=dev)
     dR = torch.empty_like(dL)
     post = torch.empty((h, w), dtype=torch.float32, device=dev) if wl.postprocess else None
@@ -202,9 +414,9 @@ def main():
         step(i)
     torch.cuda.synchronize()
 
-    # ---- device-resident throughput ------------------------------------
+    # ---- device-resident throughput of the plain path -------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    tri_ms = []
+    stage_ms = []
     clocks = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -215,7 +427,7 @@ def main():
         ev[i][0].record(stream)
         step(i)
         ev[i][1].record(stream)
-        tri_ms.append(pl.stats()["triangulate_ms"])
+        stage_ms.append(pl.stats()["stage_ms"])  # events recorded by the library on this stream
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -228,6 +440,7 @@ def main():
     ms_step = total_ms / args.steps
     value = ws * args.steps * px / (total_ms / 1e3) / 1e6
     st = pl.stats()
+    stages = {k: float(np.mean([s[k] for s in stage_ms])) for k in STAGES}
 
     # ---- end to end through the host-buffer call -----------------------
     hL = [torch.from_numpy(L).pin_memory() for L, _, _ in pool]
@@ -249,93 +462,55 @@ def main():
     e2e_ms = float(t_e.item())
     e2e = {"value": ws * args.steps * px / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
            "h2d_bytes_per_step": 2 * px, "d2h_bytes_per_step": 2 * px + (4 * px if wl.postprocess else 0),
-           "ms_per_step": e2e_ms / args.steps}
+           "ms_per_step": e2e_ms / args.steps, "call": "elas_pipeline_run_host (pinned host buffers)"}
 
-    # ---- per-stage kernel times (C-ABI calls bracketed by events) -------
-    stages, work = stage_times(B, torch, wl, pool[0], dev, stream, flush, reps=max(5, min(args.steps, 20)))
+    # ---- roofline of the dense argmin kernel -----------------------------
     hbm_gbs, peak_kind = _peaks()
-    prm = B.as_params(wl.params)
-    evals = dense_work(work, prm, w, h)
     probe = alu_peak(B, torch, dev, stream)
-    t_dense = stages["dense_match_ms"]
-    achieved = evals / (t_dense * 1e-3) / 1e9
     peak = probe[0] / 1e9
-    # algorithmic HBM bytes of the same launch: both descriptor images read
-    # once (32 B/px), grid vectors and meshes (small), two int16 maps written
-    dense_bytes = 2 * (16 + 16 + 2) * px
-    roof = {"kernel": "cell_kernel<kDenseFused> (prior + dense argmin, both reference images)",
+    evals_pool = [pair_dense_evals(B, torch, wl, L, R, dev) for L, R, _ in pool]
+    evals = float(np.mean([evals_pool[i % len(pool)] for i in range(args.steps)]))
+    t_dense = stages["dense_argmin"]
+    achieved = evals / (t_dense * 1e-3) / 1e9
+    dense_bytes = DENSE_MIN_BYTES_PER_PX * px
+    roof = {"kernel": "cell_kernel (dense argmin, both reference images in one launch)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SAD16/s", "frac": achieved / peak,
-            "traffic": None, "algorithmic_evals": evals,
+            "traffic": None, "algorithmic_evals_per_launch": evals,
+            "time": "mean of CUDA events around the launch, recorded by the library inside every timed step",
             "peak_source": "measured: probe kernel running the same SAD16 sequence on registers over all SMs",
             "probe_variants_gsad16": {str(k): v / 1e9 for k, v in probe.items()},
             "hbm": {"achieved_gbs": dense_bytes / (t_dense * 1e-3) / 1e9, "peak_gbs": hbm_gbs,
                     "frac": dense_bytes / (t_dense * 1e-3) / 1e9 / hbm_gbs,
+                    "min_bytes_per_launch": dense_bytes,
                     "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_kind}}
+
+    extra = {}
+    if rank == 0 and not args.skip_extra:
+        extra["batch"] = run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
+                                           args.batch_pairs, args.batch_distinct, peak)
+        extra["mixed_batch"] = run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
+                                                 args.mixed_pairs)
+        extra["serving"] = run_serve_section(B, torch, args.serve_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": {"workload": wl.name, "w": w, "h": h, "disp_max": wl.disp_max,
-                           "pairs_per_step": 1, "pool": args.pool, "path": "plain one-pair path",
+                           "pairs_per_step": 1, "pool": args.pool, "path": "plain one-pair path (elas_pipeline_run)",
+                           "triangulation": "GPU",
                            "l2": "flushed before every timed step (256 MB write, then 256 MB read so no dirty lines remain)"},
                 "pairs_per_s": ws * args.steps / (total_ms / 1e3),
-                "triangulate_ms_median": float(np.median(tri_ms)),
                 "support_points": st["n_support"], "triangles": [st["n_tri_left"], st["n_tri_right"]],
                 "stages_ms": stages, "clocks": clk, "e2e": e2e,
-                "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof}
+                "gpu_launches": KERNELS_PER_STEP[bool(wl.postprocess)] * args.steps, "roofline": roof}
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, cfg)
         print(json.dumps(line), flush=True)
     if ws > 1:
+        dist.barrier()
         dist.destroy_process_group()
-
-
-def stage_times(B, torch, wl, pair, dev, stream, flush, reps=10):
-    """Median device time of each stage's C-ABI call on one pair, plus the
-    inputs needed to count the dense matcher's algorithmic work."""
-    L, R, _ = pair
-    prm = B.as_params(wl.params)
-    tL, tR = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
-    descL, descR = B.elas_descriptors(tL, tR)
-    sp = B.elas_support_points(descL, descR, prm)
-    torch.cuda.synchronize()
-    n = int(sp["count"].item())
-    lst_h = sp["list"][:n].cpu().numpy()
-    triL = torch.from_numpy(B.elas_triangulate(lst_h, False)).to(dev)
-    triR = torch.from_numpy(B.elas_triangulate(lst_h, True)).to(dev)
-    lst = sp["list"][:max(n, 1)].contiguous()
-    h, w = L.shape
-    dpL = B.elas_plane_prior(lst, triL, w, h, prm, False)
-    dpR = B.elas_plane_prior(lst, triR, w, h, prm, True)
-    dl, dr = B.elas_dense_match(descL, descR, prm, lst, n, triL, triR, sp["grid_L"], sp["grid_R"])
-    dl2, dr2 = dl.clone(), dr.clone()
-    calls = {
-        "descriptors_ms": lambda: B.elas_descriptors(tL, tR),
-        "support_ms": lambda: B.elas_support_points(descL, descR, prm),
-        "dense_match_ms": lambda: B.elas_dense_match(descL, descR, prm, lst, n, triL, triR, sp["grid_L"],
-                                                     sp["grid_R"]),
-        "plane_prior_L_ms": lambda: B.elas_plane_prior(lst, triL, w, h, prm, False),
-        "dense_argmin_L_ms": lambda: B.elas_dense_argmin(descL, descR, prm, dpL, sp["grid_L"], False),
-        "lr_check_ms": lambda: B.elas_lr_check(dl2, dr2, prm.lr_threshold, masks=False),
-        "postprocess_ms": lambda: B.elas_postprocess(dl, prm),
-    }
-    out = {}
-    for name, fn in calls.items():
-        fn()
-        ts = []
-        for i in range(reps):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        out[name] = float(np.median(ts))
-    work = dict(descL=descL.cpu().numpy(), descR=descR.cpu().numpy(), dpL=dpL.cpu().numpy(),
-                dpR=dpR.cpu().numpy(), gridL=sp["grid_L"].cpu().numpy(), gridR=sp["grid_R"].cpu().numpy())
-    return out, work
 
 
 def dense_work(work, prm, w, h):

@@ -310,6 +310,10 @@ typedef struct {
     int32_t n_tri_right;   /* triangles, right coordinates               */
     double  triangulate_ms;/* host wall time of both triangulations (host
                               triangulation only, else 0)               */
+    float   stage_ms[6];   /* with profiling on and GPU triangulation:
+                              device ms of descriptors, support points,
+                              triangulation, plane prior, dense argmin,
+                              LR check + post-processing; else 0        */
 } elas_pipeline_stats;
 
 elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_params *p, elas_pipeline **out);
@@ -323,7 +327,11 @@ elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const
  * on_gpu = 0 copies the support list to the host and runs elas_triangulate
  * (left and right meshes on two threads).  Both give identical meshes. */
 elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu);
-/* Counts of the last pair; waits for the pipeline's last stream. */
+/* on = 1: every run records events between its stages (GPU triangulation
+ * only) and elas_pipeline_stats_get reports the stage times. */
+elas_status elas_pipeline_set_profiling(elas_pipeline *pl, int32_t on);
+/* Counts (and stage times) of the last pair; waits for the pipeline's last
+ * stream. */
 elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st);
 void elas_pipeline_destroy(elas_pipeline *pl);
 
@@ -374,6 +382,11 @@ elas_status elas_batch_stats(elas_batch *b, int32_t *n_support, int32_t *n_tri_l
 elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL, const uint8_t *const *imgR,
                             const int32_t *pitch, int16_t *const *dL, elas_stream stream,
                             elas_batch_config *chosen);
+/* One eager run (with the buffers of the last elas_batch_run) bracketed by
+ * events: stage_ms[0..5] = descriptors, support points, triangulation,
+ * plane prior, dense argmin, LR check + post-processing (device ms).
+ * Returns when done. */
+elas_status elas_batch_profile(elas_batch *b, elas_stream stream, float *stage_ms);
 /* Device bytes the batch holds (slots, tables and scratch). */
 size_t elas_batch_device_bytes(const elas_batch *b);
 void elas_batch_destroy(elas_batch *b);

@@ -47,7 +47,7 @@ class Params(C.Structure):
 
 class PipelineStats(C.Structure):
     _fields_ = [("n_support", C.c_int32), ("n_tri_left", C.c_int32),
-                ("n_tri_right", C.c_int32), ("triangulate_ms", C.c_double)]
+                ("n_tri_right", C.c_int32), ("triangulate_ms", C.c_double), ("stage_ms", C.c_float * 6)]
 
 
 class BatchConfig(C.Structure):
@@ -99,6 +99,7 @@ SIGNATURES = {
     "elas_pipeline_run": (C.c_int, [_P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_pipeline_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "elas_pipeline_set_triangulation": (C.c_int, [_P, _I]),
+    "elas_pipeline_set_profiling": (C.c_int, [_P, _I]),
     "elas_pipeline_stats_get": (C.c_int, [_P, _P]),
     "elas_pipeline_destroy": (None, [_P]),
     "elas_batch_create": (C.c_int, [_I, _P, _P, _P, _P]),
@@ -108,6 +109,7 @@ SIGNATURES = {
     "elas_batch_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "elas_batch_stats": (C.c_int, [_P, _P, _P, _P]),
     "elas_batch_tune": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "elas_batch_profile": (C.c_int, [_P, _P, _P]),
     "elas_batch_device_bytes": (_Z, [_P]),
     "elas_batch_destroy": (None, [_P]),
     "elas_server_config_default": (C.c_int, [_P]),

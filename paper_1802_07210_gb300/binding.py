@@ -209,11 +209,15 @@ class Pipeline:
                                            hp(dL, torch.int16, "dL"), hp(dR, torch.int16, "dR"),
                                            hp(post, torch.float32, "post"), _stream(stream)))
 
+    def set_profiling(self, on=True):
+        check(lib().elas_pipeline_set_profiling(self._h, int(bool(on))))
+
     def stats(self):
         st = PipelineStats()
         check(lib().elas_pipeline_stats_get(self._h, C.byref(st)))
+        names = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")
         return dict(n_support=st.n_support, n_tri_left=st.n_tri_left, n_tri_right=st.n_tri_right,
-                    triangulate_ms=st.triangulate_ms)
+                    triangulate_ms=st.triangulate_ms, stage_ms={k: float(v) for k, v in zip(names, st.stage_ms)})
 
     def close(self):
         if self._h:
@@ -321,6 +325,13 @@ class Batch:
         check(lib().elas_batch_tune(self._h, aL, aR, None, aD, _stream(stream), C.byref(cfg)))
         return dict(desc_tile_rows=cfg.desc_tile_rows, support_warps=cfg.support_warps,
                     dense_threads_per_pixel=cfg.dense_threads_per_pixel, use_graph=cfg.use_graph)
+
+    def profile(self, stream=None):
+        """Device ms of each stage of one eager run on the last-bound buffers."""
+        ms = (C.c_float * 6)()
+        check(lib().elas_batch_profile(self._h, _stream(stream), ms))
+        names = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")
+        return {k: float(v) for k, v in zip(names, ms)}
 
     def device_bytes(self):
         return int(lib().elas_batch_device_bytes(self._h))

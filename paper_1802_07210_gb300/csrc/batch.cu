@@ -270,7 +270,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
         return launch_status("tune fork");
     if ((s = b->pool.upload(b->work)) != ELAS_OK) return s;
     StageMarks mk;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < kStageMarks; ++i)
         if (cudaEventCreate(&mk.ev[i]) != cudaSuccess) {
             for (int j = 0; j < i; ++j) cudaEventDestroy(mk.ev[j]);
             return launch_status("tune events");
@@ -282,7 +282,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
         int values[3];
     };
     Knobs k = b->knobs;
-    Axis axes[3] = {{&k.desc_rows, 0, {4, 8, 16}}, {&k.support_warps, 1, {4, 8, 16}}, {&k.dense_tpp, 3, {1, 2, 4}}};
+    Axis axes[3] = {{&k.desc_rows, 0, {4, 8, 16}}, {&k.support_warps, 1, {4, 8, 16}}, {&k.dense_tpp, 4, {1, 2, 4}}};
     const int reps = 3;
     for (Axis &ax : axes) {
         float best_ms = 1e30f;
@@ -293,7 +293,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
             for (int r = 0; r <= reps && s == ELAS_OK; ++r) {  // r = 0 warms up
                 s = b->pool.launch(b->ids.data(), (int)b->ids.size(), k, b->work, b->counter, &mk);
                 if (s != ELAS_OK) break;
-                if (cudaEventSynchronize(mk.ev[5]) != cudaSuccess) {
+                if (cudaEventSynchronize(mk.ev[kStageMarks - 1]) != cudaSuccess) {
                     s = launch_status("tune run");
                     break;
                 }
@@ -310,7 +310,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
         *ax.field = best_v;
         if (s != ELAS_OK) break;
     }
-    for (int i = 0; i < 6; ++i) cudaEventDestroy(mk.ev[i]);
+    for (int i = 0; i < kStageMarks; ++i) cudaEventDestroy(mk.ev[i]);
     if (s != ELAS_OK) return s;
     if (cudaEventRecord(b->ev_out, b->work) != cudaSuccess || cudaStreamWaitEvent(st, b->ev_out, 0) != cudaSuccess)
         return launch_status("tune join");
@@ -321,6 +321,36 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
     }
     if (chosen) elas_batch_get_config(b, chosen);
     return ELAS_OK;
+}
+
+extern "C" elas_status elas_batch_profile(elas_batch *b, elas_stream stream, float *stage_ms) {
+    if (!b || !stage_ms) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->ran) return fail(ELAS_ERR_INVALID_ARG, "run the batch once first");
+    cudaStream_t st = to_stream(stream);
+    StageMarks mk;
+    elas_status s = ELAS_OK;
+    int made = 0;
+    for (; made < kStageMarks; ++made)
+        if (cudaEventCreate(&mk.ev[made]) != cudaSuccess) {
+            s = launch_status("profile events");
+            break;
+        }
+    if (s == ELAS_OK && (cudaEventRecord(b->ev_in, st) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->work, b->ev_in, 0) != cudaSuccess))
+        s = launch_status("profile fork");
+    if (s == ELAS_OK) s = b->pool.upload(b->work);
+    if (s == ELAS_OK) s = wave(b, &mk);
+    if (s == ELAS_OK && cudaEventSynchronize(mk.ev[kStageMarks - 1]) != cudaSuccess) s = launch_status("profile run");
+    if (s == ELAS_OK)
+        for (int i = 0; i + 1 < kStageMarks; ++i) {
+            stage_ms[i] = 0.0f;
+            cudaEventElapsedTime(&stage_ms[i], mk.ev[i], mk.ev[i + 1]);
+        }
+    if (s == ELAS_OK && (cudaEventRecord(b->ev_out, b->work) != cudaSuccess ||
+                         cudaStreamWaitEvent(st, b->ev_out, 0) != cudaSuccess))
+        s = launch_status("profile join");
+    for (int i = 0; i < made; ++i) cudaEventDestroy(mk.ev[i]);
+    return s;
 }
 
 extern "C" size_t elas_batch_device_bytes(const elas_batch *b) {

@@ -256,15 +256,19 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long k) {
     return k;
 }
 
-// Circumdisc of (p, a, b) inside the disc of radius R around p:
-// |pa|^2 |pb|^2 |ab|^2 <= R^2 area2^2 (twice the circumradius <= R); the
-// operands are integers below 2^53, so the double products are exact.
+// Is the circle through p, a, b no wider than R (2r <= R, r its radius)?
+// With 4 r^2 = |pa|^2 |pb|^2 |ab|^2 / orient(p, a, b)^2 this is
+// |pa|^2 |pb|^2 |ab|^2 <= R^2 orient^2, in exact integer arithmetic.  A point
+// farther than R from p makes the diameter exceed R at once, so the products
+// only see points within R: below R^4 * 4 R^2 < 2^63 for R <= 1024.
 __device__ __forceinline__ bool dt_small_circle(const int4 &p, const int4 &a, const int4 &b, int R) {
-    const double pa = (double)(a.x - p.x) * (a.x - p.x) + (double)(a.y - p.y) * (a.y - p.y);
-    const double pb = (double)(b.x - p.x) * (b.x - p.x) + (double)(b.y - p.y) * (b.y - p.y);
-    const double ab = (double)(b.x - a.x) * (b.x - a.x) + (double)(b.y - a.y) * (b.y - a.y);
-    const double ar = (double)dt_orient(p.x, p.y, a.x, a.y, b.x, b.y);
-    return pa * pb * ab <= (double)R * R * ar * ar;
+    const int64_t R2 = (int64_t)R * R;
+    const int64_t pa = (int64_t)(a.x - p.x) * (a.x - p.x) + (int64_t)(a.y - p.y) * (a.y - p.y);
+    const int64_t pb = (int64_t)(b.x - p.x) * (b.x - p.x) + (int64_t)(b.y - p.y) * (b.y - p.y);
+    if (pa > R2 || pb > R2) return false;
+    const int64_t ab = (int64_t)(b.x - a.x) * (b.x - a.x) + (int64_t)(b.y - a.y) * (b.y - a.y);
+    const int64_t ar = dt_orient(p.x, p.y, a.x, a.y, b.x, b.y);
+    return pa * pb * ab <= R2 * ar * ar;
 }
 
 // Records triangle (p, a, b) if p owns it (lowest index).
@@ -324,14 +328,6 @@ constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (the radius-32 disc holds at most ~120 lattice points)
 constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
 constexpr int kDtListCapB = 640; // the radius-64 disc holds at most ~520 lattice points
-
-__device__ __forceinline__ bool dt_small_circle_exact(const int4 &p, const int4 &a, const int4 &b, int R) {
-    const int64_t pa = (int64_t)(a.x - p.x) * (a.x - p.x) + (int64_t)(a.y - p.y) * (a.y - p.y);
-    const int64_t pb = (int64_t)(b.x - p.x) * (b.x - p.x) + (int64_t)(b.y - p.y) * (b.y - p.y);
-    const int64_t ab = (int64_t)(b.x - a.x) * (b.x - a.x) + (int64_t)(b.y - a.y) * (b.y - a.y);
-    const int64_t ar = dt_orient(p.x, p.y, a.x, a.y, b.x, b.y);
-    return pa * pb * ab <= (int64_t)R * R * ar * ar;  // below 2^43 for R = 32
-}
 
 __device__ __forceinline__ int4 gshfl4(unsigned m, const int4 &v, int src) {
     return make_int4(__shfl_sync(m, v.x, src), __shfl_sync(m, v.y, src), __shfl_sync(m, v.z, src),
@@ -462,7 +458,7 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
                     e_l = cur;
                     break;
                 }
-                if (!dt_small_circle_exact(p, cur, best, R)) {
+                if (!dt_small_circle(p, cur, best, R)) {
                     certified = false;
                     break;
                 }
@@ -495,7 +491,7 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
                         e_r = cur;
                         break;
                     }
-                    if (!dt_small_circle_exact(p, best, cur, R)) {
+                    if (!dt_small_circle(p, best, cur, R)) {
                         certified = false;
                         break;
                     }
@@ -555,14 +551,16 @@ __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b(const Dt
     dt_pass1_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-// CTA pass: one CTA per star left by both group passes.  The points within
-// kDtRadius2 are cached in shared memory; every wrap step first takes the
+// CTA pass: one CTA per star left by the group passes.  The points within
+// kDtRadius1 are cached in shared memory; every wrap step first takes the
 // best cached candidate and keeps it when its circumdisc lies inside the
-// cached disc (then no other point can beat it); a step that does not fit
-// (large circle, no cached candidate on that side, or the cache overflowed)
-// scans the grid cells its disc or half-plane meets, which is exact.  So
-// every queued star comes out exact.
-constexpr int kDtRadius2 = 192;    // cache radius of the CTA pass
+// cached disc (then no other point can beat it); the first step that does
+// not fit refills the cache with the points within kDtRadius2, and a step
+// that fits neither (large circle, no cached candidate on that side, or the
+// cache overflowed) scans the grid cells its disc or half-plane meets, which
+// is exact.  So every queued star comes out exact.
+constexpr int kDtRadius1 = 96;     // first cache radius of the CTA pass
+constexpr int kDtRadius2 = 192;    // its second, when a step's circle does not fit the first
 constexpr int kDtCandCap2 = 3072;  // candidates cached per CTA (48 KB)
 constexpr int kDtMaxRows = 64;     // cell rows a radius-192 disc spans, with margin
 static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "the CTA pass's disc must fit the row table");
@@ -641,86 +639,91 @@ __device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, co
 // Exact step for edge (p, cur) on `side` without the radius limit.  Only
 // points strictly inside the closed circumdisc of (p, cur, bc) can beat the
 // cached best bc, and with no cached candidate only the open half-plane on
-// that side matters; so the CTA scans the grid cells that meet that region
-// (disc or half-plane, widened by 2 pixels and one cell, in double precision:
-// a superset), taking each cell row's cells as one contiguous range.
+// that side matters; so the CTA scans the grid cells that meet that region,
+// taking each cell row's cells as one contiguous range.  The region is
+// widened so that float rounding cannot lose a cell: the circle's centre
+// comes from exact integer numerators (one rounding each in the division),
+// its radius is padded by 4 pixels plus 1e-4 of itself, each cell row band
+// by 2 pixels and each x-range by a cell; a circle wider than 1e6 pixels is
+// replaced by its half-plane (the part of the disc beyond the chord p-cur
+// is then thinner than a pixel, and only that side's points are candidates).
 __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int4 &p, const int4 &cur, int side,
-                                     const int4 &bc, DtBlockShared &sh, int *r_start, int *r_pre) {
+                                     const int4 &bc, DtBlockShared &sh, int *r_start, int *r_len) {
     const int tid = threadIdx.x, nth = blockDim.x;
-    double ccx = 0, ccy = 0, rad = 0;
-    const bool disc = bc.w != 0;
-    if (disc) {
-        const double ax = cur.x - p.x, ay = cur.y - p.y, bx = bc.x - p.x, by = bc.y - p.y;
-        const double d = 2.0 * (ax * by - ay * bx);
-        const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
-        const double ux = (by * a2 - ay * b2) / d, uy = (ax * b2 - bx * a2) / d;
-        ccx = p.x + ux;
-        ccy = p.y + uy;
-        rad = sqrt(ux * ux + uy * uy) + 2.0;
+    float ccx = 0.0f, ccy = 0.0f, rad = 0.0f;
+    bool disc = false;
+    if (bc.w) {
+        const int64_t ax = cur.x - p.x, ay = cur.y - p.y, bx = bc.x - p.x, by = bc.y - p.y;
+        const int64_t d = 2 * (ax * by - ay * bx);  // nonzero: bc lies strictly on `side`
+        const int64_t a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+        const float fd = (float)d;
+        const float ux = (float)(by * a2 - ay * b2) / fd, uy = (float)(ax * b2 - bx * a2) / fd;
+        const float r = sqrtf(ux * ux + uy * uy);
+        if (r <= 1e6f) {
+            disc = true;
+            ccx = (float)p.x + ux;
+            ccy = (float)p.y + uy;
+            rad = r * 1.0001f + 4.0f;
+        }
     }
     // half-plane: side * ((cur.x-p.x)(y-p.y) - (cur.y-p.y)(x-p.x)) > 0
-    const double ex = cur.x - p.x, ey = cur.y - p.y;
+    const int ex = cur.x - p.x, ey = cur.y - p.y;
     for (int cy = tid; cy < a.gh; cy += nth) {
-        const double y0 = cy * kDtCell - 2.0, y1 = cy * kDtCell + kDtCell + 1.0;
-        double xlo = -1e30, xhi = 1e30;
+        const int y0 = cy * kDtCell - 2, y1 = cy * kDtCell + kDtCell + 1;
+        float xlo = -1e30f, xhi = 1e30f;
         bool any = true;
         if (disc) {
-            const double dy = ccy < y0 ? y0 - ccy : (ccy > y1 ? ccy - y1 : 0.0);
+            const float dy = ccy < (float)y0 ? (float)y0 - ccy : (ccy > (float)y1 ? ccy - (float)y1 : 0.0f);
             if (dy > rad) {
                 any = false;
             } else {
-                const double hc = sqrt(rad * rad - dy * dy) + 2.0;
+                const float hc = sqrtf(rad * rad - dy * dy) + 2.0f;
                 xlo = ccx - hc;
                 xhi = ccx + hc;
             }
-        } else if (ey != 0.0) {
-            // boundary x at the band's two edges; the admissible side of x
-            double xa = p.x + ex * (y0 - p.y) / ey, xb = p.x + ex * (y1 - p.y) / ey;
-            const double xm = xa < xb ? xa : xb, xM = xa < xb ? xb : xa;
+        } else if (ey != 0) {
+            // boundary x at the band's two edges (exact products, one rounding
+            // in each division); the admissible side of x
+            const float xa = (float)p.x + (float)(ex * (y0 - p.y)) / (float)ey;
+            const float xb = (float)p.x + (float)(ex * (y1 - p.y)) / (float)ey;
+            const float xm = fminf(xa, xb), xM = fmaxf(xa, xb);
             // side*(ex*(y-py) - ey*(x-px)) > 0  <=>  x < boundary if side*ey > 0
-            if (side * ey > 0) xhi = xM + 2.0; else xlo = xm - 2.0;
+            if (side * ey > 0)
+                xhi = xM + 2.0f;
+            else
+                xlo = xm - 2.0f;
         } else {
             // horizontal edge: the whole row is in or out
-            any = side * ex * ((y0 + y1) * 0.5 - p.y) > 0 || (y0 <= p.y && p.y <= y1);
+            any = side * ex * (y0 + y1 - 2 * p.y) > 0 || (y0 <= p.y && p.y <= y1);
         }
         int c0 = 0, c1 = a.gw - 1;
         if (any) {
-            c0 = xlo < 0 ? 0 : (int)fmin((double)(a.gw - 1), floor(xlo / kDtCell) - 1);
-            c1 = xhi >= 1e29 ? a.gw - 1 : (int)fmax(0.0, fmin((double)(a.gw - 1), floor(xhi / kDtCell) + 1));
+            c0 = xlo < 0.0f ? 0 : (int)fminf((float)(a.gw - 1), floorf(xlo / kDtCell) - 1.0f);
+            c1 = xhi >= 1e29f ? a.gw - 1 : (int)fmaxf(0.0f, fminf((float)(a.gw - 1), floorf(xhi / kDtCell) + 1.0f));
             c0 = max(0, c0);
         }
         const int s0 = any && c0 <= c1 ? S.cell_start[cy * a.gw + c0] : 0;
         const int e0 = any && c0 <= c1 ? S.cell_start[cy * a.gw + c1 + 1] : 0;
         r_start[cy] = s0;
-        r_pre[cy] = e0 - s0;  // length for now
+        r_len[cy] = e0 - s0;  // the row's range length
     }
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int cy = 0; cy < a.gh; ++cy) {
-            const int l = r_pre[cy];
-            r_pre[cy] = acc;
-            acc += l;
-        }
-        r_pre[a.gh] = acc;
-    }
-    __syncthreads();
-    const int total = r_pre[a.gh];
+    // each warp takes cell rows in turn; its lanes stride over the row's
+    // contiguous range of the grid-sorted points
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
     int4 best = bc;
     DtKey<int64_t> bk = bc.w ? dt_key<int64_t>(p, cur, bc, side) : DtKey<int64_t>{0, 1};
-    for (int j = tid; j < total; j += nth) {
-        int lo = 0, hi = a.gh - 1;  // last row whose prefix is <= j
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (r_pre[mid] <= j) lo = mid; else hi = mid - 1;
-        }
-        const int4 q = S.pts[r_start[lo] + (j - r_pre[lo])];
-        if (!q.w || q.z == cur.z || q.z == p.z) continue;
-        const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
-        if (qk.D <= 0) continue;
-        if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
-            best = q;
-            bk = qk;
+    for (int cy = warp; cy < a.gh; cy += nwarps) {
+        const int s0 = r_start[cy], len = r_len[cy];
+        for (int j = lane; j < len; j += 32) {
+            const int4 q = S.pts[s0 + j];
+            if (!q.w || q.z == cur.z || q.z == p.z) continue;
+            const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
+            if (qk.D <= 0) continue;
+            if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
+                best = q;
+                bk = qk;
+            }
         }
     }
     return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
@@ -739,7 +742,7 @@ __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, 
 // slots or, with out != NULL, to out.  Returns 1, or -1 if it exceeded
 // kDtMaxStar.
 __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4 &p, int n, int4 *cand, int R, int k,
-                             int *written, int32_t *out, DtBlockShared &sh, int *r_start, int *r_pre) {
+                             int *written, int32_t *out, DtBlockShared &sh, int *r_start, int *r_len) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
     // nearest neighbour: a cached point is nearer than every point outside
     // the cache, so a non-empty cache holds it; else one pass over all points
@@ -791,7 +794,7 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
             R = kDtRadius2;  // refill the cache once with the larger disc
             k = dt_block_gather(a, S, p, R, cand, sh);
         }
-        if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_pre);
+        if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_len);
         return dt_block_step(S, p, cur, side, nullptr, 0, n, sh);
     };
     int4 cur = first;
@@ -828,7 +831,7 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
 // and each warp places its hits with one atomic.
 __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, int R, int4 *cand,
                                DtBlockShared &sh) {
-    const int tid = threadIdx.x, lane = tid & 31, nth = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, max(0, p.x + R) / kDtCell);
     const int cy0 = max(0, p.y - R) / kDtCell, cy1 = min(a.gh - 1, max(0, p.y + R) / kDtCell);
     const int nrows = min(kDtMaxRows, cy1 - cy0 + 1);
@@ -840,51 +843,40 @@ __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, 
     }
     if (tid == 0) sh.cnt = 0;
     __syncthreads();
-    if (tid == 0) {  // exclusive prefix of the row lengths, in place
-        int acc = 0;
-        for (int r = 0; r < nrows; ++r) {
-            const int l = sh.rlen[r];
-            sh.rlen[r] = acc;
-            acc += l;
-        }
-        sh.rlen[nrows] = acc;
-    }
-    __syncthreads();
-    const int total = sh.rlen[nrows];
+    // each warp takes cell rows in turn; its lanes stride over the row's
+    // contiguous range and the warp places its hits with one atomic
     const int64_t R2 = (int64_t)R * R;
-    for (int j0 = 0; j0 < total; j0 += nth) {
-        const int j = j0 + tid;
-        bool take = false;
-        int4 q = make_int4(0, 0, 0, 0);
-        if (j < total) {
-            int lo = 0, hi = nrows - 1;  // last row whose prefix is <= j
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sh.rlen[mid] <= j) lo = mid; else hi = mid - 1;
+    for (int r = warp; r < nrows; r += nwarps) {
+        const int s0 = sh.rs[r], len = sh.rlen[r];
+        for (int j0 = 0; j0 < len; j0 += 32) {
+            const int j = j0 + lane;
+            bool take = false;
+            int4 q = make_int4(0, 0, 0, 0);
+            if (j < len) {
+                q = S.pts[s0 + j];
+                const int64_t dx = q.x - p.x, dy = q.y - p.y;
+                take = q.w && q.z != p.z && dx * dx + dy * dy <= R2;
             }
-            q = S.pts[sh.rs[lo] + (j - sh.rlen[lo])];
-            const int64_t dx = q.x - p.x, dy = q.y - p.y;
-            take = q.w && q.z != p.z && dx * dx + dy * dy <= R2;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&sh.cnt, __popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (take && pos < kDtCandCap2) cand[pos] = q;
         }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-        int base = 0;
-        if (lane == 0 && m) base = atomicAdd(&sh.cnt, __popc(m));
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        const int pos = base + __popc(m & ((1u << lane) - 1u));
-        if (take && pos < kDtCandCap2) cand[pos] = q;
     }
     __syncthreads();
     return sh.cnt;
 }
 
 // One queued star rebuilt by the whole CTA (exact): cached steps among the
-// points within kDtRadius2, region scans otherwise.
+// points within kDtRadius1 (then kDtRadius2), region scans otherwise.
 __device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, int i, int n, int4 *s_cand,
-                                              DtBlockShared &sh, int *r_start, int *r_pre) {
+                                              DtBlockShared &sh, int *r_start, int *r_len) {
     const int4 p = S.pts[S.slot[i]];
-    const int k = dt_block_gather(a, S, p, kDtRadius2, s_cand, sh);
+    const int k = dt_block_gather(a, S, p, kDtRadius1, s_cand, sh);
     int written = 0;
-    const int r = dt_block_star(a, S, i, p, n, s_cand, kDtRadius2, k, &written, nullptr, sh, r_start, r_pre);
+    const int r = dt_block_star(a, S, i, p, n, s_cand, kDtRadius1, k, &written, nullptr, sh, r_start, r_len);
     if (threadIdx.x == 0) {
         if (r == 1) {
             S.status[i] = 2;
@@ -897,16 +889,18 @@ __device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, 
     __syncthreads();
 }
 
-// One pair: the CTAs of side blockIdx.y stride over that side's queue.
-__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a) {
+// One pair: the CTAs of side blockIdx.y stride over that side's queue (the
+// group pass's, or with second_queue the warp pass's).
+__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a, int second_queue) {
     extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows
     __shared__ DtBlockShared sh;
     int *r_start = reinterpret_cast<int *>(s_cand + kDtCandCap2);
-    int *r_pre = r_start + a.gh;
+    int *r_len = r_start + a.gh;
     const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int nq = *S.npending2;
-    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, S.pending2[q0], n, s_cand, sh, r_start, r_pre);
+    const int nq = second_queue ? *S.npending2 : *S.npending;
+    const int32_t *queue = second_queue ? S.pending2 : S.pending;
+    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, queue[q0], n, s_cand, sh, r_start, r_len);
 }
 
 // Many pairs, persistent: the queues of every (pair, side) of the launch are
@@ -1148,15 +1142,16 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     dt_scatter_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_dedup_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     const int gblocks = max(1, min((cap + kDtGroupThreads / kDtGroup - 1) / (kDtGroupThreads / kDtGroup), 152 * 8));
+    // one pair: the CTA pass takes the group pass's queue directly (its time
+    // is that of the longest star, which the warp pass would not shorten)
     dt_pass1_kernel<<<dim3(gblocks, nsides), kDtGroupThreads, 0, st>>>(a);
-    dt_pass1b_kernel<<<dim3(152, nsides), kDtGroupThreads, 0, st>>>(a);
     const int smem2 = kDtCandCap2 * (int)sizeof(int4);
     const int smem3 = smem2 + (2 * a.gh + 1) * (int)sizeof(int);
     if (smem3 > 227 * 1024) return fail(ELAS_ERR_INVALID_ARG, "image too tall for the triangulation grid");
     if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel shared memory attribute");
     (void)smem2;
-    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a);
+    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a, 0);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_emit_big_kernel<<<dim3(152, nsides), 256, 0, st>>>(a);

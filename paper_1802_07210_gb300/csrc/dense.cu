@@ -477,19 +477,20 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
 elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                               const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
                               const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
-                              cudaStream_t st, const int32_t *ntri_dev) {
+                              cudaStream_t st, const int32_t *ntri_dev, cudaEvent_t after_prior) {
     DenseStage d;
     elas_status s = dense_args(descL, descR, w, h, p, list, triL, ntriL, triR, ntriR, gridL, gridR, dL, dR, ws,
                                ntri_dev, &d);
     if (s != ELAS_OK) return s;
     if ((s = raster_meshes(d.raster, st)) != ELAS_OK) return s;
+    if (after_prior && cudaEventRecord(after_prior, st) != cudaSuccess) return launch_status("prior mark");
     return launch_cells(d.cell, 2, st);
 }
 
 // Batched plane prior and dense matching over the pairs of `pairs`; host
 // is the host copy of the table.
 elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp,
-                           cudaStream_t st) {
+                           cudaStream_t st, cudaEvent_t after_prior) {
     if (pairs.n == 0) return ELAS_OK;
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
     VMap m_init, m_tri, m_big, m_cell;
@@ -518,6 +519,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
     plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
+    if (after_prior && cudaEventRecord(after_prior, st) != cudaSuccess) return launch_status("prior mark");
     const int total = vmap_total(m_cell);
     if (tpp == 1)
         cell_kernel_b<1><<<total, threads, 0, st>>>(t.cell, m_cell);

@@ -23,11 +23,12 @@ elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int 
                          const int16_t *dplane, const uint32_t *grid, int right, int16_t *out, cudaStream_t st);
 size_t dense_workspace(int w, int h, const elas_params *p);
 // With ntri_dev (two device counts) the triangle counts are read on the device
-// and ntriL/ntriR are the capacities the launch is sized for.
+// and ntriL/ntriR are the capacities the launch is sized for; after_prior (may
+// be NULL) is recorded between the prior and the argmin.
 elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                               const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
                               const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
-                              cudaStream_t st, const int32_t *ntri_dev);
+                              cudaStream_t st, const int32_t *ntri_dev, cudaEvent_t after_prior = nullptr);
 size_t triangulate_device_workspace(int cap, int w, int h, int nsides);
 elas_status launch_triangulate_device(const int16_t *list, const int32_t *count, int cap, int w, int h, int nsides,
                                       const int *rights, int32_t *const *tri, int32_t *const *ntri, int cap_tri,
@@ -68,8 +69,9 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
 // counter: one device int, the CTA pass's queue position.
 elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VMap &pairs, int nsides,
                                  int32_t *counter, cudaStream_t st);
+// after_prior (may be NULL) is recorded between the prior and the argmin.
 elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp,
-                           cudaStream_t st);
+                           cudaStream_t st, cudaEvent_t after_prior = nullptr);
 // post_tab[k]: table of post-processing pass k (k < 4); npass[i]: passes of
 // pair i of `pairs`.
 elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const PostArgs *const *post_tab,

@@ -98,6 +98,11 @@ struct elas_pipeline {
     void *ws_dt = nullptr;
     size_t ws_dt_bytes = 0;
     cudaStream_t last_stream = nullptr;
+    // stage marks (profiling on): descriptors | support | triangulation |
+    // plane prior | dense argmin | LR check + post-processing
+    int profiling = 0;
+    bool marked = false;
+    cudaEvent_t marks[7] = {};
     // last run
     elas_pipeline_stats stats{};
     std::vector<int32_t> triL_v, triR_v;
@@ -113,6 +118,8 @@ template <class T> cudaError_t dalloc(T **p, size_t bytes) {
 void release(elas_pipeline *pl) {
     if (!pl) return;
     delete pl->helper;
+    for (cudaEvent_t &e : pl->marks)
+        if (e) cudaEventDestroy(e);
     void *dev[] = {pl->img, pl->descL, pl->descR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
                    pl->ws_support, pl->ws_dense, pl->ws_post, pl->dL, pl->dR, pl->post, pl->ws_dt};
     for (void *d : dev)
@@ -206,10 +213,18 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
     int32_t *count = reinterpret_cast<int32_t *>(pl->countlist);
     elas_status s;
     pl->last_stream = st;
+    const bool prof = pl->profiling && pl->gpu_tri;
+    auto mark = [&](int i) {
+        if (prof) cudaEventRecord(pl->marks[i], st);
+    };
+    pl->marked = prof;
+    mark(0);
     if ((s = launch_descriptors(imgL, imgR, w, h, pitch, pl->descL, pl->descR, st)) != ELAS_OK) return s;
+    mark(1);
     if ((s = launch_support(pl->descL, pl->descR, w, h, p, pl->dcan, list, count, pl->gridL, pl->gridR,
                             pl->ws_support, st)) != ELAS_OK)
         return s;
+    mark(2);
     int16_t *outR = dR ? dR : pl->dR;
     if (pl->gpu_tri) {
         // everything stays on the device: no synchronisation in the step
@@ -220,9 +235,12 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
         if ((s = launch_triangulate_device(list, count, pl->nc, w, h, 2, rights, tris, nts, pl->tri_cap, pl->ws_dt,
                                            st)) != ELAS_OK)
             return s;
+        mark(3);
         if ((s = launch_dense_both(pl->descL, pl->descR, w, h, p, list, tris[0], pl->tri_cap, tris[1], pl->tri_cap,
-                                   pl->gridL, pl->gridR, dL, outR, pl->ws_dense, st, ntri_dev)) != ELAS_OK)
+                                   pl->gridL, pl->gridR, dL, outR, pl->ws_dense, st, ntri_dev,
+                                   prof ? pl->marks[4] : nullptr)) != ELAS_OK)
             return s;
+        mark(5);
         if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return launch_status("stats to host");
         pl->stats.triangulate_ms = 0.0;
@@ -251,7 +269,8 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
             return s;
     }
     if ((s = launch_lr_check(dL, outR, w, h, p->lr_threshold, nullptr, nullptr, st)) != ELAS_OK) return s;
-    if (post) return launch_post(dL, w, h, p, post, pl->ws_post, st);
+    if (post && (s = launch_post(dL, w, h, p, post, pl->ws_post, st)) != ELAS_OK) return s;
+    mark(6);
     return ELAS_OK;
 }
 
@@ -283,9 +302,23 @@ extern "C" elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_
     return ELAS_OK;
 }
 
+extern "C" elas_status elas_pipeline_set_profiling(elas_pipeline *pl, int32_t on) {
+    if (!pl) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL pipeline");
+    if (on && !pl->marks[0])
+        for (cudaEvent_t &e : pl->marks)
+            if (cudaEventCreate(&e) != cudaSuccess) return elas::launch_status("profiling events");
+    pl->profiling = on ? 1 : 0;
+    return ELAS_OK;
+}
+
 extern "C" elas_status elas_pipeline_stats_get(const elas_pipeline *pl, elas_pipeline_stats *st) {
     if (!pl || !st) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL argument");
     *st = pl->stats;
+    for (float &v : st->stage_ms) v = 0.0f;
+    if (pl->marked) {
+        if (cudaEventSynchronize(pl->marks[6]) != cudaSuccess) return elas::launch_status("stage marks");
+        for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&st->stage_ms[i], pl->marks[i], pl->marks[i + 1]);
+    }
     if (pl->gpu_tri) {
         if (cudaStreamSynchronize(pl->last_stream) != cudaSuccess) return elas::launch_status("stats sync");
         const int32_t *c = reinterpret_cast<const int32_t *>(pl->h_countlist);

@@ -56,9 +56,12 @@ struct Slot {
     bool async_mem = false;  // memory from the stream-ordered allocator
 };
 
-// Per-stage event marks of a wave (for the tuner); NULL entries are skipped.
+// Event marks of a wave (tuner, profiling); NULL entries are skipped.  The
+// intervals are: descriptors, support points, triangulation, plane prior,
+// dense argmin, LR check + post-processing.
+constexpr int kStageMarks = 7;
 struct StageMarks {
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[kStageMarks] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 class SlotPool {

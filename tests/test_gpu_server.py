@@ -124,18 +124,21 @@ def test_burst_matches_oracle_and_alone(requests, alone):
     srv.close()
 
 
-def test_staggered_arrivals_overlap(requests, alone):
-    """Requests arriving while waves run join later waves; waves overlap."""
+def test_arrivals_during_waves_overlap(requests, alone):
+    """Requests that arrive while waves run are queued and join later waves
+    on the other lanes; those waves overlap on the device."""
     B = _B()
     srv = B.Server(lanes=3, max_wave=4)
     reqs = requests * 2
     reqs = [dict(r, id=i) for i, r in enumerate(reqs)]
     al = {i: alone[requests[i % len(requests)]["id"]] for i in range(len(reqs))}
-    results, bufs = _serve(srv, reqs, stagger_s=0.0005)
+    results, bufs = _serve(srv, reqs)
     _check(reqs, results, bufs, al)
     spans = sorted((r["t_start_ms"], r["t_done_ms"]) for r in results.values())
     overlap = any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
-    assert overlap, "no request started while another was in flight"
+    assert overlap, "no wave started while another was in flight"
+    assert max(r["wave_size"] for r in results.values()) > 1
+    assert srv.stats()["waves"] >= len(reqs) // 4
     srv.close()
 
 
