@@ -231,6 +231,10 @@ class Pipeline:
             pass
 
 
+def _cfg_dict(cfg):
+    return {k: int(getattr(cfg, k)) for k, _ in BatchConfig._fields_}
+
+
 def _ptr_array(ptrs):
     arr = (C.c_void_p * len(ptrs))()
     for i, p in enumerate(ptrs):
@@ -265,14 +269,13 @@ class Batch:
     def config(self):
         cfg = BatchConfig()
         check(lib().elas_batch_get_config(self._h, C.byref(cfg)))
-        return dict(desc_tile_rows=cfg.desc_tile_rows, support_warps=cfg.support_warps,
-                    dense_threads_per_pixel=cfg.dense_threads_per_pixel, use_graph=cfg.use_graph)
+        return _cfg_dict(cfg)
 
     def set_config(self, **kw):
         cur = self.config()
         cur.update(kw)
         cfg = BatchConfig(cur["desc_tile_rows"], cur["support_warps"], cur["dense_threads_per_pixel"],
-                          cur["use_graph"])
+                          cur["use_graph"], cur["dense_pixels_per_thread"])
         check(lib().elas_batch_set_config(self._h, C.byref(cfg)))
 
     def _dev_arrays(self, imgL, imgR, dL, dR, post):
@@ -323,8 +326,7 @@ class Batch:
         aL, aR, aD, _, _ = self._dev_arrays(imgL, imgR, dL, None, None)
         cfg = BatchConfig()
         check(lib().elas_batch_tune(self._h, aL, aR, None, aD, _stream(stream), C.byref(cfg)))
-        return dict(desc_tile_rows=cfg.desc_tile_rows, support_warps=cfg.support_warps,
-                    dense_threads_per_pixel=cfg.dense_threads_per_pixel, use_graph=cfg.use_graph)
+        return _cfg_dict(cfg)
 
     def profile(self, stream=None):
         """Device ms of each stage of one eager run on the last-bound buffers."""

@@ -64,7 +64,7 @@ void release(elas_batch *b) {
 }
 
 std::vector<int> signature(const elas_batch *b) {
-    std::vector<int> sig{b->knobs.desc_rows, b->knobs.support_warps, b->knobs.dense_tpp};
+    std::vector<int> sig{b->knobs.desc_rows, b->knobs.support_warps, b->knobs.dense_tpp, b->knobs.dense_ppt};
     for (int id : b->ids) sig.push_back(b->pool[id].npass);
     return sig;
 }
@@ -139,7 +139,8 @@ elas_status run_bound(elas_batch *b, cudaStream_t st) {
 bool knob_ok(const Knobs &k) {
     return (k.desc_rows == 4 || k.desc_rows == 8 || k.desc_rows == 16) &&
            (k.support_warps == 4 || k.support_warps == 8 || k.support_warps == 16) &&
-           (k.dense_tpp == 1 || k.dense_tpp == 2 || k.dense_tpp == 4);
+           (k.dense_tpp == 1 || k.dense_tpp == 2 || k.dense_tpp == 4) &&
+           (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8);
 }
 
 }  // namespace
@@ -188,6 +189,7 @@ extern "C" elas_status elas_batch_get_config(const elas_batch *b, elas_batch_con
     cfg->desc_tile_rows = b->knobs.desc_rows;
     cfg->support_warps = b->knobs.support_warps;
     cfg->dense_threads_per_pixel = b->knobs.dense_tpp;
+    cfg->dense_pixels_per_thread = b->knobs.dense_ppt;
     cfg->use_graph = b->use_graph;
     return ELAS_OK;
 }
@@ -198,9 +200,10 @@ extern "C" elas_status elas_batch_set_config(elas_batch *b, const elas_batch_con
     k.desc_rows = cfg->desc_tile_rows;
     k.support_warps = cfg->support_warps;
     k.dense_tpp = cfg->dense_threads_per_pixel;
+    k.dense_ppt = cfg->dense_pixels_per_thread;
     if (!knob_ok(k))
-        return fail(ELAS_ERR_INVALID_ARG, "config %d/%d/%d outside {4,8,16}/{4,8,16}/{1,2,4}", k.desc_rows,
-                    k.support_warps, k.dense_tpp);
+        return fail(ELAS_ERR_INVALID_ARG, "config %d/%d/%d/%d outside {4,8,16}/{4,8,16}/{1,2,4}/{1,2,4,8}",
+                    k.desc_rows, k.support_warps, k.dense_tpp, k.dense_ppt);
     b->knobs = k;
     b->use_graph = cfg->use_graph ? 1 : 0;
     return ELAS_OK;
@@ -282,7 +285,10 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
         int values[3];
     };
     Knobs k = b->knobs;
-    Axis axes[3] = {{&k.desc_rows, 0, {4, 8, 16}}, {&k.support_warps, 1, {4, 8, 16}}, {&k.dense_tpp, 4, {1, 2, 4}}};
+    Axis axes[4] = {{&k.desc_rows, 0, {4, 8, 16}},
+                    {&k.support_warps, 1, {4, 8, 16}},
+                    {&k.dense_tpp, 4, {1, 2, 4}},
+                    {&k.dense_ppt, 4, {2, 4, 8}}};
     const int reps = 3;
     for (Axis &ax : axes) {
         float best_ms = 1e30f;

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) plane_raster_big_kernel_b(const RasterArg
 
 
 
-constexpr int kListPad = 16;  // the candidate list is padded to a multiple of this
+constexpr int kListPad = 16;  // padding entries (2047) after the candidate list
 
 // TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
 // every TPP-th candidate of its list and of its plane window and merge their
@@ -243,12 +243,16 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
         if (lane == 0) s_nlist = base;
     }
     __syncthreads();
-    constexpr int kStep = 4 * TPP;  // list entries per unrolled round of a pixel group
-    const int nlist = full ? 0 : (s_nlist + kStep - 1) / kStep * kStep;
+    const int nlist = full ? 0 : s_nlist;
+    const int dlast = nlist > 0 ? (int)s_list[nlist - 1] : -1;  // largest entry
     const int sub = TPP > 1 ? (tid & (TPP - 1)) : 0;
 
     // ---- per-pixel argmin -------------------------------------------------------
+    // pixel p of the cell is (x0 + p % cw, y0 + p / cw); a thread's pixels
+    // advance by ppb, so after one division the position steps incrementally
     const int ppb = blockDim.x / TPP;  // pixels per pass of the CTA
+    const int sdy = ppb / cw, sdx = ppb - sdy * cw;
+    int px = (tid / TPP) % cw, py = (tid / TPP) / cw;
     for (int pb = 0; pb < npx; pb += ppb) {
         const int p = pb + tid / TPP;
         int best = 0x7FFFFFFF;
@@ -256,8 +260,8 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
         size_t row = 0;
         int x = 0;
         if (p < npx) {
-            x = x0 + p % cw;
-            const int y = y0 + p / cw;
+            x = x0 + px;
+            const int y = y0 + py;
             row = (size_t)y * W;
             live = true;
             if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
@@ -275,13 +279,24 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     } else {
-#pragma unroll 4
-                        for (int k = sub; k < nlist; k += TPP) {
-                            const int d = s_list[k];
-                            if (d <= dlim) {
-                                const int c = (int)sad16(r, __ldg(orow + dir * d));
-                                best = min(best, ((c + kKeyBias) << 11) | d);
+                        // the admissible entries are a prefix of the ascending list
+                        int cnt = nlist;
+                        if (dlim < dlast) {
+                            int lo = 0, hi = nlist;  // first entry above dlim
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if ((int)s_list[mid] <= dlim)
+                                    lo = mid + 1;
+                                else
+                                    hi = mid;
                             }
+                            cnt = lo;
+                        }
+#pragma unroll 4
+                        for (int k = sub; k < cnt; k += TPP) {
+                            const int d = s_list[k];
+                            const int c = (int)sad16(r, __ldg(orow + dir * d));
+                            best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                         const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
                         for (int d = lo + sub; d <= hi; d += TPP) {
@@ -298,6 +313,12 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
             for (int o = TPP / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
         }
         if (live && sub == 0) S.out[row + x] = (int16_t)(best != 0x7FFFFFFF ? (best & 2047) : -1);
+        px += sdx;
+        py += sdy;
+        if (px >= cw) {
+            px -= cw;
+            ++py;
+        }
     }
 }
 
@@ -407,9 +428,10 @@ static CellArgs cell_args(int w, int h, const elas_params *p, const int *P) {
     return a;
 }
 
-// Threads of a cell CTA: TPP per pixel of a G x G cell, at most 1024.
-int cell_threads(int G, int tpp) {
-    const int t = (G * G * tpp + 31) / 32 * 32;
+// Threads of a cell CTA: tpp per pixel of a G x G cell, each thread (group)
+// taking ppt pixels in turn, at most 1024.
+int cell_threads(int G, int tpp, int ppt) {
+    const int t = ((G * G + ppt - 1) / ppt * tpp + 31) / 32 * 32;
     return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }
 
@@ -418,7 +440,7 @@ dim3 cell_grid(const CellArgs &a, int nsides) {
 }
 
 static elas_status launch_cells(const CellArgs &a, int nsides, cudaStream_t st) {
-    cell_kernel<<<cell_grid(a, nsides), cell_threads(a.G, 1), 0, st>>>(a);
+    cell_kernel<<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
     return launch_status("cell_kernel");
 }
 
@@ -489,10 +511,11 @@ elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w,
 
 // Batched plane prior and dense matching over the pairs of `pairs`; host
 // is the host copy of the table.
-elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp,
+elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp, int ppt,
                            cudaStream_t st, cudaEvent_t after_prior) {
     if (pairs.n == 0) return ELAS_OK;
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
+    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return fail(ELAS_ERR_INVALID_ARG, "dense pixels per thread %d", ppt);
     VMap m_init, m_tri, m_big, m_cell;
     vmap_clear(m_init, pairs.stride);
     vmap_clear(m_tri, pairs.stride);
@@ -512,7 +535,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
         vmap_add(m_big, slot, dim3(32));
         vmap_add(m_cell, slot, cell_grid(d.cell, 2));
-        threads = max(threads, cell_threads(d.cell.G, tpp));
+        threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }
     raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
     plane_raster_kernel_b<<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri);

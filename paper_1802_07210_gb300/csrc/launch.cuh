@@ -55,7 +55,7 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
                        const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
                        const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
                        const int32_t *ntri_dev, DenseStage *o);
-int cell_threads(int G, int tpp);
+int cell_threads(int G, int tpp, int ppt);
 int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, PostArgs *passes);
 
 // ---- many pairs per launch --------------------------------------------------
@@ -70,7 +70,7 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
 elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VMap &pairs, int nsides,
                                  int32_t *counter, cudaStream_t st);
 // after_prior (may be NULL) is recorded between the prior and the argmin.
-elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp,
+elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp, int ppt,
                            cudaStream_t st, cudaEvent_t after_prior = nullptr);
 // post_tab[k]: table of post-processing pass k (k < 4); npass[i]: passes of
 // pair i of `pairs`.

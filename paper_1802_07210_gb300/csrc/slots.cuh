@@ -20,6 +20,7 @@ struct Knobs {
     int desc_rows = 8;      // descriptor tile height: 4, 8, 16
     int support_warps = 8;  // lattice candidates (warps) per support CTA: 4, 8, 16
     int dense_tpp = 1;      // threads per pixel in the dense argmin: 1, 2, 4
+    int dense_ppt = 4;      // pixels per thread (per pixel group) in the dense argmin: 1, 2, 4, 8
 };
 
 // The stage arguments of one slot, one record per slot in the tables.

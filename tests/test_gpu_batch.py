@@ -138,14 +138,16 @@ def test_mixed_batch_equals_per_pair_path(mix):
 
 
 KNOBS = [
-    dict(desc_tile_rows=4, support_warps=4, dense_threads_per_pixel=1),
-    dict(desc_tile_rows=16, support_warps=16, dense_threads_per_pixel=2),
-    dict(desc_tile_rows=8, support_warps=8, dense_threads_per_pixel=4),
-    dict(desc_tile_rows=16, support_warps=4, dense_threads_per_pixel=4),
+    dict(desc_tile_rows=4, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=1),
+    dict(desc_tile_rows=16, support_warps=16, dense_threads_per_pixel=2, dense_pixels_per_thread=2),
+    dict(desc_tile_rows=8, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=1),
+    dict(desc_tile_rows=16, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=4),
+    dict(desc_tile_rows=4, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=4),
+    dict(desc_tile_rows=8, support_warps=16, dense_threads_per_pixel=1, dense_pixels_per_thread=8),
 ]
 
 
-@pytest.mark.parametrize("knobs", KNOBS, ids=lambda k: "%d-%d-%d" % tuple(k.values()))
+@pytest.mark.parametrize("knobs", KNOBS, ids=lambda k: "%d-%d-%d-%d" % tuple(k.values()))
 @pytest.mark.parametrize("graph", [0, 1])
 def test_knob_settings_give_identical_results(mix, knobs, graph):
     b = _batch(mix)
@@ -167,14 +169,14 @@ def test_tuner_picks_valid_knobs(mix):
     assert cfg["desc_tile_rows"] in (4, 8, 16)
     assert cfg["support_warps"] in (4, 8, 16)
     assert cfg["dense_threads_per_pixel"] in (1, 2, 4)
+    assert cfg["dense_pixels_per_thread"] in (1, 2, 4, 8)
     assert b.config()["desc_tile_rows"] == cfg["desc_tile_rows"]
     b.run(imgL, imgR, dL, dR, post)
     _check(mix, dL, dR, post, "tuned")
     # a second batch of the same shapes starts from the tuned setting
     b2 = _batch(mix)
     c2 = b2.config()
-    assert (c2["desc_tile_rows"], c2["support_warps"], c2["dense_threads_per_pixel"]) == \
-        (cfg["desc_tile_rows"], cfg["support_warps"], cfg["dense_threads_per_pixel"])
+    assert c2 == cfg
     b2.close()
     b.close()
 
