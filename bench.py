@@ -44,11 +44,10 @@ METRIC = "Mpix/s & pairs/s at 640x480 D=256; p50/p99 served latency vs per-pair 
 WORKLOADS = {"vga_640": (synth.VGA_640, 2), "small_320": (synth.SMALL_320, 1),
              "kitti_1242": (synth.KITTI_1242, 3)}
 # kernels of one plain step: descriptors 1; support 4 (match, consistency,
-# redundancy + grids, compaction); triangulation 10 (points, cell scan,
-# scatter, dedup, group pass, warp pass, CTA pass, triangle scan, emit, emit
-# big); plane prior 2 (raster, big triangles); dense 1; LR 1; post-processing
-# 4 (gap rows, gap columns, mean rows, mean columns) or 1 (copy)
-KERNELS_PER_STEP = {True: 23, False: 20}
+# redundancy + grids, compaction); triangulation 9 (points, cell scan,
+# scatter, dedup, group pass, CTA pass, triangle scan, emit, emit big); plane
+# prior 2 (raster, big triangles); dense 1; LR 1; post-processing 1 (fused) or 0
+KERNELS_PER_STEP = {True: 19, False: 18}
 STAGES = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")
 # bytes a dense launch must move at least: both descriptor images read once
 # (32 B/px), the two prior maps read (4 B/px), the two maps written (4 B/px)
@@ -173,6 +172,26 @@ def run_reference(args, wl, cfg):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(torch, dist, ws, value, device):
+    """The largest of every rank's value (a time): the job is as slow as its
+    slowest replica."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws, steps, units_per_step, total_ms):
+    """Whole-job rate of ws independent replicas that each did `steps` steps
+    of `units_per_step` units, the slowest in total_ms."""
+    return ws * steps * units_per_step / (total_ms / 1e3)
+
+
+def replica_seed(rank, i):
+    """Pair seeds of a replica: disjoint across ranks."""
+    return rank * 1000 + i
+
+
 def _timed(torch, stream, flush, fn, steps):
     """Device ms of each of `steps` calls of fn(i), L2 flushed before each."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -206,7 +225,7 @@ def pair_dense_evals(B, torch, wl, L, R, dev):
     return dense_work(work, prm, w, h)
 
 
-def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad):
+def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad, tune=True):
     """64 x 1242x375 D=256 through one batched wave vs the plain path."""
     wl, cfg = synth.KITTI_1242, 3
     w, h = wl.spec.w, wl.spec.h
@@ -216,7 +235,7 @@ def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, pea
     dL = [torch.empty((h, w), dtype=torch.int16, device=dev) for _ in range(npairs)]
     dR = [torch.empty_like(t) for t in dL]
     b = B.Batch([(w, h)] * npairs, wl.params)
-    tuned = b.tune(imgL, imgR, dL)
+    tuned = b.tune(imgL, imgR, dL) if tune else b.config()
     for _ in range(3):
         b.run(imgL, imgR, dL, dR)
     ms = _timed(torch, stream, flush, lambda i: b.run(imgL, imgR, dL, dR), steps)
@@ -246,7 +265,7 @@ def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, pea
                                "time_source": "CUDA events around the launch in an eager run of the same batch"}}
 
 
-def run_mixed_section(B, torch, dev, stream, flush, steps, npairs):
+def run_mixed_section(B, torch, dev, stream, flush, steps, npairs, tune=True):
     """128 pairs of mixed sizes and disparity ranges: one wave vs plain runs."""
     spec = synth.mixed_batch(npairs, 4)
     distinct = {}
@@ -259,7 +278,7 @@ def run_mixed_section(B, torch, dev, stream, flush, steps, npairs):
     dR = [torch.empty_like(t) for t in dL]
     shapes = [(wl.spec.w, wl.spec.h) for wl, _ in spec]
     b = B.Batch(shapes, [wl.params for wl, _ in spec])
-    tuned = b.tune(imgL, imgR, dL)
+    tuned = b.tune(imgL, imgR, dL) if tune else b.config()
     for _ in range(3):
         b.run(imgL, imgR, dL, dR)
     ms = _timed(torch, stream, flush, lambda i: b.run(imgL, imgR, dL, dR), steps)
@@ -354,6 +373,25 @@ def run_serve_section(B, torch, seconds, rate_per_camera=75.0, seed=5):
     return out
 
 
+def run_only(args, B, torch, dev):
+    """One section alone (profiling runs)."""
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    class _Flush:
+        def fill_(self, v):
+            flush_buf.fill_(v)
+
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 10))
+    if args.only == "batch":
+        peak = alu_peak(B, torch, dev, stream)[0] / 1e9
+        return run_batch_section(B, torch, dev, stream, _Flush(), steps, args.batch_pairs, args.batch_distinct, peak,
+                                 tune=not args.no_tune)
+    if args.only == "mixed":
+        return run_mixed_section(B, torch, dev, stream, _Flush(), steps, args.mixed_pairs, tune=not args.no_tune)
+    return run_serve_section(B, torch, args.serve_seconds)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +406,9 @@ def main():
     ap.add_argument("--mixed-pairs", type=int, default=128)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--skip-extra", action="store_true", help="only the plain-path line")
+    ap.add_argument("--only", default=None, choices=["batch", "mixed", "serve"],
+                    help="run only this section (its JSON object is printed alone)")
+    ap.add_argument("--no-tune", action="store_true", help="batched sections keep the default tile shapes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl, cfg = WORKLOADS[args.workload]
@@ -383,9 +424,16 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only:
+        if rank == 0:
+            print(json.dumps({args.only: run_only(args, B, torch, dev)}), flush=True)
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     w, h = wl.spec.w, wl.spec.h
     px = w * h
-    pool = [synth.workload_pair(wl, rank * 1000 + i, cfg) for i in range(args.pool)]
+    pool = [synth.workload_pair(wl, replica_seed(rank, i), cfg) for i in range(args.pool)]
     imgs = [(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)) for L, R, _ in pool]
     pl = B.Pipeline(w, h, wl.params)
     pl.set_profiling(True)
@@ -432,13 +480,9 @@ def main():
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_all = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    total_ms = float(t_all.item())
+    total_ms = max_over_ranks(torch, dist, ws, sum(a.elapsed_time(b) for a, b in ev), dev)
     ms_step = total_ms / args.steps
-    value = ws * args.steps * px / (total_ms / 1e3) / 1e6
+    value = replica_throughput(ws, args.steps, px, total_ms) / 1e6
     st = pl.stats()
     stages = {k: float(np.mean([s[k] for s in stage_ms])) for k in STAGES}
 
@@ -456,11 +500,8 @@ def main():
         t0 = time.perf_counter()
         pl.run_host(hL[i % len(hL)], hR[i % len(hR)], oL, None, opost)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    t_e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t_e.item())
-    e2e = {"value": ws * args.steps * px / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
+    e2e_ms = max_over_ranks(torch, dist, ws, e2e_ms, dev)
+    e2e = {"value": replica_throughput(ws, args.steps, px, e2e_ms) / 1e6, "unit": "Mpix/s",
            "h2d_bytes_per_step": 2 * px, "d2h_bytes_per_step": 2 * px + (4 * px if wl.postprocess else 0),
            "ms_per_step": e2e_ms / args.steps, "call": "elas_pipeline_run_host (pinned host buffers)"}
 
@@ -487,9 +528,9 @@ def main():
     extra = {}
     if rank == 0 and not args.skip_extra:
         extra["batch"] = run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
-                                           args.batch_pairs, args.batch_distinct, peak)
+                                           args.batch_pairs, args.batch_distinct, peak, tune=not args.no_tune)
         extra["mixed_batch"] = run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
-                                                 args.mixed_pairs)
+                                                 args.mixed_pairs, tune=not args.no_tune)
         extra["serving"] = run_serve_section(B, torch, args.serve_seconds)
 
     if rank == 0:
@@ -500,7 +541,7 @@ def main():
                            "pairs_per_step": 1, "pool": args.pool, "path": "plain one-pair path (elas_pipeline_run)",
                            "triangulation": "GPU",
                            "l2": "flushed before every timed step (256 MB write, then 256 MB read so no dirty lines remain)"},
-                "pairs_per_s": ws * args.steps / (total_ms / 1e3),
+                "pairs_per_s": replica_throughput(ws, args.steps, 1, total_ms),
                 "support_points": st["n_support"], "triangles": [st["n_tri_left"], st["n_tri_right"]],
                 "stages_ms": stages, "clocks": clk, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_STEP[bool(wl.postprocess)] * args.steps, "roofline": roof}

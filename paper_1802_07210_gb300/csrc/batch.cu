@@ -65,7 +65,7 @@ void release(elas_batch *b) {
 
 std::vector<int> signature(const elas_batch *b) {
     std::vector<int> sig{b->knobs.desc_rows, b->knobs.support_warps, b->knobs.dense_tpp, b->knobs.dense_ppt};
-    for (int id : b->ids) sig.push_back(b->pool[id].npass);
+    for (int id : b->ids) sig.push_back(b->pool[id].npass * 2 + b->pool[id].fused);
     return sig;
 }
 

@@ -57,6 +57,9 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
                        const int32_t *ntri_dev, DenseStage *o);
 int cell_threads(int G, int tpp, int ppt);
 int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, PostArgs *passes);
+bool post_fusable(const elas_params *p);
+FusedPostArgs fused_post_args(const int16_t *d, int w, int h, const elas_params *p, float *out);
+dim3 fused_post_grid(int w, int h);
 
 // ---- many pairs per launch --------------------------------------------------
 // Tables are arrays of per-slot records `pairs.stride` bytes apart: `tab`
@@ -73,8 +76,9 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
 elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp, int ppt,
                            cudaStream_t st, cudaEvent_t after_prior = nullptr);
 // post_tab[k]: table of post-processing pass k (k < 4); npass[i]: passes of
-// pair i of `pairs`.
+// pair i of `pairs`; fused[i]: pair i uses the fused kernel (table fused_tab).
 elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const PostArgs *const *post_tab,
-                             const int *npass, const VMap &pairs, cudaStream_t st);
+                             const int *npass, const FusedPostArgs *fused_tab, const int *fused, const VMap &pairs,
+                             cudaStream_t st);
 
 }  // namespace elas

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(256) lr_check_kernel_b(const LrArgs *__restric
 }
 
 // Gap interpolation along a row or a column at element k of a line of
-// length len (stride es from base).
-__device__ __forceinline__ float gap_at(const LineIn &in, size_t base, size_t es, int k, int len, int gap) {
+// length len (stride es from base); In is LineIn (global maps) or SmemIn.
+template <class In>
+__device__ __forceinline__ float gap_at(const In &in, size_t base, size_t es, int k, int len, int gap) {
     const float x = in.at(base + (size_t)k * es);
     float res = x;
     if (x < 0.0f) {
@@ -75,7 +76,8 @@ constexpr int kMeanRadius = 3;
 
 // Adaptive mean along a line: taps in ascending offset order, FP32 without
 // contraction.
-__device__ __forceinline__ float mean_at(const LineIn &in, size_t base, size_t es, int k, int len) {
+template <class In>
+__device__ __forceinline__ float mean_at(const In &in, size_t base, size_t es, int k, int len) {
     const float d0 = in.at(base + (size_t)k * es);
     float res = d0;
     if (d0 >= 0.0f) {
@@ -123,6 +125,92 @@ __global__ void __launch_bounds__(256) post_pass_kernel(PostArgs a) { post_pass_
 __global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     post_pass_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+// ---------------------------------------------------------------------------
+// Fused post-processing: the four passes on one 32x32 tile in shared memory.
+//
+// The output tile needs the vertical mean over rows +-3 (r), which needs the
+// horizontal mean over columns +-3, which needs the column gap pass over
+// rows +-g (g = ipol_gap_width), which needs the row gap pass over columns
+// +-g: the tile is loaded with a halo H = r + g, pixels outside the image
+// read -1.  That is the same as the per-pass kernels, whose searches stop at
+// the image border, because a -1 is never taken as a valid neighbour or a
+// tap.  Each pass runs over exactly the region the next one reads, with the
+// same per-element functions as the per-pass kernels.
+// ---------------------------------------------------------------------------
+constexpr int kFusedTile = 32;
+constexpr int kFusedMaxGap = 16;
+constexpr int kFusedPitch = kFusedTile + 2 * (kFusedMaxGap + kMeanRadius);
+
+struct SmemIn {
+    const float *s;
+    __device__ __forceinline__ float at(size_t idx) const { return s[idx]; }
+};
+
+__device__ __forceinline__ void fused_post_body(const FusedPostArgs &a, const VB &vb) {
+    __shared__ float s_a[kFusedPitch * kFusedPitch];
+    __shared__ float s_b[kFusedPitch * kFusedPitch];
+    const int w = a.w, h = a.h;
+    const int g = a.gap, r = a.mean ? kMeanRadius : 0, H = g + r;
+    const int P = kFusedTile + 2 * H;  // tile pitch
+    const int x0 = vb.x * kFusedTile - H, y0 = vb.y * kFusedTile - H;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < P * P; i += nth) {
+        const int gx = x0 + i % P, gy = y0 + i / P;
+        s_a[i] = (gx >= 0 && gx < w && gy >= 0 && gy < h) ? (float)a.d[(size_t)gy * w + gx] : -1.0f;
+    }
+    __syncthreads();
+    float *cur = s_a, *nxt = s_b;
+    if (g > 0) {
+        // rows: every row, the columns the later passes read
+        const int cw = P - 2 * g;
+        for (int i = tid; i < cw * P; i += nth) {
+            const int c = g + i % cw, rr = i / cw;
+            nxt[rr * P + c] = gap_at(SmemIn{cur}, (size_t)rr * P, 1, c, P, g);
+        }
+        __syncthreads();
+        // columns: those columns, the rows the means read
+        for (int i = tid; i < cw * cw; i += nth) {
+            const int c = g + i % cw, rr = g + i / cw;
+            cur[rr * P + c] = gap_at(SmemIn{nxt}, (size_t)c, (size_t)P, rr, P, g);
+        }
+        __syncthreads();
+    }
+    if (r > 0) {
+        // horizontal mean: the output columns, rows +-r
+        const int nr = kFusedTile + 2 * r;
+        for (int i = tid; i < kFusedTile * nr; i += nth) {
+            const int c = H + i % kFusedTile, rr = g + i / kFusedTile;
+            nxt[rr * P + c] = mean_at(SmemIn{cur}, (size_t)rr * P, 1, c, P);
+        }
+        __syncthreads();
+    }
+    // vertical mean (or, without the means, the gap passes' result) to the output
+    const float *src = r > 0 ? nxt : cur;
+    for (int i = tid; i < kFusedTile * kFusedTile; i += nth) {
+        const int c = H + i % kFusedTile, rr = H + i / kFusedTile;
+        const int gx = x0 + c, gy = y0 + rr;
+        if (gx >= w || gy >= h) continue;
+        a.out[(size_t)gy * w + gx] = r > 0 ? mean_at(SmemIn{src}, (size_t)c, (size_t)P, rr, P) : src[rr * P + c];
+    }
+}
+
+__global__ void __launch_bounds__(256) fused_post_kernel(FusedPostArgs a) { fused_post_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) fused_post_kernel_b(const FusedPostArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    fused_post_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+bool post_fusable(const elas_params *p) { return p->ipol_gap_width <= kFusedMaxGap; }
+
+FusedPostArgs fused_post_args(const int16_t *d, int w, int h, const elas_params *p, float *out) {
+    return FusedPostArgs{d, out, w, h, p->ipol_gap_width > 0 ? p->ipol_gap_width : 0,
+                         p->filter_adaptive_mean ? 1 : 0};
+}
+
+dim3 fused_post_grid(int w, int h) {
+    return dim3((w + kFusedTile - 1) / kFusedTile, (h + kFusedTile - 1) / kFusedTile);
 }
 
 size_t post_workspace(int w, int h) { return 2 * align_up((size_t)w * h * sizeof(float), 256); }
@@ -174,6 +262,10 @@ int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out
 dim3 post_grid(int w, int h) { return dim3((w + 31) / 32, (h + 7) / 8); }
 
 elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, cudaStream_t st) {
+    if (post_fusable(p)) {
+        fused_post_kernel<<<fused_post_grid(w, h), 256, 0, st>>>(fused_post_args(d, w, h, p, out));
+        return launch_status("fused_post_kernel");
+    }
     PostArgs passes[4];
     const int np = post_passes(d, w, h, p, out, ws, passes);
     for (int i = 0; i < np; ++i) {
@@ -184,10 +276,12 @@ elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, fl
     return ELAS_OK;
 }
 
-// Batched LR check and post-processing.  post_tab[k] is the table of pass k
-// and npass_of(slot) the number of passes of a slot (0: no post-processing).
+// Batched LR check and post-processing.  Pairs with fused[i] run the fused
+// kernel (table fused_tab); the others run npass[i] separate passes, pass k
+// from table post_tab[k] (npass 0 and not fused: no post-processing).
 elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const PostArgs *const *post_tab,
-                             const int *npass, const VMap &pairs, cudaStream_t st) {
+                             const int *npass, const FusedPostArgs *fused_tab, const int *fused, const VMap &pairs,
+                             cudaStream_t st) {
     if (pairs.n == 0) return ELAS_OK;
     VMap m_lr;
     vmap_clear(m_lr, pairs.stride);
@@ -203,6 +297,16 @@ elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const 
     if (s != ELAS_OK) return s;
     lr_check_kernel_b<<<vmap_total(m_lr), 256, smem, st>>>(lr_tab, m_lr);
     if ((s = launch_status("lr_check_kernel_b")) != ELAS_OK) return s;
+    VMap m_f;
+    vmap_clear(m_f, pairs.stride);
+    for (int i = 0; i < pairs.n; ++i) {
+        const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
+        vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h) : dim3(0));
+    }
+    if (vmap_total(m_f) > 0) {
+        fused_post_kernel_b<<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
+        if ((s = launch_status("fused_post_kernel_b")) != ELAS_OK) return s;
+    }
     for (int k = 0; k < maxp && k < 4; ++k) {
         VMap m;
         vmap_clear(m, pairs.stride);

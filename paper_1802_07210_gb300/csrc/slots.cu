@@ -194,7 +194,9 @@ elas_status SlotPool::write_records(int id) {
                                sl.gridL, sl.gridR, sl.io_dL, sl.io_dR, sl.ws_dense, sl.counters + 1, &t.dense);
     if (s != ELAS_OK) return s;
     t.lr = LrArgs{sl.io_dL, sl.io_dR, w, h, p->lr_threshold, nullptr, nullptr};
-    sl.npass = sl.post_on ? post_passes(sl.io_dL, w, h, p, sl.io_post, sl.ws_post, t.post) : 0;
+    sl.fused = sl.post_on && post_fusable(p) ? 1 : 0;
+    sl.npass = sl.post_on && !sl.fused ? post_passes(sl.io_dL, w, h, p, sl.io_post, sl.ws_post, t.post) : 0;
+    if (sl.fused) t.fpost = fused_post_args(sl.io_dL, w, h, p, sl.io_post);
     dirty_lo_ = std::min(dirty_lo_, id);
     dirty_hi_ = std::max(dirty_hi_, id);
     return ELAS_OK;
@@ -248,12 +250,13 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     if (dirty_hi_ >= dirty_lo_) return fail(ELAS_ERR_INTERNAL, "slot records changed without an upload");
     VMap pairs;
     vmap_clear(pairs, (int)sizeof(SlotTables));
-    int npass[kMaxBatch];
+    int npass[kMaxBatch], fused[kMaxBatch];
     for (int i = 0; i < n; ++i) {
         const int id = ids[i];
         if (id < 0 || id >= (int)slots_.size() || !slots_[id].used) return fail(ELAS_ERR_INVALID_ARG, "slot %d", id);
         vmap_add(pairs, id, dim3(0));
         npass[i] = slots_[id].npass;
+        fused[i] = slots_[id].fused;
     }
     auto mark = [&](int i) {
         if (marks && marks->ev[i]) cudaEventRecord(marks->ev[i], st);
@@ -274,7 +277,7 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
         return s;
     mark(5);
     const PostArgs *post_tabs[4] = {&D->post[0], &D->post[1], &D->post[2], &D->post[3]};
-    if ((s = launch_lr_post_b(&D->lr, &H->lr, post_tabs, npass, pairs, st)) != ELAS_OK) return s;
+    if ((s = launch_lr_post_b(&D->lr, &H->lr, post_tabs, npass, &D->fpost, fused, pairs, st)) != ELAS_OK) return s;
     mark(6);
     return ELAS_OK;
 }

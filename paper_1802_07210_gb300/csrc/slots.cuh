@@ -30,12 +30,14 @@ struct SlotTables {
     DtArgs dt;
     DenseStage dense;
     LrArgs lr;
-    PostArgs post[4];
+    PostArgs post[4];      // post-processing as separate passes (wide gaps)
+    FusedPostArgs fpost;   // or as one fused launch
 };
 
 struct Slot {
     bool used = false;
     int w = 0, h = 0, nc = 0, tri_cap = 0, npass = 0;
+    int fused = 0;  // post-processing by the fused kernel (npass = 0 then)
     elas_params p{};
     char *mem = nullptr;  // one device allocation holding every buffer below
     size_t bytes = 0;

@@ -165,4 +165,11 @@ struct PostArgs {
     int w, h, kind, gap;
 };
 
+// All four passes in one launch (gap widths up to 16).
+struct FusedPostArgs {
+    const int16_t *d;
+    float *out;
+    int w, h, gap, mean;
+};
+
 }  // namespace elas

@@ -148,7 +148,8 @@ def test_postprocess(pairs, name):
     out = host(B.elas_postprocess(dev(ref["lrL"]), prm))
     assert np.abs(out - exp).max() <= POST_TOL
     assert ((out < 0) == (exp < 0)).all()
-    for gap, mean in ((0, 1), (3, 0), (0, 0)):
+    # widths up to 16 run the fused one-launch kernel, wider ones the four passes
+    for gap, mean in ((0, 1), (3, 0), (0, 0), (16, 1), (17, 1), (40, 0), (1, 1)):
         prm = dict(wl.params, ipol_gap_width=gap, filter_adaptive_mean=mean)
         exp = oracle.postprocess(ref["lrL"], prm)
         out = host(B.elas_postprocess(dev(ref["lrL"]), prm))
