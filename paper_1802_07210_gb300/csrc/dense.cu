@@ -2,18 +2,19 @@
 // dense per-pixel argmin of descriptor SAD plus tabulated prior over the
 // grid-vector and plane-neighbourhood candidates (Sec. III.A, Fig. 1(h)).
 //
-// plane_raster_kernel  one warp per triangle (grid-stride), both meshes in one
-//                      launch.  Every lane evaluates the FP32 plane in the
-//                      fixed order.  For each row of the bounding box the
-//                      owned x-range follows from the three integer edge
+// plane_raster_kernel  eight lanes per triangle (grid-stride), both meshes in
+//                      one launch.  Every lane evaluates the FP32 plane in
+//                      the fixed order.  For each row of the bounding box
+//                      the owned x-range follows from the three integer edge
 //                      functions (E >= 0 on owned edges, E >= 1 otherwise);
 //                      each pixel of that range (widened by one) is
 //                      confirmed with the edge functions themselves before
 //                      it is written, so ownership is exactly the top-left
 //                      rule.  One row per lane; triangles whose bounding
-//                      box exceeds kBigArea pixels are listed instead and
-//                      drawn by plane_raster_big_kernel, one CTA each (rows
-//                      over warps, lanes across x), so they leave no tail.
+//                      box exceeds kBigArea pixels are listed instead (in up
+//                      to kBigSplit parts) and drawn by
+//                      plane_raster_big_kernel, one CTA per part (rows over
+//                      warps, lanes across x), so they leave no tail.
 // cell_kernel          one CTA per grid-vector cell (G x G pixels, which share
 //                      one candidate mask) and per reference image.  It
 //                      expands the cell's mask into an ascending candidate
@@ -141,21 +142,29 @@ __device__ __forceinline__ void raster_row(const TriGeom &g, int y, int first, i
     }
 }
 
+constexpr int kRasterGroup = 8;  // lanes per small triangle
+constexpr int kBigSplit = 8;      // CTAs a big triangle is spread over, at most
+
 __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb) {
     const int side = vb.y;
     const RasterSide S = side ? a.s[1] : a.s[0];
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
+    const int gl = threadIdx.x & (kRasterGroup - 1);
+    const int gpb = blockDim.x / kRasterGroup;  // triangles per CTA pass
     const int ntri = side_ntri(S);
-    for (int t = vb.x * wpb + (threadIdx.x >> 5); t < ntri; t += vb.gx * wpb) {
+    for (int t = vb.x * gpb + (int)threadIdx.x / kRasterGroup; t < ntri; t += vb.gx * gpb) {
         const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
         if (g.empty) continue;
         const int rows = g.ymax - g.ymin + 1;
-        if ((g.xmax - g.xmin + 1) * rows > kBigArea) {  // spread over every CTA later
-            if (lane == 0) a.big[atomicAdd(a.nbig, 1)] = (side << 30) | t;
+        if ((g.xmax - g.xmin + 1) * rows > kBigArea) {
+            // drawn by plane_raster_big_kernel, split over up to kBigSplit CTAs
+            const int nsub = min(kBigSplit, (rows + 31) / 32);
+            if (gl == 0) {
+                const int k = atomicAdd(a.nbig, nsub);
+                for (int j = 0; j < nsub; ++j) a.big[k + j] = make_int2((side << 8) | (j << 4) | nsub, t);
+            }
             continue;
         }
-        for (int r = lane; r < rows; r += 32) raster_row(g, g.ymin + r, 0, 1, a.w, a.dmin, a.dmax, S.dplane);
+        for (int r = gl; r < rows; r += kRasterGroup) raster_row(g, g.ymin + r, 0, 1, a.w, a.dmin, a.dmax, S.dplane);
     }
 }
 
@@ -165,18 +174,23 @@ __global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *_
     plane_raster_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-// Big triangles, one CTA each (grid-stride over the list): the CTA's warps
-// take the rows in turn and their lanes stride across x.
+// Big triangles: each list entry is one of the nsub parts of a triangle, one
+// CTA each (grid-stride over the list); part j takes the 8-row groups
+// j, j + nsub, j + 2 nsub, ... whose rows go to the CTA's warps, lanes
+// striding across x.
 __device__ __forceinline__ void plane_raster_big_body(const RasterArgs &a, const VB &vb) {
     const int n = *a.nbig;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     for (int k = vb.x; k < n; k += vb.gx) {
-        const int e = a.big[k];
-        const int side = e >> 30, t = e & ((1 << 30) - 1);
+        const int2 e = a.big[k];
+        const int side = e.x >> 8, part = (e.x >> 4) & 15, nsub = e.x & 15, t = e.y;
         const RasterSide S = side ? a.s[1] : a.s[0];
         const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
         const int rows = g.ymax - g.ymin + 1;
-        for (int r = warp; r < rows; r += wpb) raster_row(g, g.ymin + r, lane, 32, a.w, a.dmin, a.dmax, S.dplane);
+        for (int r0 = part * wpb; r0 < rows; r0 += nsub * wpb) {
+            const int r = r0 + warp;
+            if (r < rows) raster_row(g, g.ymin + r, lane, 32, a.w, a.dmin, a.dmax, S.dplane);
+        }
     }
 }
 
@@ -292,7 +306,7 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
                             }
                             cnt = lo;
                         }
-#pragma unroll 4
+#pragma unroll 8
                         for (int k = sub; k < cnt; k += TPP) {
                             const int d = s_list[k];
                             const int c = (int)sad16(r, __ldg(orow + dir * d));
@@ -347,9 +361,11 @@ static elas_status fill_prior_table(const elas_params *p, int *P) {
     return ELAS_OK;
 }
 
-// Scratch of the rasteriser: the big-triangle list and its counter.
+// Scratch of the rasteriser: the big-triangle list (up to kBigSplit parts
+// per triangle) and its counter.
 size_t raster_scratch_bytes(int ntri_total) {
-    return align_up(sizeof(int32_t) * 4, 256) + align_up(sizeof(int32_t) * (size_t)(ntri_total > 0 ? ntri_total : 1), 256);
+    return align_up(sizeof(int32_t) * 4, 256) +
+           align_up(sizeof(int2) * kBigSplit * (size_t)(ntri_total > 0 ? ntri_total : 1), 256);
 }
 
 // Batched launches keep no memsets: this kernel fills the prior maps of a
@@ -377,7 +393,7 @@ static RasterArgs raster_args(const int16_t *list, const RasterSide *sides, int 
     a.list = list;
     a.nsides = nsides;
     a.nbig = reinterpret_cast<int32_t *>(scratch);
-    a.big = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(scratch) + align_up(sizeof(int32_t) * 4, 256));
+    a.big = reinterpret_cast<int2 *>(reinterpret_cast<char *>(scratch) + align_up(sizeof(int32_t) * 4, 256));
     a.w = w;
     a.h = h;
     a.dmin = p->disp_min;
@@ -400,10 +416,10 @@ static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
     const int maxt = raster_max_ntri(a);
     if (maxt == 0) return ELAS_OK;
     if (cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) return launch_status("memset big count");
-    const int wpb = 8;
+    const int wpb = 256 / kRasterGroup;  // triangles per CTA pass
     int blocks = (maxt + wpb - 1) / wpb;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    plane_raster_kernel<<<dim3(blocks, a.nsides), 32 * wpb, 0, st>>>(a);
+    plane_raster_kernel<<<dim3(blocks, a.nsides), 256, 0, st>>>(a);
     elas_status s = launch_status("plane_raster_kernel");
     if (s != ELAS_OK) return s;
     plane_raster_big_kernel<<<2 * 152, 256, 0, st>>>(a);
@@ -528,7 +544,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         const size_t n8 = ((size_t)d.raster.nsides * d.raster.w * d.raster.h + 7) / 8;
         vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)152 * 4)));
         const int maxt = raster_max_ntri(d.raster);
-        const int wpb = 8;
+        const int wpb = 256 / kRasterGroup;
         int blocks = (maxt + wpb - 1) / wpb;
         if (pairs.n > 1) blocks = (blocks + 2) / 3;
         blocks = max(1, min(blocks, 152 * 16));

@@ -115,7 +115,8 @@ struct RasterArgs {
     const int16_t *list;
     RasterSide s[2];
     int nsides;
-    int32_t *big;   // (side << 30) | triangle, for triangles left to plane_raster_big_kernel
+    int2 *big;      // parts of the triangles left to plane_raster_big_kernel:
+                    // x = (side << 8) | (part << 4) | parts, y = triangle
     int32_t *nbig;  // count of big (zeroed before the launch)
     int w, h, dmin, dmax;
 };
