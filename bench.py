@@ -436,7 +436,6 @@ def main():
     pool = [synth.workload_pair(wl, replica_seed(rank, i), cfg) for i in range(args.pool)]
     imgs = [(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)) for L, R, _ in pool]
     pl = B.Pipeline(w, h, wl.params)
-    pl.set_profiling(True)
     dL = torch.empty((h, w), dtype=torch.int16, device=dev)
     dR = torch.empty_like(dL)
     post = torch.empty((h, w), dtype=torch.float32, device=dev) if wl.postprocess else None
@@ -464,7 +463,6 @@ def main():
 
     # ---- device-resident throughput of the plain path -------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = []
     clocks = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -475,11 +473,21 @@ def main():
         ev[i][0].record(stream)
         step(i)
         ev[i][1].record(stream)
-        stage_ms.append(pl.stats()["stage_ms"])  # events recorded by the library on this stream
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
+    # the same steps again with the library's stage marks on (the marks cost
+    # a few percent, so they are kept out of the headline steps)
+    pl.set_profiling(True)
+    for i in range(2):
+        step(i)
+    stage_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        step(i)
+        stage_ms.append(pl.stats()["stage_ms"])  # events recorded by the library on this stream
+    pl.set_profiling(False)
     total_ms = max_over_ranks(torch, dist, ws, sum(a.elapsed_time(b) for a, b in ev), dev)
     ms_step = total_ms / args.steps
     value = replica_throughput(ws, args.steps, px, total_ms) / 1e6
@@ -517,7 +525,7 @@ def main():
     roof = {"kernel": "cell_kernel (dense argmin, both reference images in one launch)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SAD16/s", "frac": achieved / peak,
             "traffic": None, "algorithmic_evals_per_launch": evals,
-            "time": "mean of CUDA events around the launch, recorded by the library inside every timed step",
+            "time": "mean of CUDA events around the launch, recorded by the library in a second pass of the timed steps (same pairs, same L2 flush)",
             "peak_source": "measured: probe kernel running the same SAD16 sequence on registers over all SMs",
             "probe_variants_gsad16": {str(k): v / 1e9 for k, v in probe.items()},
             "hbm": {"achieved_gbs": dense_bytes / (t_dense * 1e-3) / 1e9, "peak_gbs": hbm_gbs,

@@ -327,6 +327,10 @@ elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const
  * on_gpu = 0 copies the support list to the host and runs elas_triangulate
  * (left and right meshes on two threads).  Both give identical meshes. */
 elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu);
+/* With GPU triangulation the step is captured into a CUDA graph on the
+ * second run with the same buffers and replayed from then on (on = 1, the
+ * default); on = 0 launches every kernel each run. */
+elas_status elas_pipeline_set_graph(elas_pipeline *pl, int32_t on);
 /* on = 1: every run records events between its stages (GPU triangulation
  * only) and elas_pipeline_stats_get reports the stage times. */
 elas_status elas_pipeline_set_profiling(elas_pipeline *pl, int32_t on);

@@ -101,6 +101,7 @@ SIGNATURES = {
     "elas_pipeline_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "elas_pipeline_set_triangulation": (C.c_int, [_P, _I]),
     "elas_pipeline_set_profiling": (C.c_int, [_P, _I]),
+    "elas_pipeline_set_graph": (C.c_int, [_P, _I]),
     "elas_pipeline_stats_get": (C.c_int, [_P, _P]),
     "elas_pipeline_destroy": (None, [_P]),
     "elas_batch_create": (C.c_int, [_I, _P, _P, _P, _P]),

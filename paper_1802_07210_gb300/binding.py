@@ -212,6 +212,9 @@ class Pipeline:
     def set_profiling(self, on=True):
         check(lib().elas_pipeline_set_profiling(self._h, int(bool(on))))
 
+    def set_graph(self, on=True):
+        check(lib().elas_pipeline_set_graph(self._h, int(bool(on))))
+
     def stats(self):
         st = PipelineStats()
         check(lib().elas_pipeline_stats_get(self._h, C.byref(st)))

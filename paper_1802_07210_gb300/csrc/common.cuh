@@ -17,6 +17,15 @@ elas_status launch_status(const char *what);
 elas_status check_params(const elas_params *p, int32_t w, int32_t h);
 
 inline cudaStream_t to_stream(elas_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Records a timing mark on st; while st is being captured into a graph the
+// record becomes an event-record node of the graph.
+inline cudaError_t record_mark(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, st);
+}
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -521,7 +521,7 @@ elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w,
                                ntri_dev, &d);
     if (s != ELAS_OK) return s;
     if ((s = raster_meshes(d.raster, st)) != ELAS_OK) return s;
-    if (after_prior && cudaEventRecord(after_prior, st) != cudaSuccess) return launch_status("prior mark");
+    if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");
     return launch_cells(d.cell, 2, st);
 }
 
@@ -558,7 +558,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
     plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
-    if (after_prior && cudaEventRecord(after_prior, st) != cudaSuccess) return launch_status("prior mark");
+    if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");
     const int total = vmap_total(m_cell);
     if (tpp == 1)
         cell_kernel_b<1><<<total, threads, 0, st>>>(t.cell, m_cell);

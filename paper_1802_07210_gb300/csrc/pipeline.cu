@@ -103,6 +103,11 @@ struct elas_pipeline {
     int profiling = 0;
     bool marked = false;
     cudaEvent_t marks[7] = {};
+    // graph replay of the step (GPU triangulation)
+    int use_graph = 1;
+    cudaStream_t work = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> graph_sig;
     // last run
     elas_pipeline_stats stats{};
     std::vector<int32_t> triL_v, triR_v;
@@ -118,6 +123,9 @@ template <class T> cudaError_t dalloc(T **p, size_t bytes) {
 void release(elas_pipeline *pl) {
     if (!pl) return;
     delete pl->helper;
+    if (pl->work) cudaStreamSynchronize(pl->work);
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->work) cudaStreamDestroy(pl->work);
     for (cudaEvent_t &e : pl->marks)
         if (e) cudaEventDestroy(e);
     void *dev[] = {pl->img, pl->descL, pl->descR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
@@ -197,16 +205,19 @@ extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_par
         release(pl);
         return fail(ELAS_ERR_NO_MEMORY, "helper thread");
     }
+    if (cudaStreamCreateWithFlags(&pl->work, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        release(pl);
+        return fail(ELAS_ERR_NO_MEMORY, "pipeline capture stream");
+    }
     *out = pl;
     return ELAS_OK;
 }
 
-extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR, int32_t pitch,
-                                         int16_t *dL, int16_t *dR, float *post, elas_stream stream) {
+// The whole step for one pair on stream st (validated arguments).
+static elas_status run_step(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR, int32_t pitch, int16_t *dL,
+                            int16_t *dR, float *post, cudaStream_t st) {
     using namespace elas;
-    if (!pl || !imgL || !imgR || !dL) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
-    if (pitch < pl->w) return fail(ELAS_ERR_INVALID_ARG, "pitch %d < width %d", pitch, pl->w);
-    cudaStream_t st = to_stream(stream);
     const int w = pl->w, h = pl->h;
     const elas_params *p = &pl->p;
     int16_t *list = reinterpret_cast<int16_t *>(pl->countlist + 16);
@@ -215,7 +226,7 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
     pl->last_stream = st;
     const bool prof = pl->profiling && pl->gpu_tri;
     auto mark = [&](int i) {
-        if (prof) cudaEventRecord(pl->marks[i], st);
+        if (prof) record_mark(pl->marks[i], st);
     };
     pl->marked = prof;
     mark(0);
@@ -274,6 +285,54 @@ extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL,
     return ELAS_OK;
 }
 
+// With GPU triangulation nothing in the step depends on the host, so the
+// step is captured once per set of buffers into a CUDA graph (recorded on an
+// internal stream, which executes nothing while capturing) and replayed on
+// the caller's stream: one launch instead of ~30 kernels and memsets.  The
+// first run with new buffers goes eagerly.
+static elas_status run_graph(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR, int32_t pitch, int16_t *dL,
+                             int16_t *dR, float *post, cudaStream_t st) {
+    using namespace elas;
+    const std::vector<const void *> sig{imgL, imgR, reinterpret_cast<const void *>((intptr_t)pitch), dL, dR, post,
+                                        reinterpret_cast<const void *>((intptr_t)pl->profiling)};
+    if (sig != pl->graph_sig) {
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        pl->exec = nullptr;
+        pl->graph_sig = sig;
+        return run_step(pl, imgL, imgR, pitch, dL, dR, post, st);  // eager
+    }
+    if (!pl->exec) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(pl->work, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return launch_status("begin pipeline capture");
+        elas_status s = run_step(pl, imgL, imgR, pitch, dL, dR, post, pl->work);
+        const cudaError_t e = cudaStreamEndCapture(pl->work, &g);
+        if (s == ELAS_OK && e != cudaSuccess) s = fail(ELAS_ERR_CUDA, "pipeline capture: %s", cudaGetErrorString(e));
+        if (s == ELAS_OK && cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) {
+            pl->exec = nullptr;
+            s = launch_status("pipeline graph instantiate");
+        }
+        if (g) cudaGraphDestroy(g);
+        if (s != ELAS_OK) {
+            pl->graph_sig.clear();
+            return s;
+        }
+    }
+    if (cudaGraphLaunch(pl->exec, st) != cudaSuccess) return launch_status("pipeline graph launch");
+    pl->last_stream = st;
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_pipeline_run(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR, int32_t pitch,
+                                         int16_t *dL, int16_t *dR, float *post, elas_stream stream) {
+    using namespace elas;
+    if (!pl || !imgL || !imgR || !dL) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
+    if (pitch < pl->w) return fail(ELAS_ERR_INVALID_ARG, "pitch %d < width %d", pitch, pl->w);
+    cudaStream_t st = to_stream(stream);
+    if (pl->gpu_tri && pl->use_graph) return run_graph(pl, imgL, imgR, pitch, dL, dR, post, st);
+    return run_step(pl, imgL, imgR, pitch, dL, dR, post, st);
+}
+
 extern "C" elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const uint8_t *imgR,
                                               int16_t *dL, int16_t *dR, float *post, elas_stream stream) {
     using namespace elas;
@@ -299,6 +358,15 @@ extern "C" elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *
 extern "C" elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu) {
     if (!pl) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL pipeline");
     pl->gpu_tri = on_gpu ? 1 : 0;
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_pipeline_set_graph(elas_pipeline *pl, int32_t on) {
+    if (!pl) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL pipeline");
+    if ((on ? 1 : 0) != pl->use_graph) {
+        pl->use_graph = on ? 1 : 0;
+        pl->graph_sig.clear();  // the next graph run starts eagerly
+    }
     return ELAS_OK;
 }
 

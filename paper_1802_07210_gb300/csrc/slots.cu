@@ -259,7 +259,7 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
         fused[i] = slots_[id].fused;
     }
     auto mark = [&](int i) {
-        if (marks && marks->ev[i]) cudaEventRecord(marks->ev[i], st);
+        if (marks && marks->ev[i]) record_mark(marks->ev[i], st);
     };
     const SlotTables *D = dev_tab_;
     const SlotTables *H = host_tab_;

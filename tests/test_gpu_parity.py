@@ -167,8 +167,13 @@ def test_pipeline_end_to_end(pairs, name):
     dL = torch.empty((h, w), dtype=torch.int16, device="cuda")
     dR = torch.empty_like(dL)
     post = torch.empty((h, w), dtype=torch.float32, device="cuda")
-    for _ in range(2):  # a second run reuses every buffer
-        pl.run(dev(L), dev(R), dL, dR, post)
+    tL, tR = dev(L), dev(R)
+    # run 1 eager, run 2 captured into a graph, runs 3-4 replayed, run 5 eager
+    for graph in (True, True, True, True, False):
+        pl.set_graph(graph)
+        for t in (dL, dR):
+            t.fill_(-7)
+        pl.run(tL, tR, dL, dR, post)
         np.testing.assert_array_equal(host(dL), ref["lrL"])
         np.testing.assert_array_equal(host(dR), ref["lrR"])
         assert np.abs(host(post) - ref["post"]).max() <= POST_TOL
