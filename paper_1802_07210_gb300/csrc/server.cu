@@ -45,7 +45,6 @@ struct Request {
 struct Lane {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
-    int32_t *counter = nullptr;    // device
     int32_t *h_counters = nullptr; // pinned, capacity * 4
     std::vector<Request *> reqs;
     bool busy = false;
@@ -77,6 +76,11 @@ struct elas_server {
     std::deque<elas_server_result> results;
     bool stop = false;
     elas_server_stats stats{};
+    // captured waves, by composition (slot, generation, post passes per slot);
+    // a composition is captured the second time it is launched
+    cudaStream_t cap_st = nullptr;
+    std::map<std::vector<uint32_t>, cudaGraphExec_t> graphs;
+    std::map<std::vector<uint32_t>, int> seen;
     // plain mode
     std::map<std::vector<int>, elas_pipeline *> pipelines;
     std::thread th;
@@ -163,6 +167,43 @@ int admit(elas_server *s, Request *r, cudaStream_t st, int *error) {
     return id;
 }
 
+void drop_graphs(elas_server *s) {
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    s->seen.clear();
+}
+
+// The kernels of a wave: replayed from a graph when this composition was
+// launched before, else eagerly (captured on its second launch).
+elas_status launch_kernels(elas_server *s, const std::vector<int> &ids, const Knobs &knobs, cudaStream_t st) {
+    std::vector<uint32_t> key;
+    for (int id : ids) {
+        const Slot &sl = s->pool[id];
+        key.insert(key.end(), {(uint32_t)id, sl.generation, (uint32_t)sl.npass, (uint32_t)sl.fused});
+    }
+    auto it = s->graphs.find(key);
+    if (it != s->graphs.end()) {
+        if (cudaGraphLaunch(it->second, st) != cudaSuccess) return launch_status("wave graph launch");
+        return ELAS_OK;
+    }
+    if (s->seen.size() > 8192) s->seen.clear();
+    if (s->seen[key]++ == 0 || s->graphs.size() >= 512)
+        return s->pool.launch(ids.data(), (int)ids.size(), knobs, st, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return launch_status("begin wave capture");
+    elas_status e = s->pool.launch(ids.data(), (int)ids.size(), knobs, s->cap_st, nullptr);
+    const cudaError_t ce = cudaStreamEndCapture(s->cap_st, &g);
+    if (e == ELAS_OK && ce != cudaSuccess) e = fail(ELAS_ERR_CUDA, "wave capture: %s", cudaGetErrorString(ce));
+    if (e == ELAS_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) e = launch_status("wave graph instantiate");
+    if (g) cudaGraphDestroy(g);
+    if (e != ELAS_OK) return e;
+    s->graphs[key] = exec;
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return launch_status("wave graph launch");
+    return ELAS_OK;
+}
+
 elas_status launch_wave(elas_server *s, Lane &ln) {
     const Knobs knobs;
     std::vector<int> ids;
@@ -179,7 +220,7 @@ elas_status launch_wave(elas_server *s, Lane &ln) {
             return launch_status("request images to device");
     }
     if ((e = s->pool.upload(ln.st)) != ELAS_OK) return e;
-    if ((e = s->pool.launch(ids.data(), (int)ids.size(), knobs, ln.st, ln.counter)) != ELAS_OK) return e;
+    if ((e = launch_kernels(s, ids, knobs, ln.st)) != ELAS_OK) return e;
     for (Request *r : ln.reqs) {
         const Slot &sl = s->pool[r->slot];
         const size_t npx = (size_t)sl.w * sl.h;
@@ -272,8 +313,9 @@ void run_batched(elas_server *s) {
         if (s->stop && s->queue.empty() && !busy) return;
         if (launched) continue;
         if (busy) {
+            // waves in flight: poll their events again right away
             g.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            std::this_thread::yield();
         } else if (s->queue.empty()) {
             s->cv_sched.wait_for(g, std::chrono::milliseconds(2));
         } else {
@@ -339,10 +381,11 @@ void release(elas_server *s) {
     for (Lane &ln : s->lanes) {
         if (ln.st) cudaStreamSynchronize(ln.st);
         if (ln.done) cudaEventDestroy(ln.done);
-        if (ln.counter) cudaFree(ln.counter);
         if (ln.h_counters) cudaFreeHost(ln.h_counters);
         if (ln.st) cudaStreamDestroy(ln.st);
     }
+    drop_graphs(s);
+    if (s->cap_st) cudaStreamDestroy(s->cap_st);
     for (auto &kv : s->pipelines) elas_pipeline_destroy(kv.second);
     for (Request *r : s->queue) delete r;
     delete s;
@@ -408,12 +451,16 @@ extern "C" elas_status elas_server_create(const elas_server_config *cfg, elas_se
         const size_t cb = sizeof(int32_t) * 4 * (size_t)std::max(1, s->cfg.max_slots);
         if (cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(reinterpret_cast<void **>(&ln.counter), 256) != cudaSuccess ||
             cudaMallocHost(reinterpret_cast<void **>(&ln.h_counters), cb) != cudaSuccess) {
             cudaGetLastError();
             release(s);
             return fail(ELAS_ERR_NO_MEMORY, "server lanes");
         }
+    }
+    if (cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        release(s);
+        return fail(ELAS_ERR_NO_MEMORY, "server capture stream");
     }
     s->stats.hbm_budget_bytes = s->budget;
     try {

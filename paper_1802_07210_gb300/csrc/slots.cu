@@ -114,7 +114,9 @@ elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStrea
     if (k < 0) return fail(ELAS_ERR_CAPACITY, "all %d slots in use", (int)slots_.size());
     if ((s = wait_mirror()) != ELAS_OK) return s;
     Slot &sl = slots_[k];
+    const uint32_t gen = sl.generation + 1;
     sl = Slot();
+    sl.generation = gen;
     sl.w = w;
     sl.h = h;
     sl.p = *p;
@@ -173,7 +175,9 @@ void SlotPool::remove(int id, cudaStream_t free_stream) {
     else
         cudaFree(sl.mem);
     bytes_in_use_ -= sl.bytes;
+    const uint32_t gen = sl.generation;
     sl = Slot();
+    sl.generation = gen;
 }
 
 elas_status SlotPool::write_records(int id) {
@@ -248,6 +252,7 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     if (n < 1) return ELAS_OK;
     if (n > kMaxBatch) return fail(ELAS_ERR_CAPACITY, "%d pairs in one wave (at most %d)", n, kMaxBatch);
     if (dirty_hi_ >= dirty_lo_) return fail(ELAS_ERR_INTERNAL, "slot records changed without an upload");
+    if (!counter) counter = dev_counters_ + 4 * ids[0] + 3;
     VMap pairs;
     vmap_clear(pairs, (int)sizeof(SlotTables));
     int npass[kMaxBatch], fused[kMaxBatch];

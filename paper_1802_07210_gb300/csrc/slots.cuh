@@ -57,6 +57,7 @@ struct Slot {
     float *io_post = nullptr;
     bool post_on = false;
     bool async_mem = false;  // memory from the stream-ordered allocator
+    uint32_t generation = 0;  // changes whenever the slot's buffers do
 };
 
 // Event marks of a wave (tuner, profiling); NULL entries are skipped.  The
@@ -89,7 +90,10 @@ class SlotPool {
                        bool post_on, float *post);
     // Copies changed records to the device, on `st`.
     elas_status upload(cudaStream_t st);
-    // The whole path for the slots ids[0..n-1]; counter = one device int.
+    // The whole path for the slots ids[0..n-1]; counter = one device int for
+    // the triangulation's queue, or NULL for the first slot's spare counter
+    // (a slot is in one wave at a time, so waves on different streams and
+    // graphs captured from them never share it).
     elas_status launch(const int *ids, int n, const Knobs &k, cudaStream_t st, int32_t *counter,
                        const StageMarks *marks = nullptr);
     // Counters of every slot to pinned host memory (after launch, same
