@@ -224,6 +224,39 @@ def test_uniform_batch_of_many_pairs():
     b.close()
 
 
+def test_batch_of_the_maximum_size():
+    """256 pairs, the most one batch takes: small pairs of varied sizes and
+    disparity ranges (ragged widths and heights), every eighth one textureless
+    (no support point, an empty triangulation, every pixel invalid). Each
+    pair's maps equal the oracle's for that pair alone."""
+    B = _B()
+    shapes = [(48, 40, 16), (37, 29, 16), (64, 48, 32), (100, 30, 24), (29, 61, 8), (80, 20, 48)]
+    items = []
+    for i in range(256):
+        w, h, D = shapes[i % len(shapes)]
+        wl = synth.scaled_workload(w, h, D)
+        if i % 8 == 7:
+            L = np.full((h, w), 40 + i % 100, np.uint8)
+            R = L.copy()
+        else:
+            L, R, _ = synth.workload_pair(wl, i, 11)
+        items.append(dict(name="pair%d_%dx%d" % (i, w, h), L=L, R=R, prm=dict(wl.params), post=False,
+                          ref=oracle.pipeline(L, R, wl.params, postprocess_on=False)))
+    b = _batch(items)
+    dL, dR, post = _alloc(items)
+    for run in range(2):
+        for t in dL + dR:
+            t.fill_(-7)
+        b.run([dev(it["L"]) for it in items], [dev(it["R"]) for it in items], dL, dR)
+        _check(items, dL, dR, post, "256 pairs run %d" % run)
+    st = b.stats()
+    for i, it in enumerate(items):
+        assert st["n_support"][i] == len(it["ref"]["list"]), it["name"]
+        if i % 8 == 7:
+            assert st["n_support"][i] == 0 and (host(dL[i]) == -1).all()
+    b.close()
+
+
 def test_invalid_batches():
     B = _B()
     prm = synth.SMALL_320.params
