@@ -611,29 +611,133 @@ struct DtBlockShared {
     int64_t rn[32], rd[32];
     unsigned long long key[32];
     int rs[kDtMaxRows], rlen[kDtMaxRows + 1], cnt;
+    unsigned fmin[3];  // least float key of a selection (three buffers, used in turn)
+    int nband[3];      // band members listed by a selection
+    int4 win;          // winner of an exactly ordered band
 };
+
+// Float filter of the pencil order (CTA pass).  With coordinates below 2^14
+// the key (N, D) of every candidate fits in 32 bits (|N|, |D| < 2^31) and
+// two keys compare exactly through 64-bit products.  The float
+// f = fl(N) / fl(D) (two conversions rounded to nearest, one division within
+// 2 ulp) is within 2^-21 |t| of t = N / D, so the exact winner w (least t)
+// has f_w - f_min <= 2^-21 (|f_w| + |f_min|) + rounding, f_min the least f
+// over the candidates: every candidate that can win lies in the band
+// f - f_min <= 2^-17 (|f| + |f_min|).  A band of one is the winner; a larger
+// band (cocircular candidates, or nearly) is ordered exactly.
+constexpr int kDtBandCap = 32;
+
+__device__ __forceinline__ unsigned dt_fbits(float f) {  // monotone in f (no NaN)
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float dt_fbits_value(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ float dt_fkey(const DtKey<int> &k) { return __fdividef((float)k.N, (float)k.D); }
+__device__ __forceinline__ bool dt_in_band(float f, float fmin) {
+    return f - fmin <= 0x1p-17f * (fabsf(f) + fabsf(fmin));
+}
+
+// Does c2 (key k2) beat c1 (key k1)?  32-bit keys, 64-bit products.
+__device__ __forceinline__ bool dt_key_better_w(const DtKey<int> &k1, const DtKey<int> &k2, const int4 &p,
+                                                const int4 &e, const int4 &c1, const int4 &c2, int side) {
+    const int64_t l = (int64_t)k2.N * k1.D, r = (int64_t)k1.N * k2.D;
+    if (l != r) return l < r;
+    const int s = side > 0 ? dt_incircle<int64_t>(p, e, c1, c2) : dt_incircle<int64_t>(p, c1, e, c2);
+    return s > 0 || (s == 0 && c2.z < c1.z);
+}
+
+// CTA-wide Delaunay third vertex of edge (p, e) on `side`: each thread
+// offers its candidates through each(visit) (called twice), thread 0 also
+// the seed (w = 0: none).  Pass 1 finds the least float key (one warp
+// reduction and a shared atomic), pass 2 has every thread take the exact
+// best of its candidates in the band and list it; a single listed candidate
+// is the winner, else warp 0 orders the list exactly (the whole CTA when it
+// overflows).  par: the caller's turn counter (the same on every thread).
+// Thread 0 resets the next call's buffers before this call's first barrier:
+// their last readers (two calls back) have passed the previous call's first
+// barrier, and the next call writes them only after this call's.
+template <typename Each>
+__device__ int4 dt_block_select(Each each, const int4 &p, const int4 &e, int side, const int4 &seed,
+                                DtBlockShared &sh, int &par) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int b = par, nxt = par == 2 ? 0 : par + 1;
+    par = nxt;
+    if (tid == 0) {
+        sh.fmin[nxt] = 0xFFFFFFFFu;
+        sh.nband[nxt] = 0;
+    }
+    auto usable = [&](const int4 &q) { return q.w && q.z != e.z && q.z != p.z; };
+    float fl = __int_as_float(0x7F800000);  // +inf
+    each([&](const int4 &q) {
+        if (!usable(q)) return;
+        const DtKey<int> k = dt_key<int>(p, e, q, side);
+        if (k.D > 0) fl = fminf(fl, dt_fkey(k));
+    });
+    if (tid == 0 && usable(seed)) {
+        const DtKey<int> k = dt_key<int>(p, e, seed, side);
+        if (k.D > 0) fl = fminf(fl, dt_fkey(k));
+    }
+    const unsigned kb = __reduce_min_sync(0xFFFFFFFFu, fl == __int_as_float(0x7F800000) ? 0xFFFFFFFFu : dt_fbits(fl));
+    if (lane == 0 && kb != 0xFFFFFFFFu) atomicMin(&sh.fmin[b], kb);
+    __syncthreads();
+    const unsigned kmin = sh.fmin[b];
+    if (kmin == 0xFFFFFFFFu) return make_int4(0, 0, 0, 0);  // uniform: no candidate on this side
+    const float fmin = dt_fbits_value(kmin);
+    int4 best = make_int4(0, 0, 0, 0);
+    DtKey<int> bk{0, 1};
+    auto visit = [&](const int4 &q) {
+        if (!usable(q)) return;
+        const DtKey<int> k = dt_key<int>(p, e, q, side);
+        if (k.D <= 0 || !dt_in_band(dt_fkey(k), fmin)) return;
+        if (!best.w || dt_key_better_w(bk, k, p, e, best, q, side)) {
+            best = q;
+            bk = k;
+        }
+    };
+    each(visit);
+    if (tid == 0) visit(seed);
+    if (best.w) {
+        const int pos = atomicAdd(&sh.nband[b], 1);
+        if (pos < kDtBandCap) {
+            sh.red[pos] = best;
+            sh.rn[pos] = bk.N;
+            sh.rd[pos] = bk.D;
+        }
+    }
+    __syncthreads();
+    const int nb = sh.nband[b];
+    if (nb == 1) return sh.red[0];
+    if (nb > kDtBandCap)
+        return dt_block_best(best, DtKey<int64_t>{bk.N, bk.D}, p, e, side, sh.red, sh.rn, sh.rd);
+    if (tid < 32) {
+        int4 c = lane < nb ? sh.red[lane] : make_int4(0, 0, 0, 0);
+        DtKey<int64_t> k{lane < nb ? sh.rn[lane] : 0, lane < nb ? sh.rd[lane] : 1};
+        c = dt_warp_key_best(c, k, p, e, side);
+        if (lane == 0) sh.win = c;
+    }
+    __syncthreads();
+    return sh.win;
+}
 
 // Best third vertex for edge (p, cur) on `side`, over the cache (cand, k) or,
 // with cand == NULL, over every alive point.
 __device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, const int4 &cur, int side,
-                                              const int4 *cand, int k, int n, DtBlockShared &sh) {
-    int4 best = make_int4(0, 0, 0, 0);
-    DtKey<int64_t> bk{0, 1};
-    auto consider = [&](const int4 &q) {
-        if (q.z == cur.z || q.z == p.z || !q.w) return;
-        const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
-        if (qk.D <= 0) return;
-        if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
-            best = q;
-            bk = qk;
-        }
-    };
-    if (cand) {
-        for (int j = threadIdx.x; j < k; j += blockDim.x) consider(cand[j]);
-    } else {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) consider(S.pts[j]);
-    }
-    return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
+                                              const int4 *cand, int k, int n, DtBlockShared &sh, int &par) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int4 none = make_int4(0, 0, 0, 0);
+    if (cand)
+        return dt_block_select(
+            [&](auto &&v) {
+                for (int j = tid; j < k; j += nth) v(cand[j]);
+            },
+            p, cur, side, none, sh, par);
+    return dt_block_select(
+        [&](auto &&v) {
+            for (int j = tid; j < n; j += nth) v(S.pts[j]);
+        },
+        p, cur, side, none, sh, par);
 }
 
 // Exact step for edge (p, cur) on `side` without the radius limit.  Only
@@ -648,7 +752,7 @@ __device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, co
 // replaced by its half-plane (the part of the disc beyond the chord p-cur
 // is then thinner than a pixel, and only that side's points are candidates).
 __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int4 &p, const int4 &cur, int side,
-                                     const int4 &bc, DtBlockShared &sh, int *r_start, int *r_len) {
+                                     const int4 &bc, DtBlockShared &sh, int *r_start, int *r_len, int &par) {
     const int tid = threadIdx.x, nth = blockDim.x;
     float ccx = 0.0f, ccy = 0.0f, rad = 0.0f;
     bool disc = false;
@@ -711,22 +815,14 @@ __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int
     // each warp takes cell rows in turn; its lanes stride over the row's
     // contiguous range of the grid-sorted points
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    int4 best = bc;
-    DtKey<int64_t> bk = bc.w ? dt_key<int64_t>(p, cur, bc, side) : DtKey<int64_t>{0, 1};
-    for (int cy = warp; cy < a.gh; cy += nwarps) {
-        const int s0 = r_start[cy], len = r_len[cy];
-        for (int j = lane; j < len; j += 32) {
-            const int4 q = S.pts[s0 + j];
-            if (!q.w || q.z == cur.z || q.z == p.z) continue;
-            const DtKey<int64_t> qk = dt_key<int64_t>(p, cur, q, side);
-            if (qk.D <= 0) continue;
-            if (!best.w || dt_key_better<int64_t>(bk, qk, p, cur, best, q, side)) {
-                best = q;
-                bk = qk;
+    return dt_block_select(
+        [&](auto &&v) {
+            for (int cy = warp; cy < a.gh; cy += nwarps) {
+                const int s0 = r_start[cy], len = r_len[cy];
+                for (int j = lane; j < len; j += 32) v(S.pts[s0 + j]);
             }
-        }
-    }
-    return dt_block_best(best, bk, p, cur, side, sh.red, sh.rn, sh.rd);
+        },
+        p, cur, side, bc, sh, par);
 }
 
 __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, int R, int4 *cand,
@@ -744,6 +840,11 @@ __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, 
 __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4 &p, int n, int4 *cand, int R, int k,
                              int *written, int32_t *out, DtBlockShared &sh, int *r_start, int *r_len) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x;
+    int par = 0;  // selection buffers: cleared here, before the barriers below
+    if (tid == 0) {
+        sh.fmin[0] = sh.fmin[1] = sh.fmin[2] = 0xFFFFFFFFu;
+        sh.nband[0] = sh.nband[1] = sh.nband[2] = 0;
+    }
     // nearest neighbour: a cached point is nearer than every point outside
     // the cache, so a non-empty cache holds it; else one pass over all points
     unsigned long long key = ~0ull;
@@ -786,7 +887,7 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
         int4 b = make_int4(0, 0, 0, 0);
         for (;;) {
             if (!cand || k > kDtCandCap2) break;
-            b = dt_block_step(S, p, cur, side, cand, k, n, sh);
+            b = dt_block_step(S, p, cur, side, cand, k, n, sh, par);
             const bool small =
                 b.w && (side > 0 ? dt_small_circle(p, cur, b, R) : dt_small_circle(p, b, cur, R));
             if (small) return b;
@@ -794,8 +895,8 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
             R = kDtRadius2;  // refill the cache once with the larger disc
             k = dt_block_gather(a, S, p, R, cand, sh);
         }
-        if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_len);
-        return dt_block_step(S, p, cur, side, nullptr, 0, n, sh);
+        if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_len, par);
+        return dt_block_step(S, p, cur, side, nullptr, 0, n, sh, par);
     };
     int4 cur = first;
     bool closed = false;
