@@ -563,6 +563,8 @@ constexpr int kDtRadius1 = 96;     // first cache radius of the CTA pass
 constexpr int kDtRadius2 = 192;    // its second, when a step's circle does not fit the first
 constexpr int kDtCandCap2 = 3072;  // candidates cached per CTA (48 KB)
 constexpr int kDtMaxRows = 64;     // cell rows a radius-192 disc spans, with margin
+constexpr int kDtBlockThreads = 256;  // threads of a CTA-pass CTA
+constexpr int kDtBlocksPerSM = 3;     // CTA-pass CTAs resident per SM (85 registers a thread)
 static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "the CTA pass's disc must fit the row table");
 
 // CTA reduction of the threads' (best, key) under the pencil order: each
@@ -652,7 +654,8 @@ __device__ __forceinline__ bool dt_key_better_w(const DtKey<int> &k1, const DtKe
 // offers its candidates through each(visit) (called twice), thread 0 also
 // the seed (w = 0: none).  Pass 1 finds the least float key (one warp
 // reduction and a shared atomic), pass 2 has every thread take the exact
-// best of its candidates in the band and list it; a single listed candidate
+// best of its candidates in the band (its least one, unless its second
+// least is in the band too) and list it; a single listed candidate
 // is the winner, else warp 0 orders the list exactly (the whole CTA when it
 // overflows).  par: the caller's turn counter (the same on every thread).
 // Thread 0 resets the next call's buffers before this call's first barrier:
@@ -669,16 +672,26 @@ __device__ int4 dt_block_select(Each each, const int4 &p, const int4 &e, int sid
         sh.nband[nxt] = 0;
     }
     auto usable = [&](const int4 &q) { return q.w && q.z != e.z && q.z != p.z; };
-    float fl = __int_as_float(0x7F800000);  // +inf
-    each([&](const int4 &q) {
+    // each thread keeps its least float key (with its candidate) and its
+    // second least
+    const float inf = __int_as_float(0x7F800000);
+    float fl = inf, f2 = inf;
+    int4 q1 = make_int4(0, 0, 0, 0);
+    auto offer = [&](const int4 &q) {
         if (!usable(q)) return;
         const DtKey<int> k = dt_key<int>(p, e, q, side);
-        if (k.D > 0) fl = fminf(fl, dt_fkey(k));
-    });
-    if (tid == 0 && usable(seed)) {
-        const DtKey<int> k = dt_key<int>(p, e, seed, side);
-        if (k.D > 0) fl = fminf(fl, dt_fkey(k));
-    }
+        if (k.D <= 0) return;
+        const float f = dt_fkey(k);
+        if (f < fl) {
+            f2 = fl;
+            fl = f;
+            q1 = q;
+        } else if (f < f2) {
+            f2 = f;
+        }
+    };
+    each(offer);
+    if (tid == 0) offer(seed);
     const unsigned kb = __reduce_min_sync(0xFFFFFFFFu, fl == __int_as_float(0x7F800000) ? 0xFFFFFFFFu : dt_fbits(fl));
     if (lane == 0 && kb != 0xFFFFFFFFu) atomicMin(&sh.fmin[b], kb);
     __syncthreads();
@@ -687,17 +700,26 @@ __device__ int4 dt_block_select(Each each, const int4 &p, const int4 &e, int sid
     const float fmin = dt_fbits_value(kmin);
     int4 best = make_int4(0, 0, 0, 0);
     DtKey<int> bk{0, 1};
-    auto visit = [&](const int4 &q) {
-        if (!usable(q)) return;
-        const DtKey<int> k = dt_key<int>(p, e, q, side);
-        if (k.D <= 0 || !dt_in_band(dt_fkey(k), fmin)) return;
-        if (!best.w || dt_key_better_w(bk, k, p, e, best, q, side)) {
-            best = q;
-            bk = k;
+    // the band test is increasing in f: with the second least key outside
+    // the band only the least can be in it; else the thread offers again
+    if (q1.w && dt_in_band(fl, fmin)) {
+        if (f2 != inf && dt_in_band(f2, fmin)) {
+            auto visit = [&](const int4 &q) {
+                if (!usable(q)) return;
+                const DtKey<int> k = dt_key<int>(p, e, q, side);
+                if (k.D <= 0 || !dt_in_band(dt_fkey(k), fmin)) return;
+                if (!best.w || dt_key_better_w(bk, k, p, e, best, q, side)) {
+                    best = q;
+                    bk = k;
+                }
+            };
+            each(visit);
+            if (tid == 0) visit(seed);
+        } else {
+            best = q1;
+            bk = dt_key<int>(p, e, q1, side);
         }
-    };
-    each(visit);
-    if (tid == 0) visit(seed);
+    }
     if (best.w) {
         const int pos = atomicAdd(&sh.nband[b], 1);
         if (pos < kDtBandCap) {
@@ -819,7 +841,16 @@ __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int
         [&](auto &&v) {
             for (int cy = warp; cy < a.gh; cy += nwarps) {
                 const int s0 = r_start[cy], len = r_len[cy];
-                for (int j = lane; j < len; j += 32) v(S.pts[s0 + j]);
+                int j = lane;
+                for (; j + 96 < len; j += 128) {  // four loads in flight
+                    const int4 q0 = S.pts[s0 + j], q1 = S.pts[s0 + j + 32], q2 = S.pts[s0 + j + 64],
+                               q3 = S.pts[s0 + j + 96];
+                    v(q0);
+                    v(q1);
+                    v(q2);
+                    v(q3);
+                }
+                for (; j < len; j += 32) v(S.pts[s0 + j]);
             }
         },
         p, cur, side, bc, sh, par);
@@ -992,7 +1023,7 @@ __device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, 
 
 // One pair: the CTAs of side blockIdx.y stride over that side's queue (the
 // group pass's, or with second_queue the warp pass's).
-__global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a, int second_queue) {
+__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block_kernel(DtArgs a, int second_queue) {
     extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows
     __shared__ DtBlockShared sh;
     int *r_start = reinterpret_cast<int *>(s_cand + kDtCandCap2);
@@ -1008,7 +1039,7 @@ __global__ void __launch_bounds__(1024) dt_pass_block_kernel(DtArgs a, int secon
 // concatenated in launch order and the CTAs take their entries one at a
 // time from one atomic counter (zeroed by dt_init_kernel_b), so the long
 // stars of one pair overlap the work of all the others.
-__global__ void __launch_bounds__(1024) dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides,
+__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides,
                                                                int32_t *counter) {
     extern __shared__ int4 s_cand[];
     __shared__ DtBlockShared sh;
@@ -1252,7 +1283,7 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel shared memory attribute");
     (void)smem2;
-    dt_pass_block_kernel<<<dim3(152 * 4, nsides), 256, smem3, st>>>(a, 0);
+    dt_pass_block_kernel<<<dim3(152 * kDtBlocksPerSM, nsides), kDtBlockThreads, smem3, st>>>(a, 0);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_emit_big_kernel<<<dim3(152, nsides), 256, 0, st>>>(a);
@@ -1331,7 +1362,7 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
     dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    dt_pass_block_kernel_b<<<nsm * 4, 256, smem3, st>>>(tab, pairs, nsides, counter);
+    dt_pass_block_kernel_b<<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter);
     dt_tri_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
     dt_emit_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_emit_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(tab, m_big);
