@@ -1,9 +1,9 @@
 // Descriptors: Sobel gradient images quantised to uint8 and sampled into a
 // 16-byte descriptor per pixel (Sec. III.A, Fig. 1(b-d); Sec. VI.A).
 //
-// One CTA produces a 32xTH tile of descriptors (TH = 8 for the one-pair
-// launch; 4, 8 or 16 in batched launches, chosen by the tuner).  The image
-// tile with a 3-pixel halo is staged in shared memory, the quantised du/dv
+// One CTA produces up to four 32xTH tiles of descriptors, one above the other
+// (TH = 8 for the one-pair launch; 4, 8 or 16 in batched launches, chosen by
+// the tuner).  The image tile with a 3-pixel halo is staged in shared memory, the quantised du/dv
 // planes of the tile with a 2-pixel halo are computed once into shared
 // memory, and every thread assembles its pixel's 16 bytes and writes them as
 // one 16-byte store (a warp writes 512 contiguous bytes).
@@ -18,7 +18,12 @@ __device__ __forceinline__ int quantise(int s) {
     return q < 1 ? 1 : (q > 255 ? 255 : q);
 }
 
-// TH = tile height (image rows per CTA): one of 4, 8, 16.
+// TH = tile height (image rows of a tile): one of 4, 8, 16.  A CTA makes
+// kDescTiles vertically adjacent tiles in turn; the image bytes of the next
+// tile are loaded into registers while the current one is computed, so the
+// loads of one tile overlap the work of the previous one.
+constexpr int kDescTiles = 4;
+
 template <int TH>
 __device__ __forceinline__ void descriptor_body(const DescArgs &a, const VB &vb) {
     const uint8_t *img = vb.z ? a.imgR : a.imgL;
@@ -27,55 +32,74 @@ __device__ __forceinline__ void descriptor_body(const DescArgs &a, const VB &vb)
 
     constexpr int IW = kDescTW + 6, IH = TH + 6;  // image tile with halo 3
     constexpr int QW = kDescTW + 4, QH = TH + 4;  // gradient tile with halo 2
+    constexpr int NT = kDescTW * TH, NI = IW * IH;
+    constexpr int PER = (NI + NT - 1) / NT;  // image bytes a thread loads per tile
     __shared__ int16_t s_img[IH][IW];
     __shared__ uint8_t s_du[QH][QW];
     __shared__ uint8_t s_dv[QH][QW];
 
-    const int x0 = vb.x * kDescTW, y0 = vb.y * TH;
+    const int x0 = vb.x * kDescTW;
     const int tid = threadIdx.y * kDescTW + threadIdx.x;
-    constexpr int NT = kDescTW * TH;
+    const int nty = (h + TH - 1) / TH, ty0 = vb.y * kDescTiles;
+    const int ntile = min(kDescTiles, nty - ty0);
 
-    for (int i = tid; i < IW * IH; i += NT) {
-        const int ix = i % IW, iy = i / IW;
-        const int x = x0 - 3 + ix, y = y0 - 3 + iy;
-        int val = 0;
-        if (x >= 0 && x < w && y >= 0 && y < h) val = img[(size_t)y * pitch + x];
-        s_img[iy][ix] = (int16_t)val;
-    }
-    __syncthreads();
-
-    for (int i = tid; i < QW * QH; i += NT) {
-        const int qx = i % QW, qy = i / QW;
-        const int x = x0 - 2 + qx, y = y0 - 2 + qy;
-        int qdu = 128, qdv = 128;
-        if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
-            const int ix = qx + 1, iy = qy + 1;  // image-tile coordinates of (x, y)
-            const int a0 = s_img[iy - 1][ix - 1], b = s_img[iy - 1][ix], c = s_img[iy - 1][ix + 1];
-            const int d = s_img[iy][ix - 1], f = s_img[iy][ix + 1];
-            const int g = s_img[iy + 1][ix - 1], hh = s_img[iy + 1][ix], k = s_img[iy + 1][ix + 1];
-            const int gx = (c + 2 * f + k) - (a0 + 2 * d + g);
-            const int gy = (g + 2 * hh + k) - (a0 + 2 * b + c);
-            qdu = quantise(gx);
-            qdv = quantise(gy);
+    int v[PER];
+    auto fetch = [&](int ty) {
+        const int y0 = ty * TH;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = tid + u * NT;
+            const int ix = i % IW, iy = i / IW;
+            const int x = x0 - 3 + ix, y = y0 - 3 + iy;
+            v[u] = i < NI && x >= 0 && x < w && y >= 0 && y < h ? img[(size_t)y * pitch + x] : 0;
         }
-        s_du[qy][qx] = (uint8_t)qdu;
-        s_dv[qy][qx] = (uint8_t)qdv;
-    }
-    __syncthreads();
+    };
+    fetch(ty0);
+    for (int t = 0; t < ntile; ++t) {
+        const int y0 = (ty0 + t) * TH;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = tid + u * NT;
+            if (i < NI) s_img[i / IW][i % IW] = (int16_t)v[u];
+        }
+        __syncthreads();
+        if (t + 1 < ntile) fetch(ty0 + t + 1);  // in flight while this tile is computed
 
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= w || y >= h) return;
-    const int cx = threadIdx.x + 2, cy = threadIdx.y + 2;
+        for (int i = tid; i < QW * QH; i += NT) {
+            const int qx = i % QW, qy = i / QW;
+            const int x = x0 - 2 + qx, y = y0 - 2 + qy;
+            int qdu = 128, qdv = 128;
+            if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
+                const int ix = qx + 1, iy = qy + 1;  // image-tile coordinates of (x, y)
+                const int a0 = s_img[iy - 1][ix - 1], b = s_img[iy - 1][ix], c = s_img[iy - 1][ix + 1];
+                const int d = s_img[iy][ix - 1], f = s_img[iy][ix + 1];
+                const int g = s_img[iy + 1][ix - 1], hh = s_img[iy + 1][ix], k = s_img[iy + 1][ix + 1];
+                const int gx = (c + 2 * f + k) - (a0 + 2 * d + g);
+                const int gy = (g + 2 * hh + k) - (a0 + 2 * b + c);
+                qdu = quantise(gx);
+                qdv = quantise(gy);
+            }
+            s_du[qy][qx] = (uint8_t)qdu;
+            s_dv[qy][qx] = (uint8_t)qdv;
+        }
+        __syncthreads();
+
+        const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+        if (x < w && y < h) {
+            const int cx = threadIdx.x + 2, cy = threadIdx.y + 2;
 #define DU(ox, oy) ((uint32_t)s_du[cy + (oy)][cx + (ox)])
 #define DV(ox, oy) ((uint32_t)s_dv[cy + (oy)][cx + (ox)])
-    uint4 o;
-    o.x = DU(-2, -2) | (DU(2, -2) << 8) | (DU(-1, 0) << 16) | (DU(1, 0) << 24);
-    o.y = DU(-2, 2) | (DU(2, 2) << 8) | (DU(0, -1) << 16) | (DU(0, 1) << 24);
-    o.z = DV(0, -2) | (DV(0, 2) << 8) | (DV(-2, 0) << 16) | (DV(2, 0) << 24);
-    o.w = DV(-1, -1) | (DV(1, -1) << 8) | (DV(-1, 1) << 16) | (DV(1, 1) << 24);
+            uint4 o;
+            o.x = DU(-2, -2) | (DU(2, -2) << 8) | (DU(-1, 0) << 16) | (DU(1, 0) << 24);
+            o.y = DU(-2, 2) | (DU(2, 2) << 8) | (DU(0, -1) << 16) | (DU(0, 1) << 24);
+            o.z = DV(0, -2) | (DV(0, 2) << 8) | (DV(-2, 0) << 16) | (DV(2, 0) << 24);
+            o.w = DV(-1, -1) | (DV(1, -1) << 8) | (DV(-1, 1) << 16) | (DV(1, 1) << 24);
 #undef DU
 #undef DV
-    desc[(size_t)y * w + x] = o;
+            desc[(size_t)y * w + x] = o;
+        }
+        __syncthreads();  // the next tile overwrites the shared tiles
+    }
 }
 
 template <int TH> __global__ void __launch_bounds__(kDescTW *TH) descriptor_kernel(DescArgs a) {
@@ -89,7 +113,8 @@ __global__ void __launch_bounds__(kDescTW *TH) descriptor_kernel_b(const DescArg
 }
 
 dim3 descriptor_grid(int w, int h, int two, int tile_rows) {
-    return dim3((w + kDescTW - 1) / kDescTW, (h + tile_rows - 1) / tile_rows, two ? 2 : 1);
+    const int nty = (h + tile_rows - 1) / tile_rows;
+    return dim3((w + kDescTW - 1) / kDescTW, (nty + kDescTiles - 1) / kDescTiles, two ? 2 : 1);
 }
 
 static bool valid_tile_rows(int th) { return th == 4 || th == 8 || th == 16; }
