@@ -4,17 +4,17 @@
 //
 // plane_raster_kernel  eight lanes per triangle (grid-stride), both meshes in
 //                      one launch.  Every lane evaluates the FP32 plane in
-//                      the fixed order.  For each row of the bounding box
-//                      the owned x-range follows from the three integer edge
-//                      functions (E >= 0 on owned edges, E >= 1 otherwise);
-//                      each pixel of that range (widened by one) is
-//                      confirmed with the edge functions themselves before
-//                      it is written, so ownership is exactly the top-left
-//                      rule.  One row per lane; triangles whose bounding
-//                      box exceeds kBigArea pixels are listed instead (in up
-//                      to kBigSplit parts) and drawn by
+//                      the fixed order.  The lanes tile the bounding box
+//                      (up to eight across x, the rest over rows) and
+//                      write a pixel when the three integer edge functions
+//                      own it (E >= 0 on owned edges, E >= 1 otherwise), so
+//                      ownership is exactly the top-left rule.  Triangles
+//                      whose bounding box exceeds kBigArea pixels are listed
+//                      instead (in up to kBigSplit parts) and drawn by
 //                      plane_raster_big_kernel, one CTA per part (rows over
-//                      warps, lanes across x), so they leave no tail.
+//                      warps, lanes across x; there the owned x-range of a
+//                      row, widened by one, follows from the edge functions
+//                      first), so they leave no tail.
 // cell_kernel          one CTA per grid-vector cell (G x G pixels, which share
 //                      one candidate mask) and per reference image.  It
 //                      expands the cell's mask into an ascending candidate
@@ -142,6 +142,32 @@ __device__ __forceinline__ void raster_row(const TriGeom &g, int y, int first, i
     }
 }
 
+// Writes the owned pixels of a small triangle: the group's G lanes tile the
+// bounding box as LX x LY (LX the least power of two >= its width, at most
+// G), consecutive x on consecutive lanes (their stores are contiguous), and
+// every pixel is confirmed with the three edge functions as in raster_row.
+template <int G>
+__device__ __forceinline__ void raster_box(const TriGeom &g, int gl, int w, int dmin, int dmax,
+                                           int16_t *__restrict__ dplane) {
+    const int bw = g.xmax - g.xmin + 1;
+    const int LX = bw >= G ? G : (bw > G / 2 ? G : (bw > G / 4 ? G / 2 : (bw > 1 ? 2 : 1)));
+    const int LY = G / LX, lx = gl % LX, ly = gl / LX;
+    for (int y = g.ymin + ly; y <= g.ymax; y += LY) {
+        for (int x = g.xmin + lx; x <= g.xmax; x += LX) {
+            const int e0 = (g.ex1 - g.ex0) * (y - g.ey0) - (g.ey1 - g.ey0) * (x - g.ex0);
+            const int e1 = (g.ex2 - g.ex1) * (y - g.ey1) - (g.ey2 - g.ey1) * (x - g.ex1);
+            const int e2 = (g.ex0 - g.ex2) * (y - g.ey2) - (g.ey0 - g.ey2) * (x - g.ex2);
+            if (!((e0 > 0 || (e0 == 0 && g.o0)) && (e1 > 0 || (e1 == 0 && g.o1)) && (e2 > 0 || (e2 == 0 && g.o2))))
+                continue;
+            const float t1 = __fmul_rn(g.fa, __int2float_rn(x));
+            const float t2 = __fmul_rn(g.fb, __int2float_rn(y));
+            const float mu = __fadd_rn(__fadd_rn(t1, t2), g.fc);
+            const int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
+            dplane[(size_t)y * w + x] = (int16_t)min(max(dp, dmin), dmax);
+        }
+    }
+}
+
 constexpr int kRasterGroup = 8;  // lanes per small triangle
 constexpr int kBigSplit = 8;      // CTAs a big triangle is spread over, at most
 
@@ -164,7 +190,7 @@ __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB 
             }
             continue;
         }
-        for (int r = gl; r < rows; r += kRasterGroup) raster_row(g, g.ymin + r, 0, 1, a.w, a.dmin, a.dmax, S.dplane);
+        raster_box<kRasterGroup>(g, gl, a.w, a.dmin, a.dmax, S.dplane);
     }
 }
 
