@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Fused post-processing: the four passes on one 32x32 tile in shared memory.
+// Fused post-processing: the four passes on one TxT tile in shared memory
+// (T = 16 for one map, 32 in batched launches).
 //
 // The output tile needs the vertical mean over rows +-3 (r), which needs the
 // horizontal mean over columns +-3, which needs the column gap pass over
@@ -139,22 +140,24 @@ __global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__rest
 // tap.  Each pass runs over exactly the region the next one reads, with the
 // same per-element functions as the per-pass kernels.
 // ---------------------------------------------------------------------------
-constexpr int kFusedTile = 32;
+constexpr int kFusedTile = 32;     // batched launches (many tiles in any case)
+constexpr int kFusedTileOne = 16;  // one-map launches: more CTAs for one map
 constexpr int kFusedMaxGap = 16;
-constexpr int kFusedPitch = kFusedTile + 2 * (kFusedMaxGap + kMeanRadius);
+template <int T> __host__ __device__ constexpr int fused_pitch() { return T + 2 * (kFusedMaxGap + kMeanRadius); }
 
 struct SmemIn {
     const float *s;
     __device__ __forceinline__ float at(size_t idx) const { return s[idx]; }
 };
 
+template <int T>
 __device__ __forceinline__ void fused_post_body(const FusedPostArgs &a, const VB &vb) {
-    __shared__ float s_a[kFusedPitch * kFusedPitch];
-    __shared__ float s_b[kFusedPitch * kFusedPitch];
+    __shared__ float s_a[fused_pitch<T>() * fused_pitch<T>()];
+    __shared__ float s_b[fused_pitch<T>() * fused_pitch<T>()];
     const int w = a.w, h = a.h;
     const int g = a.gap, r = a.mean ? kMeanRadius : 0, H = g + r;
-    const int P = kFusedTile + 2 * H;  // tile pitch
-    const int x0 = vb.x * kFusedTile - H, y0 = vb.y * kFusedTile - H;
+    const int P = T + 2 * H;  // tile pitch
+    const int x0 = vb.x * T - H, y0 = vb.y * T - H;
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < P * P; i += nth) {
         const int gx = x0 + i % P, gy = y0 + i / P;
@@ -179,27 +182,29 @@ __device__ __forceinline__ void fused_post_body(const FusedPostArgs &a, const VB
     }
     if (r > 0) {
         // horizontal mean: the output columns, rows +-r
-        const int nr = kFusedTile + 2 * r;
-        for (int i = tid; i < kFusedTile * nr; i += nth) {
-            const int c = H + i % kFusedTile, rr = g + i / kFusedTile;
+        const int nr = T + 2 * r;
+        for (int i = tid; i < T * nr; i += nth) {
+            const int c = H + i % T, rr = g + i / T;
             nxt[rr * P + c] = mean_at(SmemIn{cur}, (size_t)rr * P, 1, c, P);
         }
         __syncthreads();
     }
     // vertical mean (or, without the means, the gap passes' result) to the output
     const float *src = r > 0 ? nxt : cur;
-    for (int i = tid; i < kFusedTile * kFusedTile; i += nth) {
-        const int c = H + i % kFusedTile, rr = H + i / kFusedTile;
+    for (int i = tid; i < T * T; i += nth) {
+        const int c = H + i % T, rr = H + i / T;
         const int gx = x0 + c, gy = y0 + rr;
         if (gx >= w || gy >= h) continue;
         a.out[(size_t)gy * w + gx] = r > 0 ? mean_at(SmemIn{src}, (size_t)c, (size_t)P, rr, P) : src[rr * P + c];
     }
 }
 
-__global__ void __launch_bounds__(256) fused_post_kernel(FusedPostArgs a) { fused_post_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) fused_post_kernel(FusedPostArgs a) {
+    fused_post_body<kFusedTileOne>(a, vb_single());
+}
 __global__ void __launch_bounds__(256) fused_post_kernel_b(const FusedPostArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    fused_post_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    fused_post_body<kFusedTile>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 bool post_fusable(const elas_params *p) { return p->ipol_gap_width <= kFusedMaxGap; }
@@ -209,9 +214,7 @@ FusedPostArgs fused_post_args(const int16_t *d, int w, int h, const elas_params 
                          p->filter_adaptive_mean ? 1 : 0};
 }
 
-dim3 fused_post_grid(int w, int h) {
-    return dim3((w + kFusedTile - 1) / kFusedTile, (h + kFusedTile - 1) / kFusedTile);
-}
+dim3 fused_post_grid(int w, int h, int tile) { return dim3((w + tile - 1) / tile, (h + tile - 1) / tile); }
 
 size_t post_workspace(int w, int h) { return 2 * align_up((size_t)w * h * sizeof(float), 256); }
 
@@ -263,7 +266,7 @@ dim3 post_grid(int w, int h) { return dim3((w + 31) / 32, (h + 7) / 8); }
 
 elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, cudaStream_t st) {
     if (post_fusable(p)) {
-        fused_post_kernel<<<fused_post_grid(w, h), 256, 0, st>>>(fused_post_args(d, w, h, p, out));
+        fused_post_kernel<<<fused_post_grid(w, h, kFusedTileOne), 256, 0, st>>>(fused_post_args(d, w, h, p, out));
         return launch_status("fused_post_kernel");
     }
     PostArgs passes[4];
@@ -301,7 +304,7 @@ elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const 
     vmap_clear(m_f, pairs.stride);
     for (int i = 0; i < pairs.n; ++i) {
         const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
-        vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h) : dim3(0));
+        vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h, kFusedTile) : dim3(0));
     }
     if (vmap_total(m_f) > 0) {
         fused_post_kernel_b<<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
