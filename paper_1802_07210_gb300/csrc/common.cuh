@@ -63,6 +63,22 @@ __device__ __forceinline__ uint32_t sad16(const uint4 &a, const uint4 &b) {
     return sad4_acc(a.w, b.w, s);
 }
 
+// The same sum with the byte-SIMD absolute difference and its accumulating
+// merge (one instruction per 4 bytes); the dense matcher's form, measured
+// faster there (the support matcher keeps sad16).
+__device__ __forceinline__ uint32_t sad4_vacc(uint32_t a, uint32_t b, uint32_t acc) {
+    uint32_t r = acc;
+    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t sad16_vacc(const uint4 &a, const uint4 &b) {
+    uint32_t s = sad4_vacc(a.x, b.x, 0u);
+    s = sad4_vacc(a.y, b.y, s);
+    s = sad4_vacc(a.z, b.z, s);
+    return sad4_vacc(a.w, b.w, s);
+}
+
 // Texture of a descriptor: sum of |b - 128| over its 16 bytes.
 __device__ __forceinline__ uint32_t texture16(const uint4 &a) {
     const uint32_t m = 0x80808080u;

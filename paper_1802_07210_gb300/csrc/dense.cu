@@ -315,7 +315,7 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
                     const uint4 *orow = oth + row + x;
                     if (full) {
                         for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
-                            const int c = (int)sad16(r, __ldg(orow + dir * d));
+                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     } else {
@@ -335,12 +335,12 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
 #pragma unroll 8
                         for (int k = sub; k < cnt; k += TPP) {
                             const int d = s_list[k];
-                            const int c = (int)sad16(r, __ldg(orow + dir * d));
+                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                         const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
                         for (int d = lo + sub; d <= hi; d += TPP) {
-                            int c = (int)sad16(r, __ldg(orow + dir * d));
+                            int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
                             if (!a.prior_off) c += s_P[abs(d - dp)];
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }

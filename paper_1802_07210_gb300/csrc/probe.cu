@@ -8,9 +8,9 @@
 
 namespace elas {
 
-// variant 0: __vabsdiffu4 + __dp4a (the sequence the kernels use)
+// variant 0: __vabsdiffu4 + __dp4a (the support matcher's sequence)
 // variant 1: __vsadu4
-// variant 2: PTX vabsdiff4 with accumulate
+// variant 2: PTX vabsdiff4 with accumulate (the dense matcher's sequence)
 __device__ __forceinline__ uint32_t sad16_v(const uint4 &a, const uint4 &b, uint32_t acc, int variant) {
     if (variant == 1) {
         return acc + __vsadu4(a.x, b.x) + __vsadu4(a.y, b.y) + __vsadu4(a.z, b.z) + __vsadu4(a.w, b.w);
