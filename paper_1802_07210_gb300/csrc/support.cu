@@ -3,10 +3,15 @@
 // one-hot masks, Sec. VI.D) and raster-order compaction.
 //
 // Kernels, in launch order:
-//   support_match_kernel    one warp per lattice candidate; lanes stride the
-//                           disparity range, each lane keeps (best, second)
-//                           and the warp merges them with two min-reductions;
-//                           the right-to-left re-match runs in the same warp.
+//   support_match_row_kernel  one CTA per lattice row: warps hold 32 right
+//                           windows each and walk the row's candidates
+//                           (below); the re-match is one warp per candidate.
+//   support_match_kernel    (rows too wide for the row kernel's shared
+//                           memory) one warp per lattice candidate; lanes
+//                           stride the disparity range, each lane keeps
+//                           (best, second) and the warp merges them with two
+//                           min-reductions; the right-to-left re-match runs
+//                           in the same warp.
 //   consistency_kernel      32x8 candidate tile with its halo in shared
 //                           memory, window count per candidate; also clears
 //                           the grid-vector masks.
@@ -103,6 +108,159 @@ __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB 
 }
 
 __global__ void __launch_bounds__(512) support_match_kernel(MatchArgs m) { support_match_body(m, vb_single()); }
+
+// The same matching with one CTA per lattice row, organised around the
+// right-image positions: a right window s (its four descriptors at
+// (s+-2, v+-2)) meets the candidates u = s + d of every disparity d, so a
+// warp holds the windows of 32 consecutive s in registers and walks the
+// row's candidates once: per candidate each lane costs its own d = u - s
+// against the candidate's left window (shared memory, the same address on
+// every lane), and two warp minimum-reductions give the best (cost, d) of
+// those 32 disparities and the least other cost.  Each candidate collects
+// one such result per 32-disparity window in shared memory; their merge is
+// the same (best, second) as a search over the whole range: the least key
+// over the windows and, for the second, the least of the other windows'
+// best costs and the winning window's second.  The right-to-left re-match
+// of the candidates that pass runs with one warp per candidate as in
+// support_match_kernel.  Keys are (cost << 16) | d: least cost, then least d.
+struct SupRowSmem {
+    int slots;  // windows a candidate's range can meet
+    size_t desc, res, lohi, d1;  // byte offsets
+    size_t total;
+};
+
+__host__ __device__ __forceinline__ SupRowSmem sup_row_smem(int wc, int dmin, int dmax) {
+    SupRowSmem o;
+    o.slots = (dmax - dmin + 1 + 31) / 32 + 1;
+    o.desc = 0;
+    o.res = o.desc + (size_t)wc * 4 * sizeof(uint4);
+    o.lohi = o.res + (size_t)wc * o.slots * sizeof(uint2);
+    o.d1 = o.lohi + (size_t)wc * sizeof(int2);
+    o.total = o.d1 + (((size_t)wc * sizeof(int) + 15) & ~(size_t)15);
+    return o;
+}
+
+__device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const VB &vb) {
+    const SupportArgs &a = m.a;
+    const uint4 *__restrict__ dL = m.dL;
+    const uint4 *__restrict__ dR = m.dR;
+    const int w = a.w, wc = a.wc, step = a.step, dmin = a.dmin, dmax = a.dmax;
+    const int ic = vb.x, v = ic * step;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const SupRowSmem L = sup_row_smem(wc, dmin, dmax);
+    uint4 *s_desc = reinterpret_cast<uint4 *>(s_raw + L.desc);
+    uint2 *s_res = reinterpret_cast<uint2 *>(s_raw + L.res);
+    int2 *s_lohi = reinterpret_cast<int2 *>(s_raw + L.lohi);
+    int *s_d1 = reinterpret_cast<int *>(s_raw + L.d1);
+    const bool row_ok = v >= 4 && v <= a.h - 5;
+    const size_t rt = (size_t)(v - 2) * w, rb = (size_t)(v + 2) * w;
+    // candidates: left windows, texture, disparity range (lo > hi: none)
+    for (int k = tid; k < wc; k += blockDim.x) {
+        const int u = k * step;
+        int lo = 1, hi = 0;
+        if (row_ok && u >= 4 && u <= w - 5) {
+            const uint4 l0 = __ldg(dL + rt + u - 2), l1 = __ldg(dL + rt + u + 2);
+            const uint4 l2 = __ldg(dL + rb + u - 2), l3 = __ldg(dL + rb + u + 2);
+            s_desc[4 * k] = l0;
+            s_desc[4 * k + 1] = l1;
+            s_desc[4 * k + 2] = l2;
+            s_desc[4 * k + 3] = l3;
+            const uint32_t texL = texture16(l0) + texture16(l1) + texture16(l2) + texture16(l3);
+            if ((int)texL >= a.support_texture) {
+                lo = max(dmin, u - w + 5);
+                hi = min(dmax, u - 4);
+                if (hi - lo + 1 < 2) lo = 1, hi = 0;
+            }
+        }
+        s_lohi[k] = make_int2(lo, hi);
+        for (int j = 0; j < L.slots; ++j) s_res[k * L.slots + j] = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+    }
+    __syncthreads();
+    // right windows s = 4 + 32 j + lane, 4 <= s <= w - 5
+    const int nwin = row_ok ? (w - 8 + 31) / 32 : 0;
+    for (int j = warp; j < nwin; j += nwarps) {
+        const int s0 = 4 + 32 * j, sl = s0 + lane;
+        const bool s_ok = sl <= w - 5;
+        uint4 r0 = make_uint4(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+        if (s_ok) {
+            r0 = __ldg(dR + rt + sl - 2);
+            r1 = __ldg(dR + rt + sl + 2);
+            r2 = __ldg(dR + rb + sl - 2);
+            r3 = __ldg(dR + rb + sl + 2);
+        }
+        // candidates u = s + d with d in [dmin, dmax] for some s of the window
+        const int k0 = max(0, (s0 + dmin + step - 1) / step), k1 = min(wc - 1, (s0 + 31 + dmax) / step);
+        const int slot = j % L.slots;
+        for (int k = k0; k <= k1; ++k) {
+            const int2 lh = s_lohi[k];
+            if (lh.x > lh.y) continue;  // uniform over the warp
+            const int d = k * step - sl;
+            const bool in = s_ok && d >= lh.x && d <= lh.y;
+            const uint4 *lw = s_desc + 4 * k;
+            uint32_t c = sad16(lw[0], r0);
+            c += sad16(lw[1], r1);
+            c += sad16(lw[2], r2);
+            c += sad16(lw[3], r3);
+            const uint32_t key = in ? ((c << 16) | (uint32_t)d) : 0xFFFFFFFFu;
+            const uint32_t kmin = __reduce_min_sync(0xFFFFFFFFu, key);
+            const uint32_t other = (in && key != kmin) ? c : 0xFFFFFFFFu;
+            const uint32_t m2 = __reduce_min_sync(0xFFFFFFFFu, other);
+            if (lane == 0 && kmin != 0xFFFFFFFFu) s_res[k * L.slots + slot] = make_uint2(kmin, m2);
+        }
+    }
+    __syncthreads();
+    // merge the windows of each candidate; ratio test
+    for (int k = tid; k < wc; k += blockDim.x) {
+        uint32_t best = 0xFFFFFFFFu;
+        int bj = -1;
+        for (int j = 0; j < L.slots; ++j) {
+            const uint32_t x = s_res[k * L.slots + j].x;
+            if (x < best) {
+                best = x;
+                bj = j;
+            }
+        }
+        int d1 = -1;
+        if (bj >= 0) {
+            uint32_t gm2 = s_res[k * L.slots + bj].y;
+            for (int j = 0; j < L.slots; ++j) {
+                const uint32_t x = s_res[k * L.slots + j].x;
+                if (j != bj && x != 0xFFFFFFFFu) gm2 = min(gm2, x >> 16);
+            }
+            const uint32_t gm1 = best >> 16;
+            if (gm2 != 0u && gm2 != 0xFFFFFFFFu &&
+                __uint2float_rn(gm1) <= __fmul_rn(a.thr, __uint2float_rn(gm2)))
+                d1 = (int)(best & 0xFFFFu);
+        }
+        s_d1[k] = d1;
+        if (d1 < 0) m.raw[ic * wc + k] = (int16_t)-1;
+    }
+    __syncthreads();
+    // right-to-left re-match, one warp per candidate that passed
+    for (int k = warp; k < wc; k += nwarps) {
+        const int d1 = s_d1[k];
+        if (d1 < 0) continue;
+        const int ur = k * step - d1;
+        const uint4 r0 = __ldg(dR + rt + ur - 2), r1 = __ldg(dR + rt + ur + 2);
+        const uint4 r2 = __ldg(dR + rb + ur - 2), r3 = __ldg(dR + rb + ur + 2);
+        const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
+        int out = -1;
+        if ((int)texR >= a.support_texture) {
+            const int d2 = warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, dmin, dmax, a.thr, lane);
+            if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
+        }
+        if (lane == 0) m.raw[ic * wc + k] = (int16_t)out;
+    }
+}
+
+__global__ void __launch_bounds__(512) support_match_row_kernel(MatchArgs m) {
+    support_match_row_body(m, vb_single());
+}
+__global__ void __launch_bounds__(512) support_match_row_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    support_match_row_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 __global__ void __launch_bounds__(512) support_match_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     support_match_body(slot_entry(tab, vm.stride, vb.slot), vb);
@@ -310,6 +468,19 @@ static elas_status consistency_smem_attr(const void *fn, size_t smem) {
     return ELAS_OK;
 }
 
+// Shared memory of the row-organised matcher; wider rows take the
+// per-candidate kernel, and so do launches of fewer lattice rows than two
+// per SM (one CTA per row would leave SMs idle).
+constexpr size_t kSupRowSmemMax = 160 * 1024;
+constexpr int kSupRowMinRows = 2 * 152;
+
+static elas_status sup_row_smem_attr(const void *fn, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return launch_status("support_match_row_kernel shared memory attribute");
+    return ELAS_OK;
+}
+
 dim3 support_match_grid(const MatchArgs &m, int warps) {
     const int nc = m.a.wc * m.a.hc;
     return dim3((nc + warps - 1) / warps);
@@ -333,8 +504,16 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
         return ELAS_OK;
     }
     const int warps_per_block = 8;
-    support_match_kernel<<<support_match_grid(sa.match, warps_per_block), 32 * warps_per_block, 0, st>>>(sa.match);
-    if ((s = launch_status("support_match_kernel")) != ELAS_OK) return s;
+    const size_t row_smem = sup_row_smem(sa.match.a.wc, sa.match.a.dmin, sa.match.a.dmax).total;
+    if (row_smem <= kSupRowSmemMax && sa.match.a.hc >= kSupRowMinRows) {
+        if ((s = sup_row_smem_attr((const void *)support_match_row_kernel, row_smem)) != ELAS_OK) return s;
+        support_match_row_kernel<<<lattice_row_grid(sa.match.a.hc), 32 * warps_per_block, row_smem, st>>>(sa.match);
+        if ((s = launch_status("support_match_row_kernel")) != ELAS_OK) return s;
+    } else {
+        support_match_kernel<<<support_match_grid(sa.match, warps_per_block), 32 * warps_per_block, 0, st>>>(
+            sa.match);
+        if ((s = launch_status("support_match_kernel")) != ELAS_OK) return s;
+    }
     const size_t smem = consistency_smem(sa.cons.r);
     if ((s = consistency_smem_attr((const void *)consistency_kernel, smem)) != ELAS_OK) return s;
     consistency_kernel<<<consistency_grid(sa.cons), dim3(kConsTX, kConsTY), smem, st>>>(sa.cons);
@@ -352,6 +531,7 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
     if (match_warps != 4 && match_warps != 8 && match_warps != 16)
         return fail(ELAS_ERR_INVALID_ARG, "support warps per CTA %d", match_warps);
     VMap m_match, m_cons, m_rows;
+    size_t row_smem = 0;
     vmap_clear(m_match, pairs.stride);
     vmap_clear(m_cons, pairs.stride);
     vmap_clear(m_rows, pairs.stride);
@@ -362,14 +542,21 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
         if (h.match.a.wc * h.match.a.hc == 0)
             return fail(ELAS_ERR_INVALID_ARG, "pair %d has no lattice candidate", i);
         vmap_add(m_match, slot, support_match_grid(h.match, match_warps));
+        row_smem = max(row_smem, sup_row_smem(h.match.a.wc, h.match.a.dmin, h.match.a.dmax).total);
         vmap_add(m_cons, slot, consistency_grid(h.cons));
         vmap_add(m_rows, slot, lattice_row_grid(h.red.hc));
         cons_smem = cons_smem > consistency_smem(h.cons.r) ? cons_smem : consistency_smem(h.cons.r);
     }
     if (pairs.n == 0) return ELAS_OK;
     elas_status s;
-    support_match_kernel_b<<<vmap_total(m_match), 32 * match_warps, 0, st>>>(t.match, m_match);
-    if ((s = launch_status("support_match_kernel_b")) != ELAS_OK) return s;
+    if (row_smem <= kSupRowSmemMax && vmap_total(m_rows) >= kSupRowMinRows) {
+        if ((s = sup_row_smem_attr((const void *)support_match_row_kernel_b, row_smem)) != ELAS_OK) return s;
+        support_match_row_kernel_b<<<vmap_total(m_rows), 32 * match_warps, row_smem, st>>>(t.match, m_rows);
+        if ((s = launch_status("support_match_row_kernel_b")) != ELAS_OK) return s;
+    } else {
+        support_match_kernel_b<<<vmap_total(m_match), 32 * match_warps, 0, st>>>(t.match, m_match);
+        if ((s = launch_status("support_match_kernel_b")) != ELAS_OK) return s;
+    }
     if ((s = consistency_smem_attr((const void *)consistency_kernel_b, cons_smem)) != ELAS_OK) return s;
     consistency_kernel_b<<<vmap_total(m_cons), dim3(kConsTX, kConsTY), cons_smem, st>>>(t.cons, m_cons);
     if ((s = launch_status("consistency_kernel_b")) != ELAS_OK) return s;

@@ -224,6 +224,38 @@ def test_uniform_batch_of_many_pairs():
     b.close()
 
 
+def test_batch_with_row_organised_support_matching():
+    """Enough lattice rows (four 640x480 and four 1242x375 pairs) for the
+    batched support stage to take the row-organised matcher: every pair's
+    maps and support count equal the per-pair path's (the per-candidate
+    matcher), and the first pair's support list equals the oracle's."""
+    B = _B()
+    items = [(synth.VGA_640, 2, i) for i in range(4)] + [(synth.KITTI_1242, 3, i) for i in range(4)]
+    pairs = [synth.workload_pair(wl, idx, cfg)[:2] for wl, cfg, idx in items]
+    shapes = [(wl.spec.w, wl.spec.h) for wl, _, _ in items]
+    b = B.Batch(shapes, [wl.params for wl, _, _ in items])
+    dL = [torch.empty((h, w), dtype=torch.int16, device="cuda") for w, h in shapes]
+    dR = [torch.empty_like(t) for t in dL]
+    b.run([dev(L) for L, _ in pairs], [dev(R) for _, R in pairs], dL, dR)
+    st = b.stats()
+    for i, ((wl, _, _), (L, R)) in enumerate(zip(items, pairs)):
+        h, w = L.shape
+        pl = B.Pipeline(w, h, wl.params)
+        aL = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        aR = torch.empty_like(aL)
+        pl.run(dev(L), dev(R), aL, aR)
+        np.testing.assert_array_equal(host(dL[i]), host(aL), err_msg="pair %d left" % i)
+        np.testing.assert_array_equal(host(dR[i]), host(aR), err_msg="pair %d right" % i)
+        assert st["n_support"][i] == pl.stats()["n_support"], i
+        pl.close()
+    L, R = pairs[0]
+    wl = items[0][0]
+    ref = oracle.support_list(oracle.support_points(oracle.descriptors(L), oracle.descriptors(R), wl.params),
+                              wl.params)
+    assert st["n_support"][0] == len(ref)
+    b.close()
+
+
 def test_batch_of_the_maximum_size():
     """256 pairs, the most one batch takes: small pairs of varied sizes and
     disparity ranges (ragged widths and heights), every eighth one textureless
