@@ -198,10 +198,10 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
             const int d = k * step - sl;
             const bool in = s_ok && d >= lh.x && d <= lh.y;
             const uint4 *lw = s_desc + 4 * k;
-            uint32_t c = sad16(lw[0], r0);
-            c += sad16(lw[1], r1);
-            c += sad16(lw[2], r2);
-            c += sad16(lw[3], r3);
+            uint32_t c = sad16_vacc(lw[0], r0);
+            c += sad16_vacc(lw[1], r1);
+            c += sad16_vacc(lw[2], r2);
+            c += sad16_vacc(lw[3], r3);
             const uint32_t key = in ? ((c << 16) | (uint32_t)d) : 0xFFFFFFFFu;
             const uint32_t kmin = __reduce_min_sync(0xFFFFFFFFu, key);
             const uint32_t other = (in && key != kmin) ? c : 0xFFFFFFFFu;
