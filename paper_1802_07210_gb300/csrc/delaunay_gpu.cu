@@ -314,7 +314,8 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
     return s > 0 || (s == 0 && c2.z < c1.z);
 }
 
-// Pass 1: one group of kDtGroup lanes per point.  The group lists the
+// Pass 1: one group of kDtGroup (batched) or kDtGroupOne (one pair) lanes
+// per point.  The group lists the
 // points within kDtRadius of p (indices into the grid-sorted array, in
 // shared memory), then wraps the star: each lane keeps the best candidate of
 // its share of the list under the pencil key (32-bit integers are exact:
@@ -323,7 +324,8 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
 // (4 r^2 <= R^2, exact) and, for an open star (p on the hull), nothing lies
 // beyond either open edge (checked against the extreme points of every image
 // row).  Other stars are queued for the next pass.
-constexpr int kDtGroup = 8;
+constexpr int kDtGroup = 8;       // lanes per star in batched launches (issue-bound: less divergence waste)
+constexpr int kDtGroupOne = 16;   // lanes per star for one pair (latency-bound: shorter star chains)
 constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (the radius-32 disc holds at most ~120 lattice points)
 constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
@@ -532,8 +534,8 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
 }
 
 
-__device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
-    dt_group_pass_body<kDtGroup, kDtRadius, kDtListCap, false>(a, vb);
+template <int G> __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
+    dt_group_pass_body<G, kDtRadius, kDtListCap, false>(a, vb);
 }
 __device__ __forceinline__ void dt_pass1b_body(const DtArgs &a, const VB &vb) {
     dt_group_pass_body<32, kDtRadiusB, kDtListCapB, true>(a, vb);
@@ -545,10 +547,12 @@ __global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel_b(const D
     dt_pass1b_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) { dt_pass1_body(a, vb_single()); }
+__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) {
+    dt_pass1_body<kDtGroupOne>(a, vb_single());
+}
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    dt_pass1_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    dt_pass1_body<kDtGroup>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // CTA pass: one CTA per star left by the group passes.  The points within
@@ -1273,7 +1277,8 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     dt_cell_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_scatter_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_dedup_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
-    const int gblocks = max(1, min((cap + kDtGroupThreads / kDtGroup - 1) / (kDtGroupThreads / kDtGroup), 152 * 8));
+    const int gblocks =
+        max(1, min((cap + kDtGroupThreads / kDtGroupOne - 1) / (kDtGroupThreads / kDtGroupOne), 152 * 16));
     // one pair: the CTA pass takes the group pass's queue directly (its time
     // is that of the longest star, which the warp pass would not shorten)
     dt_pass1_kernel<<<dim3(gblocks, nsides), kDtGroupThreads, 0, st>>>(a);
