@@ -194,7 +194,8 @@ __global__ void dt_dedup_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
 // Stars
 // -------------------------------------------------------------------------
 
-constexpr int kDtRadius = 32;     // pass-1 search radius
+constexpr int kDtRadius = 32;     // pass-1 search radius (one pair)
+constexpr int kDtRadiusBatch = 18;  // pass-1 search radius in batched launches
 constexpr int kDtCandCap = 160;   // pass-1 candidates cached per warp
 constexpr int kDtSlots = 32;      // owned triangles kept per point
 constexpr int kDtWarps = 8;       // warps per CTA
@@ -534,8 +535,8 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
 }
 
 
-template <int G> __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
-    dt_group_pass_body<G, kDtRadius, kDtListCap, false>(a, vb);
+template <int G, int R> __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
+    dt_group_pass_body<G, R, kDtListCap, false>(a, vb);
 }
 __device__ __forceinline__ void dt_pass1b_body(const DtArgs &a, const VB &vb) {
     dt_group_pass_body<32, kDtRadiusB, kDtListCapB, true>(a, vb);
@@ -548,11 +549,11 @@ __global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel_b(const D
 }
 
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) {
-    dt_pass1_body<kDtGroupOne>(a, vb_single());
+    dt_pass1_body<kDtGroupOne, kDtRadius>(a, vb_single());
 }
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    dt_pass1_body<kDtGroup>(slot_entry(tab, vm.stride, vb.slot), vb);
+    dt_pass1_body<kDtGroup, kDtRadiusBatch>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // CTA pass: one CTA per star left by the group passes.  The points within
