@@ -194,7 +194,7 @@ __global__ void dt_dedup_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
 // Stars
 // -------------------------------------------------------------------------
 
-constexpr int kDtRadius = 32;     // pass-1 search radius (one pair)
+constexpr int kDtRadius = 24;     // pass-1 search radius (one pair)
 constexpr int kDtRadiusBatch = 18;  // pass-1 search radius in batched launches
 constexpr int kDtCandCap = 160;   // pass-1 candidates cached per warp
 constexpr int kDtSlots = 32;      // owned triangles kept per point
@@ -315,12 +315,12 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
     return s > 0 || (s == 0 && c2.z < c1.z);
 }
 
-// Pass 1: one group of kDtGroup (batched) or kDtGroupOne (one pair) lanes
-// per point.  The group lists the
-// points within kDtRadius of p (indices into the grid-sorted array, in
-// shared memory), then wraps the star: each lane keeps the best candidate of
-// its share of the list under the pencil key (32-bit integers are exact:
-// every difference is at most 32) and the group reduces with shuffles.  A
+// Pass 1: one group of kDtGroup lanes (kDtGroupOne for one pair) per point.
+// The group lists the points within R of p (kDtRadius for one pair,
+// kDtRadiusBatch in batches; indices into the grid-sorted array, in shared
+// memory), then wraps the star: each lane keeps the best candidate of its
+// share of the list under the pencil key (32-bit integers are exact: every
+// difference is at most R <= 64) and the group reduces with shuffles.  A
 // star is accepted when every triangle's circumdisc lies inside the radius
 // (4 r^2 <= R^2, exact) and, for an open star (p on the hull), nothing lies
 // beyond either open edge (checked against the extreme points of every image
@@ -328,7 +328,7 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
 constexpr int kDtGroup = 8;       // lanes per star in batched launches (issue-bound: less divergence waste)
 constexpr int kDtGroupOne = 16;   // lanes per star for one pair (latency-bound: shorter star chains)
 constexpr int kDtGroupThreads = 256;
-constexpr int kDtListCap = 128;  // candidates per point (the radius-32 disc holds at most ~120 lattice points)
+constexpr int kDtListCap = 128;  // candidates per point (a radius-24 disc holds at most ~75 lattice points at step 5)
 constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
 constexpr int kDtListCapB = 640; // the radius-64 disc holds at most ~520 lattice points
 
