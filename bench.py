@@ -44,10 +44,11 @@ METRIC = "Mpix/s & pairs/s at 640x480 D=256; p50/p99 served latency vs per-pair 
 WORKLOADS = {"vga_640": (synth.VGA_640, 2), "small_320": (synth.SMALL_320, 1),
              "kitti_1242": (synth.KITTI_1242, 3)}
 # kernels of one plain step: descriptors 1; support 4 (match, consistency,
-# redundancy + grids, compaction); triangulation 9 (points, cell scan,
+# redundancy + grids, compaction); triangulation 10 (init, points, cell scan,
 # scatter, dedup, group pass, CTA pass, triangle scan, emit, emit big); plane
-# prior 2 (raster, big triangles); dense 1; LR 1; post-processing 1 (fused) or 0
-KERNELS_PER_STEP = {True: 19, False: 18}
+# prior 3 (init, raster, big triangles); dense 1; LR 1; post-processing 1
+# (fused) or 0.  No memsets.
+KERNELS_PER_STEP = {True: 21, False: 20}
 STAGES = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")
 # bytes a dense launch must move at least: both descriptor images read once
 # (32 B/px), the two prior maps read (4 B/px), the two maps written (4 B/px)

@@ -329,7 +329,10 @@ elas_status elas_pipeline_run_host(elas_pipeline *pl, const uint8_t *imgL, const
 elas_status elas_pipeline_set_triangulation(elas_pipeline *pl, int32_t on_gpu);
 /* With GPU triangulation the step is captured into a CUDA graph on the
  * second run with the same buffers and replayed from then on (on = 1, the
- * default); on = 0 launches every kernel each run. */
+ * default); one graph is kept per set of buffers (input and output pointers,
+ * pitch, profiling), up to 8 sets, the least recently used replaced, so a
+ * ring of camera buffers replays too.  on = 0 launches every kernel each
+ * run. */
 elas_status elas_pipeline_set_graph(elas_pipeline *pl, int32_t on);
 /* on = 1: every run records events between its stages (GPU triangulation
  * only) and elas_pipeline_stats_get reports the stage times. */

@@ -1246,6 +1246,8 @@ static DtSide dt_carve(void *ws, int cap, int w, int h) {
     return s;
 }
 
+__global__ void __launch_bounds__(256) dt_init_kernel(DtArgs a);
+
 // Triangulates one or both sides.  sides[i] = right flag; tri/ntri per side.
 elas_status launch_triangulate_device(const int16_t *list, const int32_t *count, int cap, int w, int h, int nsides,
                                       const int *rights, int32_t *const *tri, int32_t *const *ntri, int cap_tri,
@@ -1264,13 +1266,10 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
         a.s[i].right = rights[i];
         a.s[i].tri = tri[i];
         a.s[i].ntri = ntri[i];
-        const size_t cells = (size_t)a.gw * a.gh + 1;
-        if (cudaMemsetAsync(a.s[i].cell_cnt, 0, cells * 4, st) != cudaSuccess ||
-            cudaMemsetAsync(a.s[i].err, 0, 16, st) != cudaSuccess ||
-            cudaMemsetAsync(a.s[i].rowmin, 0x7F, (size_t)h * 4, st) != cudaSuccess ||
-            cudaMemsetAsync(a.s[i].rowmax, 0x80, (size_t)h * 4, st) != cudaSuccess)
-            return launch_status("triangulation memsets");
     }
+    // counters, cell counts and row extremes of both sides: one kernel
+    const int nall = a.gw * a.gh + 1 + 2 * h + 4;
+    dt_init_kernel<<<dim3((nall + 255) / 256, nsides), 256, 0, st>>>(a);
     const int tb = 256;
     const int pblocks = max(1, min((cap + tb - 1) / tb, 152 * 8));
     const int wblocks = max(1, min((cap + kDtWarps - 1) / kDtWarps, 152 * 16));
@@ -1302,7 +1301,7 @@ __device__ __forceinline__ void dt_init_body(const DtArgs &a, const VB &vb, int3
     const DtSide &S = a.s[vb.y];
     const int ncell1 = a.gw * a.gh + 1;
     const int nall = ncell1 + 2 * a.h + 4;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
     for (int k = vb.x * blockDim.x + threadIdx.x; k < nall; k += vb.gx * blockDim.x) {
         if (k < ncell1)
             S.cell_cnt[k] = 0;
@@ -1315,6 +1314,7 @@ __device__ __forceinline__ void dt_init_body(const DtArgs &a, const VB &vb, int3
     }
 }
 
+__global__ void __launch_bounds__(256) dt_init_kernel(DtArgs a) { dt_init_body(a, vb_single(), nullptr); }
 __global__ void __launch_bounds__(256) dt_init_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int32_t *counter) {
     const VB vb = vb_batch(vm);
     dt_init_body(slot_entry(tab, vm.stride, vb.slot), vb, counter);

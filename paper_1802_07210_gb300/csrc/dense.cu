@@ -408,6 +408,7 @@ __device__ __forceinline__ void raster_init_body(const RasterArgs &a, const VB &
     if (t == 0) *a.nbig = 0;
 }
 
+__global__ void __launch_bounds__(256) raster_init_kernel(RasterArgs a) { raster_init_body(a, vb_single()); }
 __global__ void __launch_bounds__(256) raster_init_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     raster_init_body(slot_entry(tab, vm.stride, vb.slot), vb);
@@ -435,13 +436,21 @@ static int raster_max_ntri(const RasterArgs &a) {
 }
 
 // Prior maps of one or two meshes.  With two, the maps must be contiguous
-// (dplane1 == dplane0 + w*h) so that one memset clears both.
+// (dplane1 == dplane0 + w*h) so that one pass clears both: raster_init_kernel
+// (16-byte stores) when the maps are 16-byte aligned, else two memsets.
 static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
-    const size_t bytes = (size_t)a.w * a.h * sizeof(int16_t) * a.nsides;
-    if (cudaMemsetAsync(a.s[0].dplane, 0xFF, bytes, st) != cudaSuccess) return launch_status("memset d_plane");
+    const size_t n = (size_t)a.w * a.h * a.nsides;  // int16 entries
+    if (aligned(a.s[0].dplane, 16)) {
+        const size_t blocks = (n / 8 + 255) / 256;
+        raster_init_kernel<<<(unsigned)(blocks < 152 * 8 ? (blocks > 0 ? blocks : 1) : 152 * 8), 256, 0, st>>>(a);
+        elas_status s0 = launch_status("raster_init_kernel");
+        if (s0 != ELAS_OK) return s0;
+    } else if (cudaMemsetAsync(a.s[0].dplane, 0xFF, n * sizeof(int16_t), st) != cudaSuccess ||
+               cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) {
+        return launch_status("memset d_plane");
+    }
     const int maxt = raster_max_ntri(a);
     if (maxt == 0) return ELAS_OK;
-    if (cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) return launch_status("memset big count");
     const int wpb = 256 / kRasterGroup;  // triangles per CTA pass
     int blocks = (maxt + wpb - 1) / wpb;
     if (blocks > 152 * 16) blocks = 152 * 16;

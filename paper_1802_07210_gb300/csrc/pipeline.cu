@@ -103,11 +103,20 @@ struct elas_pipeline {
     int profiling = 0;
     bool marked = false;
     cudaEvent_t marks[7] = {};
-    // graph replay of the step (GPU triangulation)
+    // graph replay of the step (GPU triangulation): one executable graph per
+    // argument signature (input/output pointers, pitch, profiling), up to
+    // kGraphCache of them, least recently used replaced; a signature is run
+    // eagerly the first time and captured the second
+    struct GraphEntry {
+        std::vector<const void *> sig;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t last = 0;
+    };
+    static constexpr size_t kGraphCache = 8;
     int use_graph = 1;
     cudaStream_t work = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    std::vector<const void *> graph_sig;
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
     // last run
     elas_pipeline_stats stats{};
     std::vector<int32_t> triL_v, triR_v;
@@ -124,7 +133,8 @@ void release(elas_pipeline *pl) {
     if (!pl) return;
     delete pl->helper;
     if (pl->work) cudaStreamSynchronize(pl->work);
-    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    for (auto &g : pl->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (pl->work) cudaStreamDestroy(pl->work);
     for (cudaEvent_t &e : pl->marks)
         if (e) cudaEventDestroy(e);
@@ -295,30 +305,43 @@ static elas_status run_graph(elas_pipeline *pl, const uint8_t *imgL, const uint8
     using namespace elas;
     const std::vector<const void *> sig{imgL, imgR, reinterpret_cast<const void *>((intptr_t)pitch), dL, dR, post,
                                         reinterpret_cast<const void *>((intptr_t)pl->profiling)};
-    if (sig != pl->graph_sig) {
-        if (pl->exec) cudaGraphExecDestroy(pl->exec);
-        pl->exec = nullptr;
-        pl->graph_sig = sig;
-        return run_step(pl, imgL, imgR, pitch, dL, dR, post, st);  // eager
+    elas_pipeline::GraphEntry *ge = nullptr;
+    for (auto &g : pl->graphs)
+        if (g.sig == sig) ge = &g;
+    if (!ge) {  // first time: eager, remembered (replacing the least recently used)
+        if (pl->graphs.size() < elas_pipeline::kGraphCache) {
+            pl->graphs.emplace_back();
+            ge = &pl->graphs.back();
+        } else {
+            ge = &pl->graphs[0];
+            for (auto &g : pl->graphs)
+                if (g.last < ge->last) ge = &g;
+            if (ge->exec) cudaGraphExecDestroy(ge->exec);
+            ge->exec = nullptr;
+        }
+        ge->sig = sig;
+        ge->last = ++pl->graph_clock;
+        return run_step(pl, imgL, imgR, pitch, dL, dR, post, st);
     }
-    if (!pl->exec) {
+    ge->last = ++pl->graph_clock;
+    if (!ge->exec) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(pl->work, cudaStreamCaptureModeRelaxed) != cudaSuccess)
             return launch_status("begin pipeline capture");
         elas_status s = run_step(pl, imgL, imgR, pitch, dL, dR, post, pl->work);
         const cudaError_t e = cudaStreamEndCapture(pl->work, &g);
         if (s == ELAS_OK && e != cudaSuccess) s = fail(ELAS_ERR_CUDA, "pipeline capture: %s", cudaGetErrorString(e));
-        if (s == ELAS_OK && cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) {
-            pl->exec = nullptr;
+        if (s == ELAS_OK && cudaGraphInstantiate(&ge->exec, g, 0) != cudaSuccess) {
+            ge->exec = nullptr;
             s = launch_status("pipeline graph instantiate");
         }
         if (g) cudaGraphDestroy(g);
         if (s != ELAS_OK) {
-            pl->graph_sig.clear();
+            ge->sig.clear();
             return s;
         }
     }
-    if (cudaGraphLaunch(pl->exec, st) != cudaSuccess) return launch_status("pipeline graph launch");
+    if (cudaGraphLaunch(ge->exec, st) != cudaSuccess) return launch_status("pipeline graph launch");
     pl->last_stream = st;
     return ELAS_OK;
 }
@@ -365,7 +388,10 @@ extern "C" elas_status elas_pipeline_set_graph(elas_pipeline *pl, int32_t on) {
     if (!pl) return elas::fail(ELAS_ERR_INVALID_ARG, "NULL pipeline");
     if ((on ? 1 : 0) != pl->use_graph) {
         pl->use_graph = on ? 1 : 0;
-        pl->graph_sig.clear();  // the next graph run starts eagerly
+        if (pl->work) cudaStreamSynchronize(pl->work);
+        for (auto &g : pl->graphs)  // the next graph runs start eagerly
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        pl->graphs.clear();
     }
     return ELAS_OK;
 }
