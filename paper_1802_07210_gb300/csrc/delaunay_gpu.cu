@@ -551,6 +551,11 @@ __global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel_b(const D
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) {
     dt_pass1_body<kDtGroupOne, kDtRadius>(a, vb_single());
 }
+// A batch of one pair takes the one-pair group pass (wider groups, larger disc).
+__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b1(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_pass1_body<kDtGroupOne, kDtRadius>(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     dt_pass1_body<kDtGroup, kDtRadiusBatch>(slot_entry(tab, vm.stride, vb.slot), vb);
@@ -1043,9 +1048,11 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block
 // Many pairs, persistent: the queues of every (pair, side) of the launch are
 // concatenated in launch order and the CTAs take their entries one at a
 // time from one atomic counter (zeroed by dt_init_kernel_b), so the long
-// stars of one pair overlap the work of all the others.
-__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides,
-                                                               int32_t *counter) {
+// stars of one pair overlap the work of all the others.  queue_id 1: the
+// warp pass's queues; 0: the group pass's (a batch of one pair, which skips
+// the warp pass).
+__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM)
+    dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides, int32_t *counter, int queue_id) {
     extern __shared__ int4 s_cand[];
     __shared__ DtBlockShared sh;
     __shared__ int s_pre[2 * kMaxBatch + 1];
@@ -1060,7 +1067,10 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block
         for (int j = 0; j < kPer; ++j) {
             const int q = lane * kPer + j;
             v[j] = 0;
-            if (q < nq_all) v[j] = max(0, *slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides].npending2);
+            if (q < nq_all) {
+                const DtSide &Q = slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides];
+                v[j] = max(0, queue_id ? *Q.npending2 : *Q.npending);
+            }
             sum += v[j];
         }
         int incl = sum;
@@ -1098,7 +1108,8 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block
         const DtArgs &a = slot_entry(tab, vm.stride, vm.slot[lo / nsides]);
         const DtSide &S = a.s[lo % nsides];
         const int n = min(max(*a.count, 0), a.cap);
-        dt_block_item(a, S, S.pending2[item - s_pre[lo]], n, s_cand, sh, r_start, r_start + a.gh);
+        dt_block_item(a, S, (queue_id ? S.pending2 : S.pending)[item - s_pre[lo]], n, s_cand, sh, r_start,
+                      r_start + a.gh);
     }
 }
 
@@ -1347,12 +1358,12 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         vmap_add(m_init, slot, dim3((nall + 255) / 256, nsides));
         vmap_add(m_pts, slot, dim3(dt_point_blocks(a.cap, 256, pairs.n), nsides));
         vmap_add(m_scan, slot, dim3(1, nsides));
-        const int gthreads = kDtGroupThreads / kDtGroup;
+        const int gthreads = kDtGroupThreads / (pairs.n == 1 ? kDtGroupOne : kDtGroup);
         vmap_add(m_grp, slot, dim3(dt_point_blocks(a.cap, gthreads, pairs.n), nsides));
         // the second group pass gets a warp per star of a queue of a few
         // percent of the points
         vmap_add(m_grp2, slot, dim3(max(1, min(152, a.cap / 256)), nsides));
-        vmap_add(m_big, slot, dim3(64, nsides));
+        vmap_add(m_big, slot, dim3(pairs.n == 1 ? 152 : 64, nsides));
         max_gh = max(max_gh, a.gh);
     }
     const int smem3 = kDtCandCap2 * (int)sizeof(int4) + (2 * max_gh + 1) * (int)sizeof(int);
@@ -1364,11 +1375,20 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
     dt_cell_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
     dt_scatter_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_dedup_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
-    dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
-    dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
+    // one pair: the one-pair group pass, then the CTA pass on its queue (as
+    // in launch_triangulate_device); several: the batch group pass and the
+    // warp pass
+    const bool one = pairs.n == 1;
+    if (one) {
+        dt_pass1_kernel_b1<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
+    } else {
+        dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
+        dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
+    }
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    dt_pass_block_kernel_b<<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter);
+    dt_pass_block_kernel_b<<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter,
+                                                                                 one ? 0 : 1);
     dt_tri_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
     dt_emit_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_emit_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(tab, m_big);

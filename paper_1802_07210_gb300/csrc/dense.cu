@@ -584,7 +584,8 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         if (pairs.n > 1) blocks = (blocks + 2) / 3;
         blocks = max(1, min(blocks, 152 * 16));
         vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
-        vmap_add(m_big, slot, dim3(32));
+        // big triangles: the one-pair launch's 2 CTAs per SM, shared by the pairs
+        vmap_add(m_big, slot, dim3(max(32, 2 * 152 / pairs.n)));
         vmap_add(m_cell, slot, cell_grid(d.cell, 2));
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }

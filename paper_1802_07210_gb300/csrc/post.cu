@@ -202,9 +202,10 @@ __device__ __forceinline__ void fused_post_body(const FusedPostArgs &a, const VB
 __global__ void __launch_bounds__(256) fused_post_kernel(FusedPostArgs a) {
     fused_post_body<kFusedTileOne>(a, vb_single());
 }
+template <int T>
 __global__ void __launch_bounds__(256) fused_post_kernel_b(const FusedPostArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    fused_post_body<kFusedTile>(slot_entry(tab, vm.stride, vb.slot), vb);
+    fused_post_body<T>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 bool post_fusable(const elas_params *p) { return p->ipol_gap_width <= kFusedMaxGap; }
@@ -302,12 +303,16 @@ elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const 
     if ((s = launch_status("lr_check_kernel_b")) != ELAS_OK) return s;
     VMap m_f;
     vmap_clear(m_f, pairs.stride);
+    const int tile = pairs.n == 1 ? kFusedTileOne : kFusedTile;  // one map: the one-map tiles
     for (int i = 0; i < pairs.n; ++i) {
         const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
-        vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h, kFusedTile) : dim3(0));
+        vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h, tile) : dim3(0));
     }
     if (vmap_total(m_f) > 0) {
-        fused_post_kernel_b<<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
+        if (tile == kFusedTileOne)
+            fused_post_kernel_b<kFusedTileOne><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
+        else
+            fused_post_kernel_b<kFusedTile><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
         if ((s = launch_status("fused_post_kernel_b")) != ELAS_OK) return s;
     }
     for (int k = 0; k < maxp && k < 4; ++k) {

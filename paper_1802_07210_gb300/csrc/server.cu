@@ -205,7 +205,8 @@ elas_status launch_kernels(elas_server *s, const std::vector<int> &ids, const Kn
 }
 
 elas_status launch_wave(elas_server *s, Lane &ln) {
-    const Knobs knobs;
+    Knobs knobs;
+    if (ln.reqs.size() == 1) knobs.dense_ppt = 1;  // a lone pair: one pixel per thread, as the per-pair path
     std::vector<int> ids;
     elas_status e = ELAS_OK;
     for (Request *r : ln.reqs) {

@@ -224,6 +224,21 @@ def test_uniform_batch_of_many_pairs():
     b.close()
 
 
+@pytest.mark.parametrize("idx", [2, 3, 6])
+def test_batch_of_one_pair(mix, idx):
+    """A batch of one pair takes the one-pair triangulation settings (wider
+    groups, no warp pass): its maps still equal the oracle's."""
+    it = mix[idx]
+    b = _batch([it])
+    dL, dR, post = _alloc([it])
+    for run in range(3):
+        b.run([dev(it["L"])], [dev(it["R"])], dL, dR, post)
+        _check([it], dL, dR, post, "one pair run %d" % run)
+    st = b.stats()
+    assert st["n_tri_left"][0] == len(it["ref"]["triL"]) and st["n_tri_right"][0] == len(it["ref"]["triR"])
+    b.close()
+
+
 def test_batch_with_row_organised_support_matching():
     """Enough lattice rows (four 640x480 and four 1242x375 pairs) for the
     batched support stage to take the row-organised matcher: every pair's
