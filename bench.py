@@ -588,7 +588,8 @@ def main():
     dense_bytes = DENSE_MIN_BYTES_PER_PX * px
     roof = {"kernel": "cell_kernel (dense argmin, both reference images in one launch)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SAD16/s", "frac": achieved / peak,
-            "traffic": None, "algorithmic_evals_per_launch": evals,
+            "traffic": DENSE_TRAFFIC_BYTES.get(wl.name), "traffic_source": DENSE_TRAFFIC_SOURCE,
+            "algorithmic_evals_per_launch": evals,
             "time": "mean of CUDA events around the launch, recorded by the library in a second pass of the timed steps (same pairs, same L2 flush)",
             "peak_source": "measured: probe kernel running the dense matcher's SAD16 sequence (variant %d, the "
                            "fastest of the three) on registers over all SMs" % KERNEL_SAD_VARIANT,
@@ -664,6 +665,15 @@ def dense_work(work, prm, w, h):
                 total += int(cnt.sum())
     return total
 
+
+# DRAM bytes (read + write) of one cell_kernel launch, from one ncu capture of
+# the kernel as it is now (dram__bytes_read.sum + dram__bytes_write.sum);
+# to be taken again whenever the kernel changes.
+DENSE_TRAFFIC_BYTES = {"640x480_D256": 11032832}
+DENSE_TRAFFIC_SOURCE = ("ncu --set full --clock-control none -k regex:cell_kernel -s 2 -c 1 on "
+                        "python bench.py --steps 3 --warmup 3 --no-cpu-baseline --skip-extra (L2 flushed before "
+                        "each step; below the minimum bytes because the descriptors written just before stay "
+                        "partly in L2)")
 
 KERNEL_SAD_VARIANT = 2  # the probe variant whose instruction sequence the dense matcher uses
 

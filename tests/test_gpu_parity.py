@@ -187,3 +187,43 @@ def test_pipeline_end_to_end(pairs, name):
     np.testing.assert_array_equal(hL.numpy(), ref["lrL"])
     assert np.abs(hpost.numpy() - ref["post"]).max() <= POST_TOL
     pl.close()
+
+
+def test_pipeline_graph_per_buffer_set():
+    """A ring of ten input/output buffer sets (more than the eight graphs the
+    handle keeps) cycled three times: every run, eager, captured or replayed,
+    gives the eager result of its pair, and a buffer set's graph follows new
+    contents of its buffers."""
+    B = _B()
+    wl = synth.SMALL_320
+    h, w = wl.spec.h, wl.spec.w
+    n = 10
+    pairs = [synth.workload_pair(wl, 50 + i, 1)[:2] for i in range(n)]
+    ref = B.Pipeline(w, h, wl.params)
+    ref.set_graph(False)
+    exp = []
+    for L, R in pairs:
+        eL = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        eR = torch.empty_like(eL)
+        ref.run(dev(L), dev(R), eL, eR)
+        exp.append((host(eL), host(eR)))
+    ref.close()
+    pl = B.Pipeline(w, h, wl.params)
+    ins = [(dev(L), dev(R)) for L, R in pairs]
+    outs = [(torch.empty((h, w), dtype=torch.int16, device="cuda"),
+             torch.empty((h, w), dtype=torch.int16, device="cuda")) for _ in range(n)]
+    order = list(range(n)) + list(range(n)) + [3, 1, 3, 1, 7, 7]
+    for i in order:
+        oL, oR = outs[i]
+        oL.fill_(-7)
+        oR.fill_(-7)
+        pl.run(ins[i][0], ins[i][1], oL, oR)
+        np.testing.assert_array_equal(host(oL), exp[i][0], err_msg="buffer set %d" % i)
+        np.testing.assert_array_equal(host(oR), exp[i][1], err_msg="buffer set %d" % i)
+    # new contents in buffer set 3 (its graph is replayed on them)
+    ins[3][0].copy_(ins[5][0])
+    ins[3][1].copy_(ins[5][1])
+    for _ in range(2):
+        pl.run(ins[3][0], ins[3][1], outs[3][0], outs[3][1])
+        np.testing.assert_array_equal(host(outs[3][0]), exp[5][0])
+    pl.close()
