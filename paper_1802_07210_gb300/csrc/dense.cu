@@ -9,7 +9,8 @@
 //                      write a pixel when the three integer edge functions
 //                      own it (E >= 0 on owned edges, E >= 1 otherwise), so
 //                      ownership is exactly the top-left rule.  Triangles
-//                      whose bounding box exceeds kBigArea pixels are listed
+//                      whose bounding box exceeds kBigAreaOne (one pair) or
+//                      kBigAreaBatch pixels are listed
 //                      instead (in up to kBigSplit parts) and drawn by
 //                      plane_raster_big_kernel, one CTA per part (rows over
 //                      warps, lanes across x; there the owned x-range of a
@@ -64,7 +65,10 @@ __device__ __forceinline__ int side_ntri(const RasterSide &S) {
 }
 
 
-constexpr int kBigArea = 1024;  // bounding-box pixels above which a triangle is "big"
+// bounding-box pixels above which a triangle is "big": one pair (latency:
+// shorter tails in the small-triangle kernel) and batches (throughput)
+constexpr int kBigAreaOne = 384;
+constexpr int kBigAreaBatch = 1024;
 
 // Plane and positively oriented integer edges of one triangle.
 struct TriGeom {
@@ -171,7 +175,7 @@ __device__ __forceinline__ void raster_box(const TriGeom &g, int gl, int w, int 
 constexpr int kRasterGroup = 8;  // lanes per small triangle
 constexpr int kBigSplit = 8;      // CTAs a big triangle is spread over, at most
 
-__device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb) {
+__device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb, int big_area) {
     const int side = vb.y;
     const RasterSide S = side ? a.s[1] : a.s[0];
     const int gl = threadIdx.x & (kRasterGroup - 1);
@@ -181,7 +185,7 @@ __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB 
         const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
         if (g.empty) continue;
         const int rows = g.ymax - g.ymin + 1;
-        if ((g.xmax - g.xmin + 1) * rows > kBigArea) {
+        if ((g.xmax - g.xmin + 1) * rows > big_area) {
             // drawn by plane_raster_big_kernel, split over up to kBigSplit CTAs
             const int nsub = min(kBigSplit, (rows + 31) / 32);
             if (gl == 0) {
@@ -194,10 +198,13 @@ __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB 
     }
 }
 
-__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) { plane_raster_body(a, vb_single()); }
-__global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
+    plane_raster_body(a, vb_single(), kBigAreaOne);
+}
+__global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *__restrict__ tab, VMap vm,
+                                                             int big_area) {
     const VB vb = vb_batch(vm);
-    plane_raster_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    plane_raster_body(slot_entry(tab, vm.stride, vb.slot), vb, big_area);
 }
 
 // Big triangles: each list entry is one of the nsub parts of a triangle, one
@@ -453,7 +460,7 @@ static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
     if (maxt == 0) return ELAS_OK;
     const int wpb = 256 / kRasterGroup;  // triangles per CTA pass
     int blocks = (maxt + wpb - 1) / wpb;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 152 * 4) blocks = 152 * 4;
     plane_raster_kernel<<<dim3(blocks, a.nsides), 256, 0, st>>>(a);
     elas_status s = launch_status("plane_raster_kernel");
     if (s != ELAS_OK) return s;
@@ -590,7 +597,8 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }
     raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
-    plane_raster_kernel_b<<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri);
+    plane_raster_kernel_b<<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri,
+                                                             pairs.n == 1 ? kBigAreaOne : kBigAreaBatch);
     plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
