@@ -15,11 +15,13 @@
 //   consistency_kernel      32x8 candidate tile with its halo in shared
 //                           memory, window count per candidate; also clears
 //                           the grid-vector masks.
-//   redundancy_grid_kernel  one lattice row per CTA: four directional scans,
-//                           atomicOr of the {d-1,d,d+1} bits of every
-//                           surviving point into the 3x3 cells around it (OR
-//                           is order free, so the masks are deterministic),
-//                           and the row's point count.
+//   redundancy_grid_kernel  one lattice row per CTA: four directional scans
+//                           over the rows within maxd (staged in shared
+//                           memory), atomicOr of the {d-1,d,d+1} bits of every
+//                           surviving point into the 3x3 cells around it (in
+//                           shared memory, then one global atomic per word;
+//                           OR is order free, so the masks are
+//                           deterministic), and the row's point count.
 //   compact_rows_kernel     one lattice row per CTA: offset = points in the
 //                           rows above, ballot-based placement; raster order.
 #include "launch.cuh"
@@ -325,26 +327,50 @@ __device__ __forceinline__ void or_bits(uint32_t *cell, int d, int dmin, int dma
 
 
 // Redundancy filter for one lattice row per CTA, the grid-vector bits of the
-// surviving points (atomicOr: order free) and the row's point count.
-__device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB &vb) {
+// surviving points and the row's point count.  Staged (when the shared
+// memory fits): the consistency rows within maxd are read once into shared
+// memory, and the bits go to a shared copy of the three cell rows the row's
+// points reach (both sides), ORed into the grid with one atomic per non-zero
+// word afterwards; else every read and OR goes to global memory.  OR is order
+// free, so the masks are deterministic either way.
+__host__ __device__ __forceinline__ size_t red_rows_bytes(int wc, int maxd) {
+    return ((size_t)(2 * maxd + 1) * wc * sizeof(int16_t) + 15) & ~(size_t)15;
+}
+__host__ __device__ __forceinline__ size_t red_smem_bytes(int wc, int maxd, int gw, int nw) {
+    return red_rows_bytes(wc, maxd) + 2 * (size_t)3 * gw * nw * sizeof(uint32_t);
+}
+
+__device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB &vb, bool staged) {
+    extern __shared__ __align__(16) unsigned char s_red[];
     __shared__ int s_cnt[4];
     const int16_t *__restrict__ con = ra.con;
     const int wc = ra.wc, hc = ra.hc, maxd = ra.maxd;
     const GridArgs g = ra.g;
-    const int ic = vb.x;
+    const int ic = vb.x, tid = threadIdx.x, nth = blockDim.x;
+    const int r0 = max(0, ic - maxd), r1 = min(hc - 1, ic + maxd);
+    int16_t *s_rows = reinterpret_cast<int16_t *>(s_red);
+    uint32_t *s_or = reinterpret_cast<uint32_t *>(s_red + red_rows_bytes(wc, maxd));
+    const int cy = ic * g.step / g.G, cy0 = max(0, cy - 1), ncy = min(g.gh - 1, cy + 1) - cy0 + 1;
+    const int orw = 3 * g.gw * g.nw;  // shared words per side
+    if (staged) {
+        for (int k = tid; k < (r1 - r0 + 1) * wc; k += nth) s_rows[k] = con[(size_t)r0 * wc + k];
+        for (int k = tid; k < 2 * orw; k += nth) s_or[k] = 0u;
+        __syncthreads();
+    }
+    auto at = [&](int i, int j) -> int { return staged ? s_rows[(i - r0) * wc + j] : con[(size_t)i * wc + j]; };
     int mine = 0;
-    for (int jc = threadIdx.x; jc < wc; jc += blockDim.x) {
-        const int d = con[ic * wc + jc];
+    for (int jc = tid; jc < wc; jc += nth) {
+        const int d = at(ic, jc);
         int res = d;
         if (d >= 0 && ra.enabled) {
             const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
             bool redundant = true;
             for (int k = 0; k < 4 && redundant; ++k) {
                 bool found = false;
-                for (int s = 1; s <= maxd; ++s) {
-                    const int i2 = ic + s * di[k], j2 = jc + s * dj[k];
+                for (int st = 1; st <= maxd; ++st) {
+                    const int i2 = ic + st * di[k], j2 = jc + st * dj[k];
                     if (i2 < 0 || i2 >= hc || j2 < 0 || j2 >= wc) break;
-                    if (con[i2 * wc + j2] == d) {
+                    if (at(i2, j2) == d) {
                         found = true;
                         break;
                     }
@@ -353,31 +379,49 @@ __device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB
             }
             if (redundant) res = -1;
         }
-        ra.dcan[ic * wc + jc] = (int16_t)res;
+        ra.dcan[(size_t)ic * wc + jc] = (int16_t)res;
         if (res >= 0) {
             ++mine;
-            const int u = jc * g.step, v = ic * g.step;
-            const int cy = v / g.G;
+            const int u = jc * g.step;
             for (int side = 0; side < 2; ++side) {
                 uint32_t *grid = side ? ra.gridR : ra.gridL;
                 if (!grid) continue;
                 const int cx = (side ? u - res : u) / g.G;
-                for (int y = max(0, cy - 1); y <= min(g.gh - 1, cy + 1); ++y)
-                    for (int x = max(0, cx - 1); x <= min(g.gw - 1, cx + 1); ++x)
-                        or_bits(grid + ((size_t)y * g.gw + x) * g.nw, res, g.dmin, g.dmax);
+                for (int y = cy0; y < cy0 + ncy; ++y)
+                    for (int x = max(0, cx - 1); x <= min(g.gw - 1, cx + 1); ++x) {
+                        if (staged) {
+                            uint32_t *cell = s_or + side * orw + ((y - cy0) * g.gw + x) * g.nw;
+                            for (int dd = res - 1; dd <= res + 1; ++dd)
+                                if (dd >= g.dmin && dd <= g.dmax) atomicOr(cell + (dd >> 5), 1u << (dd & 31));
+                        } else {
+                            or_bits(grid + ((size_t)y * g.gw + x) * g.nw, res, g.dmin, g.dmax);
+                        }
+                    }
             }
         }
     }
+    if (staged) {
+        __syncthreads();
+        const int rw = ncy * g.gw * g.nw;  // words of the cell rows that exist
+        for (int k = tid; k < 2 * rw; k += nth) {
+            const int side = k / rw, rem = k - side * rw;
+            const uint32_t word = s_or[side * orw + rem];
+            uint32_t *grid = side ? ra.gridR : ra.gridL;
+            if (word && grid) atomicOr(grid + (size_t)cy0 * g.gw * g.nw + rem, word);
+        }
+    }
     mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = mine;
+    if ((tid & 31) == 0) s_cnt[tid >> 5] = mine;
     __syncthreads();
-    if (threadIdx.x == 0) ra.rowcount[ic] = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+    if (tid == 0) ra.rowcount[ic] = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
 }
 
-__global__ void __launch_bounds__(128) redundancy_grid_kernel(RedArgs ra) { redundancy_grid_body(ra, vb_single()); }
-__global__ void __launch_bounds__(128) redundancy_grid_kernel_b(const RedArgs *__restrict__ tab, VMap vm) {
+__global__ void __launch_bounds__(128) redundancy_grid_kernel(RedArgs ra, int staged) {
+    redundancy_grid_body(ra, vb_single(), staged != 0);
+}
+__global__ void __launch_bounds__(128) redundancy_grid_kernel_b(const RedArgs *__restrict__ tab, VMap vm, int staged) {
     const VB vb = vb_batch(vm);
-    redundancy_grid_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    redundancy_grid_body(slot_entry(tab, vm.stride, vb.slot), vb, staged != 0);
 }
 
 // Raster-order compaction, one lattice row per CTA: the row's offset is the
@@ -468,6 +512,16 @@ static elas_status consistency_smem_attr(const void *fn, size_t smem) {
     return ELAS_OK;
 }
 
+// Shared memory of the staged redundancy filter; more runs it unstaged.
+constexpr size_t kRedSmemMax = 96 * 1024;
+
+static elas_status red_smem_attr(const void *fn, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return launch_status("redundancy_grid_kernel shared memory attribute");
+    return ELAS_OK;
+}
+
 // Shared memory of the row-organised matcher; wider rows take the
 // per-candidate kernel, and so do launches of fewer lattice rows than two
 // per SM (one CTA per row would leave SMs idle).
@@ -518,7 +572,11 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     if ((s = consistency_smem_attr((const void *)consistency_kernel, smem)) != ELAS_OK) return s;
     consistency_kernel<<<consistency_grid(sa.cons), dim3(kConsTX, kConsTY), smem, st>>>(sa.cons);
     if ((s = launch_status("consistency_kernel")) != ELAS_OK) return s;
-    redundancy_grid_kernel<<<lattice_row_grid(sa.red.hc), 128, 0, st>>>(sa.red);
+    size_t red_smem = red_smem_bytes(sa.red.wc, sa.red.maxd, sa.red.g.gw, sa.red.g.nw);
+    const int red_staged = red_smem <= kRedSmemMax;
+    if (!red_staged) red_smem = 0;
+    if ((s = red_smem_attr((const void *)redundancy_grid_kernel, red_smem)) != ELAS_OK) return s;
+    redundancy_grid_kernel<<<lattice_row_grid(sa.red.hc), 128, red_smem, st>>>(sa.red, red_staged);
     if ((s = launch_status("redundancy_grid_kernel")) != ELAS_OK) return s;
     compact_rows_kernel<<<lattice_row_grid(sa.compact.hc), 128, 0, st>>>(sa.compact);
     return launch_status("compact_rows_kernel");
@@ -531,7 +589,7 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
     if (match_warps != 4 && match_warps != 8 && match_warps != 16)
         return fail(ELAS_ERR_INVALID_ARG, "support warps per CTA %d", match_warps);
     VMap m_match, m_cons, m_rows;
-    size_t row_smem = 0;
+    size_t row_smem = 0, red_smem = 0;
     vmap_clear(m_match, pairs.stride);
     vmap_clear(m_cons, pairs.stride);
     vmap_clear(m_rows, pairs.stride);
@@ -543,6 +601,7 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
             return fail(ELAS_ERR_INVALID_ARG, "pair %d has no lattice candidate", i);
         vmap_add(m_match, slot, support_match_grid(h.match, match_warps));
         row_smem = max(row_smem, sup_row_smem(h.match.a.wc, h.match.a.dmin, h.match.a.dmax).total);
+        red_smem = max(red_smem, red_smem_bytes(h.red.wc, h.red.maxd, h.red.g.gw, h.red.g.nw));
         vmap_add(m_cons, slot, consistency_grid(h.cons));
         vmap_add(m_rows, slot, lattice_row_grid(h.red.hc));
         cons_smem = cons_smem > consistency_smem(h.cons.r) ? cons_smem : consistency_smem(h.cons.r);
@@ -560,7 +619,10 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
     if ((s = consistency_smem_attr((const void *)consistency_kernel_b, cons_smem)) != ELAS_OK) return s;
     consistency_kernel_b<<<vmap_total(m_cons), dim3(kConsTX, kConsTY), cons_smem, st>>>(t.cons, m_cons);
     if ((s = launch_status("consistency_kernel_b")) != ELAS_OK) return s;
-    redundancy_grid_kernel_b<<<vmap_total(m_rows), 128, 0, st>>>(t.red, m_rows);
+    const int red_staged = red_smem <= kRedSmemMax;
+    if (!red_staged) red_smem = 0;
+    if ((s = red_smem_attr((const void *)redundancy_grid_kernel_b, red_smem)) != ELAS_OK) return s;
+    redundancy_grid_kernel_b<<<vmap_total(m_rows), 128, red_smem, st>>>(t.red, m_rows, red_staged);
     if ((s = launch_status("redundancy_grid_kernel_b")) != ELAS_OK) return s;
     compact_rows_kernel_b<<<vmap_total(m_rows), 128, 0, st>>>(t.compact, m_rows);
     return launch_status("compact_rows_kernel_b");
