@@ -346,9 +346,10 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                         const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
+                        const int pmask = a.prior_off ? 0 : -1;  // prior term on or off
+#pragma unroll 5
                         for (int d = lo + sub; d <= hi; d += TPP) {
-                            int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
-                            if (!a.prior_off) c += s_P[abs(d - dp)];
+                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d)) + (s_P[abs(d - dp)] & pmask);
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     }
