@@ -447,6 +447,13 @@ extern "C" elas_status elas_server_create(const elas_server_config *cfg, elas_se
         }
         s->budget = fr > s->cfg.hbm_reserve_bytes ? fr - s->cfg.hbm_reserve_bytes : 0;
     }
+    if (!s->cfg.plain) {  // slots of every shape stay mapped up to the budget once allocated
+        elas_status e = s->pool.use_own_pool(s->budget);
+        if (e != ELAS_OK) {
+            release(s);
+            return e;
+        }
+    }
     s->lanes.resize(s->cfg.lanes);
     for (Lane &ln : s->lanes) {
         const size_t cb = sizeof(int32_t) * 4 * (size_t)std::max(1, s->cfg.max_slots);

@@ -69,6 +69,25 @@ SlotPool::~SlotPool() {
     if (host_tab_) cudaFreeHost(host_tab_);
     if (h_counters_) cudaFreeHost(h_counters_);
     if (mirror_free_) cudaEventDestroy(mirror_free_);
+    if (mem_pool_) cudaMemPoolDestroy(mem_pool_);
+}
+
+elas_status SlotPool::use_own_pool(size_t keep_bytes) {
+    if (mem_pool_) return ELAS_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return launch_status("current device");
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&mem_pool_, &props) != cudaSuccess) {
+        mem_pool_ = nullptr;
+        return launch_status("slot memory pool");
+    }
+    uint64_t keep = keep_bytes;
+    if (cudaMemPoolSetAttribute(mem_pool_, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+        return launch_status("slot memory pool threshold");
+    return ELAS_OK;
 }
 
 elas_status SlotPool::init(int max_slots) {
@@ -124,8 +143,10 @@ elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStrea
     sl.tri_cap = 2 * sl.nc + 8;
     const Layout need = layout(nullptr, w, h, p);
     sl.async_mem = alloc_stream != nullptr;
-    const cudaError_t ae = alloc_stream ? cudaMallocAsync(reinterpret_cast<void **>(&sl.mem), need.bytes, alloc_stream)
-                                        : cudaMalloc(reinterpret_cast<void **>(&sl.mem), need.bytes);
+    const cudaError_t ae =
+        !alloc_stream ? cudaMalloc(reinterpret_cast<void **>(&sl.mem), need.bytes)
+        : mem_pool_   ? cudaMallocFromPoolAsync(reinterpret_cast<void **>(&sl.mem), need.bytes, mem_pool_, alloc_stream)
+                      : cudaMallocAsync(reinterpret_cast<void **>(&sl.mem), need.bytes, alloc_stream);
     if (ae != cudaSuccess) {
         cudaGetLastError();
         sl.mem = nullptr;

@@ -76,6 +76,10 @@ class SlotPool {
     ~SlotPool();
 
     elas_status init(int max_slots);
+    // Stream-ordered slot memory from a pool of this pool's own that keeps
+    // up to keep_bytes of freed memory mapped (no remapping when slots of
+    // other shapes come and go); without it the device's default pool.
+    elas_status use_own_pool(size_t keep_bytes);
     // Device bytes a slot of this shape takes.
     static size_t slot_bytes(int w, int h, const elas_params *p);
     // alloc_stream != NULL: the slot's memory comes from the stream-ordered
@@ -119,6 +123,7 @@ class SlotPool {
     cudaEvent_t mirror_free_ = nullptr;  // recorded after each upload
     bool upload_in_flight_ = false;
     size_t bytes_in_use_ = 0;
+    cudaMemPool_t mem_pool_ = nullptr;
 };
 
 }  // namespace elas
