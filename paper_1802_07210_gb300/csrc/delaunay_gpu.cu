@@ -196,9 +196,7 @@ __global__ void dt_dedup_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
 
 constexpr int kDtRadius = 24;     // pass-1 search radius (one pair)
 constexpr int kDtRadiusBatch = 18;  // pass-1 search radius in batched launches
-constexpr int kDtCandCap = 160;   // pass-1 candidates cached per warp
 constexpr int kDtSlots = 32;      // owned triangles kept per point
-constexpr int kDtWarps = 8;       // warps per CTA
 
 __device__ __forceinline__ int4 shfl4_from(const int4 &v, int src) {
     return make_int4(__shfl_sync(0xFFFFFFFFu, v.x, src), __shfl_sync(0xFFFFFFFFu, v.y, src),
@@ -1283,7 +1281,6 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     dt_init_kernel<<<dim3((nall + 255) / 256, nsides), 256, 0, st>>>(a);
     const int tb = 256;
     const int pblocks = max(1, min((cap + tb - 1) / tb, 152 * 8));
-    const int wblocks = max(1, min((cap + kDtWarps - 1) / kDtWarps, 152 * 16));
     dt_points_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_cell_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_scatter_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
