@@ -437,6 +437,50 @@ def run_serve_section(B, torch, seconds, rate_per_camera=75.0, seed=5):
     return out
 
 
+def kitti_outliers(d, gt):
+    """Accuracy of a disparity map against ground truth with the criterion
+    the paper evaluates by: an estimate is an outlier when it differs from
+    the truth by at least 3 pixels and by at least 5 %.  Returns the density
+    (valid estimates / pixels), the outlier share of the valid estimates and
+    the share of all pixels that are invalid or outliers."""
+    d = np.asarray(d, np.int64)
+    gt = np.asarray(gt, np.int64)
+    valid = d >= 0
+    err = np.abs(d - gt)
+    bad = valid & (err >= 3) & (err >= 0.05 * gt)
+    n = d.size
+    nv = int(valid.sum())
+    return {"density": nv / n, "outliers_of_valid": int(bad.sum()) / max(1, nv),
+            "outliers_all": (int(bad.sum()) + n - nv) / n}
+
+
+def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
+    """Outlier rates of the LR-checked left map (no post-processing, as the
+    paper measures) against the generator's ground truth, for support
+    densities set by the candidate lattice step (the support-point count
+    falls with the square of the step)."""
+    out = {"criterion": "|d - gt| >= 3 and >= 5 % of gt; map: LR-checked left, no post-processing",
+           "pairs_per_config": npairs}
+    for wl, cfg in (WORKLOADS["vga_640"], WORKLOADS["kitti_1242"]):
+        h, w = wl.spec.h, wl.spec.w
+        pairs = [synth.workload_pair(wl, 200 + i, cfg) for i in range(npairs)]
+        rows = {}
+        for step in steps:
+            prm = dict(wl.params, candidate_stepsize=step)
+            pl = B.Pipeline(w, h, prm)
+            dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+            acc, nsup = [], []
+            for L, R, gt in pairs:
+                pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
+                acc.append(kitti_outliers(dL.cpu().numpy(), gt))
+                nsup.append(pl.stats()["n_support"])
+            pl.close()
+            rows["step_%d" % step] = {"support_points": float(np.mean(nsup)),
+                                      **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]}}
+        out[wl.name] = rows
+    return out
+
+
 def run_only(args, B, torch, dev):
     """One section alone (profiling runs)."""
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -453,6 +497,8 @@ def run_only(args, B, torch, dev):
                                  tune=not args.no_tune)
     if args.only == "mixed":
         return run_mixed_section(B, torch, dev, stream, _Flush(), steps, args.mixed_pairs, tune=not args.no_tune)
+    if args.only == "accuracy":
+        return run_accuracy_section(B, torch, dev)
     return run_serve_section(B, torch, args.serve_seconds)
 
 
@@ -470,7 +516,7 @@ def main():
     ap.add_argument("--mixed-pairs", type=int, default=128)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--skip-extra", action="store_true", help="only the plain-path line")
-    ap.add_argument("--only", default=None, choices=["batch", "mixed", "serve"],
+    ap.add_argument("--only", default=None, choices=["batch", "mixed", "serve", "accuracy"],
                     help="run only this section (its JSON object is printed alone)")
     ap.add_argument("--no-tune", action="store_true", help="batched sections keep the default tile shapes")
     args = ap.parse_args()
@@ -606,6 +652,7 @@ def main():
         extra["mixed_batch"] = run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
                                                  args.mixed_pairs, tune=not args.no_tune)
         extra["serving"] = run_serve_section(B, torch, args.serve_seconds)
+        extra["accuracy"] = run_accuracy_section(B, torch, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,

@@ -88,6 +88,16 @@ def test_small_grid_and_lattice():
     assert st["n_support"] == len(ref["list"]) > 50
 
 
+@pytest.mark.parametrize("step", [7, 10, 14])
+def test_sparse_candidate_lattices(step):
+    """Coarser candidate lattices (sparser support, as in the accuracy sweep):
+    the whole path still equals the oracle."""
+    wl = synth.scaled_workload(400, 300, 96)
+    wl.params.update(candidate_stepsize=step)
+    ref, st = _whole(wl, 40 + step)
+    assert st["n_support"] == len(ref["list"]) > 10
+
+
 def test_wide_image_beyond_2048():
     """Pixels with x - 2 > 2047: the candidate list's padding value must
     never be admitted."""
