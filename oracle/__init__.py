@@ -64,6 +64,7 @@ def lib():
         L.oracle_dense.argtypes = [P, P, i, i, P, P, P, i, P]
         L.oracle_lr_check.argtypes = [P, P, i, i, i, P, P, P, P]
         L.oracle_postprocess.argtypes = [P, i, i, P, P]
+        L.oracle_median.argtypes = [P, i, i, i, P]
         _lib = L
     return _lib
 
@@ -249,6 +250,16 @@ def postprocess(d, prm=None):
     h, w = d.shape
     out = np.empty((h, w), np.float32)
     lib().oracle_postprocess(_ptr(d), w, h, C.byref(prm), _ptr(out))
+    return out
+
+
+def median(d, r=1):
+    """Median filter of valid disparities (Sec. VII; the reading is stated in
+    elas_oracle.h)."""
+    d = _c(d, np.int16)
+    h, w = d.shape
+    out = np.empty((h, w), np.int16)
+    lib().oracle_median(_ptr(d), w, h, int(r), _ptr(out))
     return out
 
 

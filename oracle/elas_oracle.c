@@ -730,3 +730,38 @@ void oracle_postprocess(const int16_t *d, int w, int h, const oracle_params *p, 
     free(A);
     free(B);
 }
+
+/* The median filter of Sec. VII with the reading stated in the header: a
+ * window at a time, values collected in raster order and sorted by insertion
+ * sort, the element (n-1)/2 taken. */
+void oracle_median(const int16_t *d, int w, int h, int r, int16_t *out)
+{
+    int16_t vals[(2 * 16 + 1) * (2 * 16 + 1)];
+    if (r < 0) r = 0;
+    if (r > 16) r = 16;
+    for (int v = 0; v < h; v++)
+        for (int u = 0; u < w; u++) {
+            const int16_t c = d[(size_t)v * w + u];
+            if (c < 0) {
+                out[(size_t)v * w + u] = -1;
+                continue;
+            }
+            int n = 0;
+            for (int y = v - r; y <= v + r; y++)
+                for (int x = u - r; x <= u + r; x++) {
+                    if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                    const int16_t q = d[(size_t)y * w + x];
+                    if (q >= 0) vals[n++] = q;
+                }
+            for (int i = 1; i < n; i++) {
+                const int16_t t = vals[i];
+                int j = i - 1;
+                while (j >= 0 && vals[j] > t) {
+                    vals[j + 1] = vals[j];
+                    j--;
+                }
+                vals[j + 1] = t;
+            }
+            out[(size_t)v * w + u] = vals[(n - 1) / 2];
+        }
+}

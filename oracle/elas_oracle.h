@@ -103,4 +103,11 @@ void oracle_lr_check(const int16_t *dL, const int16_t *dR, int w, int h, int thr
 /* Sec. III.A, Fig. 1(i): gap interpolation then adaptive mean. */
 void oracle_postprocess(const int16_t *d, int w, int h, const oracle_params *p, float *out);
 
+/* Sec. VII (the median filter applied for the comparison with CSM; the paper
+ * gives no size).  Reading: every valid pixel takes the median of the valid
+ * disparities in the (2r+1) x (2r+1) window around it, clipped to the image
+ * (the lower median, element (n-1)/2 of the sorted values, when n is even);
+ * invalid pixels stay -1.  out must not alias d. */
+void oracle_median(const int16_t *d, int w, int h, int r, int16_t *out);
+
 #endif

@@ -107,3 +107,35 @@ def test_adaptive_mean_invariants(orc):
     d[4, 4] = -1
     out = _post(orc, d, 0, 1)
     assert out[4, 4] == -1.0
+
+
+# ---------------------------------------------------------------------------
+# Median filter (Sec. VII; reading: median of the valid disparities in the
+# window, the lower one for an even count, invalid pixels kept)
+# ---------------------------------------------------------------------------
+
+def test_median_hand_example(orc):
+    d = np.array([[1, 2, 3], [4, 100, 6], [7, 8, -1]], np.int16)
+    # (0,0): {1,2,4,100} -> 2; (0,1): {1,2,3,4,6,100} -> 3; (1,1): eight
+    # valid values -> 4th smallest 4; (2,1): {4,6,7,8,100} -> 7
+    exp = np.array([[2, 3, 3], [4, 4, 6], [7, 7, -1]], np.int16)
+    np.testing.assert_array_equal(orc.median(d, 1), exp)
+
+
+def test_median_invariants(orc):
+    rng = np.random.default_rng(3)
+    const = np.full((9, 11), 37, np.int16)
+    np.testing.assert_array_equal(orc.median(const, 1), const)
+    np.testing.assert_array_equal(orc.median(const, 2), const)
+    spiky = const.copy()
+    spiky[4, 5] = 200  # an isolated spike in a flat region disappears
+    np.testing.assert_array_equal(orc.median(spiky, 1), const)
+    d = rng.integers(-1, 60, size=(13, 17)).astype(np.int16)
+    np.testing.assert_array_equal(orc.median(d, 0), d)  # a 1x1 window is the identity
+    out = orc.median(d, 2)
+    np.testing.assert_array_equal(out < 0, d < 0)  # invalid pixels, and only those, stay invalid
+    # every output is one of the valid values of its window
+    for v, u in [(0, 0), (6, 8), (12, 16), (3, 14)]:
+        win = d[max(0, v - 2):v + 3, max(0, u - 2):u + 3]
+        if d[v, u] >= 0:
+            assert out[v, u] in win[win >= 0]
