@@ -459,7 +459,8 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
     paper measures) against the generator's ground truth, for support
     densities set by the candidate lattice step (the support-point count
     falls with the square of the step)."""
-    out = {"criterion": "|d - gt| >= 3 and >= 5 % of gt; map: LR-checked left, no post-processing",
+    out = {"criterion": "|d - gt| >= 3 and >= 5 % of gt; map: LR-checked left, no post-processing "
+                        "(and the same map through the 3x3 median filter, elas_median)",
            "pairs_per_config": npairs}
     for wl, cfg in (WORKLOADS["vga_640"], WORKLOADS["kitti_1242"]):
         h, w = wl.spec.h, wl.spec.w
@@ -469,15 +470,39 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
             prm = dict(wl.params, candidate_stepsize=step)
             pl = B.Pipeline(w, h, prm)
             dL = torch.empty((h, w), dtype=torch.int16, device=dev)
-            acc, nsup = [], []
+            acc, acc_med, nsup = [], [], []
             for L, R, gt in pairs:
                 pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
                 acc.append(kitti_outliers(dL.cpu().numpy(), gt))
+                acc_med.append(kitti_outliers(B.elas_median(dL, 1).cpu().numpy(), gt))
                 nsup.append(pl.stats()["n_support"])
             pl.close()
             rows["step_%d" % step] = {"support_points": float(np.mean(nsup)),
-                                      **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]}}
+                                      **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]},
+                                      "with_3x3_median": {k: float(np.mean([a[k] for a in acc_med]))
+                                                          for k in acc_med[0]}}
         out[wl.name] = rows
+    # the median kernel alone on a 1242x375 map (inputs resident; radius 1
+    # and 2), against the measured copy bandwidth at its minimum bytes
+    hbm_gbs, _ = _peaks()
+    wl = WORKLOADS["kitti_1242"][0]
+    h, w = wl.spec.h, wl.spec.w
+    d = torch.randint(-1, 250, (h, w), dtype=torch.int16, device=dev)
+    o = torch.empty_like(d)
+    timing = {}
+    for r in (1, 2):
+        for _ in range(3):
+            B.elas_median(d, r, o)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+        for a_, b_ in ev:
+            a_.record()
+            B.elas_median(d, r, o)
+            b_.record()
+        torch.cuda.synchronize()
+        us = float(np.median([a_.elapsed_time(b_) for a_, b_ in ev])) * 1e3
+        gbs = 4.0 * w * h / (us * 1e-6) / 1e9  # 2 B read + 2 B written per pixel
+        timing["radius_%d" % r] = {"us": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs}
+    out["median_kernel_1242x375"] = timing
     return out
 
 

@@ -16,6 +16,7 @@
  *   elas_dense_match      grid-vector and plane-neighbourhood candidates
  *   elas_lr_check         left-right consistency (occlusion invalidation)
  *   elas_postprocess      gap interpolation + adaptive mean (smoothing)
+ *   elas_median           median filter of valid disparities (Sec. VII)
  *
  * Conventions shared by every call
  *   - All device pointers are owned by the caller.  Calls never allocate
@@ -290,6 +291,19 @@ size_t elas_postprocess_workspace_bytes(int32_t w, int32_t h);
 elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, const elas_params *p,
                              float *out, void *workspace, size_t workspace_bytes,
                              elas_stream stream);
+
+/*
+ * Median filter (Sec. VII: the refinement the paper applies for its
+ * comparison with CSM; it gives no window size).  Every valid pixel of d
+ * takes the median of the valid disparities in its (2*radius+1)^2 window,
+ * clipped to the image (the lower median, element (n-1)/2 in sorted order,
+ * when the count n is even); invalid pixels (< 0) are written as -1.
+ * d, out: device int16 [h][w], distinct (out must not alias d);
+ * radius 0..3 (0 copies).  No workspace.  Errors: ELAS_ERR_INVALID_ARG for a
+ * size, radius or pointer out of range.
+ */
+elas_status elas_median(const int16_t *d, int32_t w, int32_t h, int32_t radius, int16_t *out,
+                        elas_stream stream);
 
 /*
  * Pipeline handle: owns device buffers, pinned staging and a host worker

@@ -96,6 +96,7 @@ SIGNATURES = {
     "elas_lr_check": (C.c_int, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "elas_postprocess_workspace_bytes": (_Z, [_I, _I]),
     "elas_postprocess": (C.c_int, [_P, _I, _I, _P, _P, _P, _Z, _P]),
+    "elas_median": (C.c_int, [_P, _I, _I, _I, _P, _P]),
     "elas_pipeline_create": (C.c_int, [_I, _I, _P, _P]),
     "elas_pipeline_run": (C.c_int, [_P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_pipeline_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),

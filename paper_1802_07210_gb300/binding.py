@@ -179,6 +179,15 @@ def elas_postprocess(d, prm=None, stream=None):
     return out
 
 
+def elas_median(d, radius=1, out=None, stream=None):
+    h, w = d.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int16, device=d.device)
+    check(lib().elas_median(_dev(d, torch.int16, "d"), w, h, int(radius), _dev(out, torch.int16, "out"),
+                            _stream(stream)))
+    return out
+
+
 class Pipeline:
     """Owner of an ``elas_pipeline`` handle for one image size."""
 

@@ -356,3 +356,67 @@ extern "C" elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, 
         return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, post_workspace(w, h));
     return launch_post(d, w, h, p, out, workspace, to_stream(stream));
 }
+
+// ---------------------------------------------------------------------------
+// Median filter (Sec. VII, the refinement applied for the comparison with
+// CSM; the paper gives no size).  Every valid pixel takes the median of the
+// valid disparities in its (2r+1) x (2r+1) window clipped to the image (the
+// lower median, element (n-1)/2 in sorted order, for an even count n);
+// invalid pixels stay -1.  A 32x8 tile with its halo in shared memory (cells
+// outside the image read -1, so they drop out as invalid values).  The
+// median is found by rank, with no sort: it is the window value v with
+// #{values < v} <= (n-1)/2 < #{values <= v}.
+// ---------------------------------------------------------------------------
+namespace elas {
+
+constexpr int kMedTX = 32, kMedTY = 8, kMedMaxR = 3;
+
+__global__ void __launch_bounds__(kMedTX *kMedTY) median_kernel(const int16_t *__restrict__ d, int w, int h, int r,
+                                                                int16_t *__restrict__ out) {
+    __shared__ int16_t s[(kMedTY + 2 * kMedMaxR) * (kMedTX + 2 * kMedMaxR)];
+    const int SW = kMedTX + 2 * r, SH = kMedTY + 2 * r;
+    const int x0 = blockIdx.x * kMedTX - r, y0 = blockIdx.y * kMedTY - r;
+    const int tid = threadIdx.y * kMedTX + threadIdx.x;
+    for (int k = tid; k < SW * SH; k += kMedTX * kMedTY) {
+        const int x = x0 + k % SW, y = y0 + k / SW;
+        s[k] = (x >= 0 && x < w && y >= 0 && y < h) ? d[(size_t)y * w + x] : (int16_t)-1;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kMedTX + threadIdx.x, y = blockIdx.y * kMedTY + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int16_t *c = s + (threadIdx.y + r) * SW + threadIdx.x + r;
+    int res = -1;
+    if (c[0] >= 0) {
+        int n = 0;
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) n += c[dy * SW + dx] >= 0;
+        const int k = (n - 1) / 2;
+        for (int j = 0; j < (2 * r + 1) * (2 * r + 1) && res < 0; ++j) {
+            const int vj = c[(j / (2 * r + 1) - r) * SW + (j % (2 * r + 1) - r)];
+            if (vj < 0) continue;
+            int lt = 0, le = 0;
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int q = c[dy * SW + dx];
+                    lt += q >= 0 && q < vj;
+                    le += q >= 0 && q <= vj;
+                }
+            if (lt <= k && k < le) res = vj;
+        }
+    }
+    out[(size_t)y * w + x] = (int16_t)res;
+}
+
+}  // namespace elas
+
+extern "C" elas_status elas_median(const int16_t *d, int32_t w, int32_t h, int32_t radius, int16_t *out,
+                                   elas_stream stream) {
+    using namespace elas;
+    if (w < 1 || h < 1 || w > 16383 || h > 16383) return fail(ELAS_ERR_INVALID_ARG, "image size %dx%d", w, h);
+    if (radius < 0 || radius > kMedMaxR) return fail(ELAS_ERR_INVALID_ARG, "median radius %d (0..%d)", radius, kMedMaxR);
+    if (!d || !out) return fail(ELAS_ERR_INVALID_ARG, "NULL buffer");
+    if (d == out) return fail(ELAS_ERR_INVALID_ARG, "median output must not alias its input");
+    const dim3 grid((w + kMedTX - 1) / kMedTX, (h + kMedTY - 1) / kMedTY);
+    median_kernel<<<grid, dim3(kMedTX, kMedTY), 0, to_stream(stream)>>>(d, w, h, radius, out);
+    return launch_status("median_kernel");
+}

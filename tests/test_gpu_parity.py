@@ -227,3 +227,24 @@ def test_pipeline_graph_per_buffer_set():
         pl.run(ins[3][0], ins[3][1], outs[3][0], outs[3][1])
         np.testing.assert_array_equal(host(outs[3][0]), exp[5][0])
     pl.close()
+
+
+@pytest.mark.parametrize("size", [(37, 23), (64, 48), (203, 117)])
+def test_median_filter(size):
+    """Median filter of valid disparities (Sec. VII) against the oracle:
+    random maps with invalid pixels, every radius, ragged sizes."""
+    B = _B()
+    w, h = size
+    rng = np.random.default_rng(w * h)
+    d = rng.integers(-1, 90, size=(h, w)).astype(np.int16)
+    d[rng.random((h, w)) < 0.2] = -1
+    for r in range(4):
+        out = host(B.elas_median(dev(d), r))
+        np.testing.assert_array_equal(out, oracle.median(d, r), err_msg="radius %d" % r)
+
+
+def test_median_filter_on_a_disparity_map(pairs):
+    B = _B()
+    wl, L, R, ref = pairs["vga_640"]
+    for r in (1, 2):
+        np.testing.assert_array_equal(host(B.elas_median(dev(ref["lrL"]), r)), oracle.median(ref["lrL"], r))

@@ -48,6 +48,13 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.elas_support_workspace_bytes(64, 64, C.byref(p)) == 0
     nt = C.c_int32(-5)
     assert L.elas_triangulate(None, -1, 0, None, 0, C.byref(nt)) == 1
+    # the median filter: radius, size, NULL and aliasing checks (no CUDA call)
+    assert L.elas_median(C.c_void_p(16), 8, 8, 4, C.c_void_p(32), None) == 1
+    assert b"radius" in L.elas_last_error()
+    assert L.elas_median(C.c_void_p(16), 0, 8, 1, C.c_void_p(32), None) == 1
+    assert L.elas_median(None, 8, 8, 1, C.c_void_p(32), None) == 1
+    assert L.elas_median(C.c_void_p(16), 8, 8, 1, C.c_void_p(16), None) == 1
+    assert b"alias" in L.elas_last_error()
 
 
 def test_batch_and_server_configs_are_checked_on_the_host():
