@@ -363,9 +363,10 @@ extern "C" elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, 
 // valid disparities in its (2r+1) x (2r+1) window clipped to the image (the
 // lower median, element (n-1)/2 in sorted order, for an even count n);
 // invalid pixels stay -1.  A 32x8 tile with its halo in shared memory (cells
-// outside the image read -1, so they drop out as invalid values).  The
-// median is found by rank, with no sort: it is the window value v with
-// #{values < v} <= (n-1)/2 < #{values <= v}.
+// outside the image read -1, so they drop out as invalid values).  For a
+// 3x3 window the nine values are sorted in registers by odd-even
+// transposition (invalid -1 first); for larger ones the median is found by
+// rank: the window value v with #{values < v} <= (n-1)/2 < #{values <= v}.
 // ---------------------------------------------------------------------------
 namespace elas {
 
@@ -386,7 +387,28 @@ __global__ void __launch_bounds__(kMedTX *kMedTY) median_kernel(const int16_t *_
     if (x >= w || y >= h) return;
     const int16_t *c = s + (threadIdx.y + r) * SW + threadIdx.x + r;
     int res = -1;
-    if (c[0] >= 0) {
+    if (c[0] >= 0 && r == 1) {
+        // 3x3: odd-even transposition sort of the nine values in registers
+        // (invalid -1 sorts first), the median among the valid ones after
+        int v[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) v[j] = c[(j / 3 - 1) * SW + (j % 3 - 1)];
+#pragma unroll
+        for (int round = 0; round < 9; ++round)
+#pragma unroll
+            for (int j = round & 1; j + 1 < 9; j += 2) {
+                const int lo = min(v[j], v[j + 1]), hi = max(v[j], v[j + 1]);
+                v[j] = lo;
+                v[j + 1] = hi;
+            }
+        int ninv = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) ninv += v[j] < 0;
+        const int m = ninv + (9 - ninv - 1) / 2;
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            if (j == m) res = v[j];
+    } else if (c[0] >= 0) {
         int n = 0;
         for (int dy = -r; dy <= r; ++dy)
             for (int dx = -r; dx <= r; ++dx) n += c[dy * SW + dx] >= 0;
