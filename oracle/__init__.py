@@ -17,6 +17,8 @@ _lib = None
 FLAG_PRIOR_OFF = 1
 FLAG_FULL_RANGE = 2
 FLAG_REDUNDANCY_OFF = 4
+FLAG_SHIFT_SUM = 8
+FLAG_PAST_REDUNDANCY = 16
 
 
 class OracleParams(C.Structure):

@@ -185,6 +185,12 @@ static int best_disparity(const uint8_t *ref, const uint8_t *oth, int w, int u, 
         if (c < m2) m2 = c;
     }
     if (m2 <= 0) return -1;
+    if (p->flags & ORACLE_FLAG_SHIFT_SUM) {
+        /* Eq. 3: T_err(m2) = m2/2 + m2/4 + m2/8 + m2/32, each term a right
+         * shift of the integer m2 (the LUT shift-sum of Sec. VI.B) */
+        int t = (m2 >> 1) + (m2 >> 2) + (m2 >> 3) + (m2 >> 5);
+        return m1 <= t ? d1 : -1;
+    }
     float lhs = (float)m1;
     float rhs = p->support_threshold * (float)m2;
     if (!(lhs <= rhs)) return -1;
@@ -244,18 +250,22 @@ void oracle_filter_consistency(const int16_t *in, int wc, int hc,
 
 /* Remove a point iff a point with the identical disparity lies within
  * redun_max_dist candidates in each of the four directions (left, right, up,
- * down).  All decisions read the consistency-filtered input. */
+ * down); with ORACLE_FLAG_PAST_REDUNDANCY (Sec. VI.C) only the directions
+ * already passed in raster order count: left and up.  All decisions read the
+ * consistency-filtered input. */
 void oracle_filter_redundancy(const int16_t *in, int wc, int hc,
                               const oracle_params *p, int16_t *out)
 {
-    static const int DIRS[4][2] = {{0, -1}, {0, 1}, {-1, 0}, {1, 0}};
+    /* left, up, right, down: the past-only rule takes the first two */
+    static const int DIRS[4][2] = {{0, -1}, {-1, 0}, {0, 1}, {1, 0}};
+    const int ndir = (p->flags & ORACLE_FLAG_PAST_REDUNDANCY) ? 2 : 4;
     for (int ic = 0; ic < hc; ic++)
         for (int jc = 0; jc < wc; jc++) {
             int d = in[(size_t)ic * wc + jc];
             int16_t res = -1;
             if (d >= 0) {
                 int redundant = 1;
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < ndir; k++) {
                     int found = 0;
                     for (int s = 1; s <= p->redun_max_dist; s++) {
                         int i2 = ic + s * DIRS[k][0], j2 = jc + s * DIRS[k][1];

@@ -32,6 +32,12 @@
 #define ORACLE_FLAG_FULL_RANGE     2u  /* dense: every in-range d is a candidate,
                                           d_plane is not required            */
 #define ORACLE_FLAG_REDUNDANCY_OFF 4u  /* support: skip the redundancy filter */
+#define ORACLE_FLAG_SHIFT_SUM      8u  /* support: Eq. 3 shift-sum threshold
+                                          m1 <= (m2>>1)+(m2>>2)+(m2>>3)+(m2>>5) */
+#define ORACLE_FLAG_PAST_REDUNDANCY 16u /* support: Sec. VI.C past-only rule:
+                                          redundant iff the identical d lies
+                                          within redun_max_dist to the left and
+                                          above */
 
 typedef struct {
     int32_t disp_min, disp_max;

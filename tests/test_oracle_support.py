@@ -70,6 +70,30 @@ def test_ratio_direction_and_tie(orc):
     assert _the_candidate(orc.support_match(dL, dR, dict(BASE, support_threshold=0.05))) == 4
 
 
+def test_shift_sum_threshold(orc):
+    """Eq. 3 (ORACLE_FLAG_SHIFT_SUM): accept iff m1 <= m2/2 + m2/4 + m2/8 +
+    m2/32 with integer shifts, in place of the float ratio test."""
+    ss = dict(BASE, flags=orc.FLAG_SHIFT_SUM)
+    # m2 = 40: T = 20 + 10 + 5 + 1 = 36.  m1 = 36 is accepted (the float test
+    # at 0.85 rejects it), m1 = 38 is not
+    dL, dR = _worked_example(18, 20)
+    assert _the_candidate(orc.support_match(dL, dR, BASE)) == -1
+    assert _the_candidate(orc.support_match(dL, dR, ss)) == 4
+    dL, dR = _worked_example(19, 20)
+    assert _the_candidate(orc.support_match(dL, dR, ss)) == -1
+    # m2 = 70: T = 35 + 17 + 8 + 2 = 62 (below 0.90625 * 70 = 63.4 by the
+    # truncations): m1 = 62 accepted, m1 = 64 rejected
+    dL, dR = _worked_example(31, 35)
+    assert _the_candidate(orc.support_match(dL, dR, ss)) == 4
+    dL, dR = _worked_example(32, 35)
+    assert _the_candidate(orc.support_match(dL, dR, ss)) == -1
+    # the threshold parameter plays no part; a tie m1 = m2 stays rejected
+    dL, dR = _worked_example(18, 20)
+    assert _the_candidate(orc.support_match(dL, dR, dict(ss, support_threshold=0.01))) == 4
+    dL, dR = _worked_example(17, 17)
+    assert _the_candidate(orc.support_match(dL, dR, ss)) == -1
+
+
 def test_left_right_recheck(orc):
     # make the right-to-left re-match prefer d = 7 (cost 0) over d = 4 (cost 34):
     # |4 - 7| = 3 > lr_threshold 2 -> rejected; lr_threshold 3 -> accepted
@@ -154,6 +178,33 @@ def test_redundancy_filter(orc):
     # identical means identical: an arm at d = 11 -> kept
     g = _grid(15, 15, {**{p: 10 for p in arms[:3]}, arms[3]: 11, (7, 7): 10})
     assert orc.filter_redundancy(g, prm)[7, 7] == 10
+
+
+def test_past_only_redundancy(orc):
+    """Sec. VI.C (ORACLE_FLAG_PAST_REDUNDANCY): only the directions already
+    passed in raster order count, left and up."""
+    past = dict(redun_max_dist=3, flags=orc.FLAG_PAST_REDUNDANCY)
+    four = dict(redun_max_dist=3)
+    # identical values to the left and above: removed by the past-only rule,
+    # kept by the four-direction rule (nothing to the right or below)
+    g = _grid(9, 9, {(4, 4): 7, (4, 1): 7, (1, 4): 7})
+    assert orc.filter_redundancy(g, past)[4, 4] == -1
+    assert orc.filter_redundancy(g, four)[4, 4] == 7
+    # the points that supplied them have no past partner: kept
+    assert orc.filter_redundancy(g, past)[4, 1] == 7 and orc.filter_redundancy(g, past)[1, 4] == 7
+    # identical values only to the right and below: kept by both rules
+    g = _grid(9, 9, {(4, 4): 7, (4, 7): 7, (7, 4): 7})
+    assert orc.filter_redundancy(g, past)[4, 4] == 7
+    assert orc.filter_redundancy(g, four)[4, 4] == 7
+    # left within reach, up beyond it (distance 4 > 3): kept
+    g = _grid(9, 9, {(5, 4): 7, (5, 2): 7, (1, 4): 7})
+    assert orc.filter_redundancy(g, past)[5, 4] == 7
+    # the full 7x7 block: every point with a block point to its left and
+    # above goes (a 6x6 corner), the top row and the left column stay
+    pts = {(i, j): 10 for i in range(4, 11) for j in range(4, 11)}
+    out = orc.filter_redundancy(_grid(15, 15, pts), dict(redun_max_dist=5, flags=orc.FLAG_PAST_REDUNDANCY))
+    for (i, j) in pts:
+        assert out[i, j] == (-1 if i > 4 and j > 4 else 10)
 
 
 def _bits(cell):
