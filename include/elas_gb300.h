@@ -65,6 +65,12 @@ typedef enum {
 #define ELAS_FLAG_FULL_RANGE     2u /* dense: every in-range d is a candidate and no
                                        plane is required                             */
 #define ELAS_FLAG_REDUNDANCY_OFF 4u /* support: skip the redundancy filter           */
+#define ELAS_FLAG_SHIFT_SUM      8u /* support: the ambiguity test of Eq. 3 (Sec. VI.B):
+                                       accept iff m1 <= (m2>>1)+(m2>>2)+(m2>>3)+(m2>>5),
+                                       support_threshold unused                       */
+#define ELAS_FLAG_PAST_REDUNDANCY 16u /* support: the past-only redundancy rule of
+                                       Sec. VI.C: an identical d within redun_max_dist
+                                       to the left and above removes a point          */
 
 /* Method parameters.  Names follow the libelas "robotics" setting used to
  * quote the workloads; elas_params_default() fills disp_max = 255 and

@@ -20,6 +20,7 @@ struct SupportArgs {
     int dmin, dmax;
     float thr;
     int support_texture, lr_threshold;
+    int shift_sum;  // Eq. 3 threshold instead of the ratio test
 };
 
 struct MatchArgs {
@@ -42,7 +43,7 @@ struct GridArgs {
 
 struct RedArgs {
     const int16_t *con;
-    int wc, hc, maxd, enabled;
+    int wc, hc, maxd, enabled, past_only;
     GridArgs g;
     int16_t *dcan;
     uint32_t *gridL, *gridR;

@@ -29,12 +29,21 @@
 namespace elas {
 
 
+// The ambiguity test of a best cost m1 against the second minimum m2 > 0:
+// the ratio test m1 <= thr * m2 (Eq. 2, in FP32), or with shift_sum Eq. 3's
+// m1 <= m2/2 + m2/4 + m2/8 + m2/32 in integer shifts.
+__device__ __forceinline__ bool sup_unambiguous(uint32_t m1, uint32_t m2, float thr, int shift_sum) {
+    if (shift_sum) return m1 <= (m2 >> 1) + (m2 >> 2) + (m2 >> 3) + (m2 >> 5);
+    return __uint2float_rn(m1) <= __fmul_rn(thr, __uint2float_rn(m2));
+}
+
 // Best disparity of the window (a0..a3 at (u+-2, v+-2)) against `oth`,
 // searching other position uo = u + dir*d with 4 <= uo <= w-5.  Warp
 // collective; returns d1 or -1 (ambiguous / not enough disparities).
 __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth, int w, const uint4 &a0,
                                                    const uint4 &a1, const uint4 &a2, const uint4 &a3, int u,
-                                                   int v, int dir, int dmin, int dmax, float thr, int lane) {
+                                                   int v, int dir, int dmin, int dmax, float thr, int shift_sum,
+                                                   int lane) {
     int lo, hi;
     if (dir < 0) {
         lo = max(dmin, u - w + 5);
@@ -72,7 +81,7 @@ __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth
     const uint32_t mine = (d1 == gd1) ? m2 : m1;
     const uint32_t gm2 = __reduce_min_sync(0xFFFFFFFFu, mine);
     if (gm2 == 0u || gm2 == 0xFFFFFFFFu) return -1;
-    return (__uint2float_rn(gm1) <= __fmul_rn(thr, __uint2float_rn(gm2))) ? gd1 : -1;
+    return sup_unambiguous(gm1, gm2, thr, shift_sum) ? gd1 : -1;
 }
 
 __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB &vb) {
@@ -92,7 +101,8 @@ __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB 
         const uint4 l2 = __ldg(dL + rb + u - 2), l3 = __ldg(dL + rb + u + 2);
         const uint32_t texL = texture16(l0) + texture16(l1) + texture16(l2) + texture16(l3);
         if ((int)texL >= a.support_texture) {
-            const int d1 = warp_best_disparity(dR, w, l0, l1, l2, l3, u, v, -1, a.dmin, a.dmax, a.thr, lane);
+            const int d1 =
+                warp_best_disparity(dR, w, l0, l1, l2, l3, u, v, -1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
             if (d1 >= 0) {
                 const int ur = u - d1;
                 const uint4 r0 = __ldg(dR + rt + ur - 2), r1 = __ldg(dR + rt + ur + 2);
@@ -100,7 +110,7 @@ __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB 
                 const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
                 if ((int)texR >= a.support_texture) {
                     const int d2 =
-                        warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, a.dmin, a.dmax, a.thr, lane);
+                        warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
                     if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
                 }
             }
@@ -232,7 +242,7 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
             }
             const uint32_t gm1 = best >> 16;
             if (gm2 != 0u && gm2 != 0xFFFFFFFFu &&
-                __uint2float_rn(gm1) <= __fmul_rn(a.thr, __uint2float_rn(gm2)))
+                sup_unambiguous(gm1, gm2, a.thr, a.shift_sum))
                 d1 = (int)(best & 0xFFFFu);
         }
         s_d1[k] = d1;
@@ -249,7 +259,7 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
         const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
         int out = -1;
         if ((int)texR >= a.support_texture) {
-            const int d2 = warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, dmin, dmax, a.thr, lane);
+            const int d2 = warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, dmin, dmax, a.thr, a.shift_sum, lane);
             if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
         }
         if (lane == 0) m.raw[ic * wc + k] = (int16_t)out;
@@ -363,9 +373,11 @@ __device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB
         const int d = at(ic, jc);
         int res = d;
         if (d >= 0 && ra.enabled) {
-            const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
+            // left, up, right, down: the past-only rule (Sec. VI.C) takes the first two
+            const int di[4] = {0, -1, 0, 1}, dj[4] = {-1, 0, 1, 0};
+            const int ndir = ra.past_only ? 2 : 4;
             bool redundant = true;
-            for (int k = 0; k < 4 && redundant; ++k) {
+            for (int k = 0; k < ndir && redundant; ++k) {
                 bool found = false;
                 for (int st = 1; st <= maxd; ++st) {
                     const int i2 = ic + st * di[k], j2 = jc + st * dj[k];
@@ -485,6 +497,7 @@ elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int 
     a.dmin = p->disp_min;
     a.dmax = p->disp_max;
     a.thr = p->support_threshold;
+    a.shift_sum = (p->test_flags & ELAS_FLAG_SHIFT_SUM) ? 1 : 0;
     a.support_texture = p->support_texture;
     a.lr_threshold = p->lr_threshold;
     const int nc = a.wc * a.hc;
@@ -497,6 +510,7 @@ elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int 
     o->cons = ConsArgs{raw, a.wc, a.hc, p->incon_window_size, p->incon_threshold, p->incon_min_support, con,
                        grid_L, grid_R, g.gw * g.gh * g.nw};
     o->red = RedArgs{con, a.wc, a.hc, p->redun_max_dist, (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1,
+                     (p->test_flags & ELAS_FLAG_PAST_REDUNDANCY) ? 1 : 0,
                      GridArgs{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax}, d_can, grid_L, grid_R,
                      rowcount};
     o->compact = CompactArgs{d_can, a.wc, a.hc, a.step, rowcount, list, count};

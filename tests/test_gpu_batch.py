@@ -248,14 +248,17 @@ def test_batch_with_row_organised_support_matching():
     items = [(synth.VGA_640, 2, i) for i in range(4)] + [(synth.KITTI_1242, 3, i) for i in range(4)]
     pairs = [synth.workload_pair(wl, idx, cfg)[:2] for wl, cfg, idx in items]
     shapes = [(wl.spec.w, wl.spec.h) for wl, _, _ in items]
-    b = B.Batch(shapes, [wl.params for wl, _, _ in items])
+    # two pairs take the paper's shift-sum threshold and past-only redundancy
+    variants = oracle.FLAG_SHIFT_SUM | oracle.FLAG_PAST_REDUNDANCY
+    prms = [dict(wl.params, flags=variants) if i in (1, 5) else dict(wl.params) for i, (wl, _, _) in enumerate(items)]
+    b = B.Batch(shapes, prms)
     dL = [torch.empty((h, w), dtype=torch.int16, device="cuda") for w, h in shapes]
     dR = [torch.empty_like(t) for t in dL]
     b.run([dev(L) for L, _ in pairs], [dev(R) for _, R in pairs], dL, dR)
     st = b.stats()
     for i, ((wl, _, _), (L, R)) in enumerate(zip(items, pairs)):
         h, w = L.shape
-        pl = B.Pipeline(w, h, wl.params)
+        pl = B.Pipeline(w, h, prms[i])
         aL = torch.empty((h, w), dtype=torch.int16, device="cuda")
         aR = torch.empty_like(aL)
         pl.run(dev(L), dev(R), aL, aR)
@@ -263,11 +266,11 @@ def test_batch_with_row_organised_support_matching():
         np.testing.assert_array_equal(host(dR[i]), host(aR), err_msg="pair %d right" % i)
         assert st["n_support"][i] == pl.stats()["n_support"], i
         pl.close()
-    L, R = pairs[0]
-    wl = items[0][0]
-    ref = oracle.support_list(oracle.support_points(oracle.descriptors(L), oracle.descriptors(R), wl.params),
-                              wl.params)
-    assert st["n_support"][0] == len(ref)
+    for i in (0, 1):
+        L, R = pairs[i]
+        ref = oracle.support_list(oracle.support_points(oracle.descriptors(L), oracle.descriptors(R), prms[i]),
+                                  prms[i])
+        assert st["n_support"][i] == len(ref)
     b.close()
 
 

@@ -248,3 +248,43 @@ def test_median_filter_on_a_disparity_map(pairs):
     wl, L, R, ref = pairs["vga_640"]
     for r in (1, 2):
         np.testing.assert_array_equal(host(B.elas_median(dev(ref["lrL"]), r)), oracle.median(ref["lrL"], r))
+
+
+@pytest.mark.parametrize("flags", [oracle.FLAG_SHIFT_SUM, oracle.FLAG_PAST_REDUNDANCY,
+                                   oracle.FLAG_SHIFT_SUM | oracle.FLAG_PAST_REDUNDANCY])
+@pytest.mark.parametrize("name", ["small_320", "vga_640"])
+def test_support_points_paper_variants(pairs, name, flags):
+    """The paper's shift-sum ambiguity threshold (Eq. 3) and past-only
+    redundancy rule (Sec. VI.C) as flags: support output and grid vectors
+    equal the oracle's."""
+    B = _B()
+    wl, L, R, ref = pairs[name]
+    prm = dict(wl.params, flags=flags)
+    r = B.elas_support_points(dev(ref["descL"]), dev(ref["descR"]), prm)
+    exp = oracle.support_points(ref["descL"], ref["descR"], prm)
+    np.testing.assert_array_equal(host(r["d_can"]), exp)
+    lst = oracle.support_list(exp, prm)
+    n = int(host(r["count"])[0])
+    assert n == len(lst)
+    np.testing.assert_array_equal(host(r["list"])[:n], lst)
+    h, w = L.shape
+    np.testing.assert_array_equal(host(r["grid_L"]), grid_as_i32(oracle.grid_vectors(lst, w, h, prm)))
+    np.testing.assert_array_equal(host(r["grid_R"]), grid_as_i32(oracle.grid_vectors(lst, w, h, prm, right=True)))
+
+
+def test_pipeline_with_paper_variants(pairs):
+    """The whole one-pair path with both flags against the oracle pipeline."""
+    B = _B()
+    wl, L, R, _ = pairs["small_320"]
+    prm = dict(wl.params, flags=oracle.FLAG_SHIFT_SUM | oracle.FLAG_PAST_REDUNDANCY)
+    ref = oracle.pipeline(L, R, prm, postprocess_on=False)
+    h, w = L.shape
+    pl = B.Pipeline(w, h, prm)
+    dL = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    dR = torch.empty_like(dL)
+    for _ in range(2):
+        pl.run(dev(L), dev(R), dL, dR)
+        np.testing.assert_array_equal(host(dL), ref["lrL"])
+        np.testing.assert_array_equal(host(dR), ref["lrR"])
+    assert pl.stats()["n_support"] == len(ref["list"])
+    pl.close()
