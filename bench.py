@@ -481,6 +481,22 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
                                       **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]},
                                       "with_3x3_median": {k: float(np.mean([a[k] for a in acc_med]))
                                                           for k in acc_med[0]}}
+        # the paper's FPGA-side rules as flags, at the default lattice step
+        flags = {"shift_sum_eq3": 8, "past_only_redundancy": 16, "both": 24}
+        var = {}
+        for key, fl in flags.items():
+            prm = dict(wl.params, flags=fl)
+            pl = B.Pipeline(w, h, prm)
+            dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+            acc, nsup = [], []
+            for L, R, gt in pairs:
+                pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
+                acc.append(kitti_outliers(dL.cpu().numpy(), gt))
+                nsup.append(pl.stats()["n_support"])
+            pl.close()
+            var[key] = {"support_points": float(np.mean(nsup)),
+                        **{k: float(np.mean([a_[k] for a_ in acc])) for k in acc[0]}}
+        rows["step_5_variants"] = var
         out[wl.name] = rows
     # the median kernel alone on a 1242x375 map (inputs resident; radius 1
     # and 2), against the measured copy bandwidth at its minimum bytes
