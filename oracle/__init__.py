@@ -33,6 +33,7 @@ class OracleParams(C.Structure):
         ("sradius", C.c_int32), ("match_texture", C.c_int32), ("lr_threshold", C.c_int32),
         ("ipol_gap_width", C.c_int32), ("filter_adaptive_mean", C.c_int32),
         ("flags", C.c_uint32),
+        ("census_support_w", C.c_int32), ("census_dense_w", C.c_int32),
     ]
 
 
@@ -46,6 +47,7 @@ def lib():
         L.oracle_params_default.argtypes = [P]
         L.oracle_sobel.argtypes = [P, i, i, P, P]
         L.oracle_descriptors.argtypes = [P, i, i, P]
+        L.oracle_census.argtypes = [P, i, i, i, i, P]
         L.oracle_support_match.argtypes = [P, P, i, i, P, P]
         L.oracle_filter_consistency.argtypes = [P, i, i, P, P]
         L.oracle_filter_redundancy.argtypes = [P, i, i, P, P]
@@ -111,6 +113,18 @@ def descriptors(img):
     h, w = img.shape
     out = np.empty((h, w, 16), np.uint8)
     lib().oracle_descriptors(_ptr(img), w, h, _ptr(out))
+    return out
+
+
+def census(img, W, nbytes):
+    """Census transform over a W x W window, packed into nbytes bytes per
+    pixel (Sec. VI.A; bit order and border rule in elas_oracle.h)."""
+    img = _c(img, np.uint8)
+    h, w = img.shape
+    if W < 1 or W % 2 == 0 or W * W > 8 * nbytes:
+        raise ValueError("census window %d does not fit %d bytes" % (W, nbytes))
+    out = np.empty((h, w, nbytes), np.uint8)
+    lib().oracle_census(_ptr(img), w, h, int(W), int(nbytes), _ptr(out))
     return out
 
 
@@ -272,9 +286,17 @@ def pipeline(imgL, imgR, prm=None, postprocess_on=True):
     prm = _p(prm)
     h, w = np.asarray(imgL).shape
     r = {}
-    r["descL"] = descriptors(imgL)
-    r["descR"] = descriptors(imgR)
-    r["dcan"] = support_points(r["descL"], r["descR"], prm)
+    if prm.census_support_w > 0:
+        # Sec. VI.A: support census (32 bytes) and dense census (16 bytes)
+        r["sdescL"] = census(imgL, prm.census_support_w, 32)
+        r["sdescR"] = census(imgR, prm.census_support_w, 32)
+        r["descL"] = census(imgL, prm.census_dense_w, 16)
+        r["descR"] = census(imgR, prm.census_dense_w, 16)
+        r["dcan"] = support_points(r["sdescL"], r["sdescR"], prm)
+    else:
+        r["descL"] = descriptors(imgL)
+        r["descR"] = descriptors(imgR)
+        r["dcan"] = support_points(r["descL"], r["descR"], prm)
     r["list"] = support_list(r["dcan"], prm)
     r["gridL"] = grid_vectors(r["list"], w, h, prm, right=False)
     r["gridR"] = grid_vectors(r["list"], w, h, prm, right=True)

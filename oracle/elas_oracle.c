@@ -46,6 +46,8 @@ void oracle_params_default(oracle_params *p)
     p->ipol_gap_width = 3;
     p->filter_adaptive_mean = 1;
     p->flags = 0;
+    p->census_support_w = 0;
+    p->census_dense_w = 0;
 }
 
 static int iabs(int x) { return x < 0 ? -x : x; }
@@ -115,6 +117,38 @@ void oracle_descriptors(const uint8_t *img, int w, int h, uint8_t *desc)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Census transform and Hamming distance (Sec. VI.A)                          */
+/* ------------------------------------------------------------------------ */
+
+static int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+void oracle_census(const uint8_t *img, int w, int h, int W, int nbytes, uint8_t *out)
+{
+    int r = W / 2;
+    for (int v = 0; v < h; v++)
+        for (int u = 0; u < w; u++) {
+            uint8_t *o = out + ((size_t)v * w + u) * nbytes;
+            memset(o, 0, (size_t)nbytes);
+            int centre = img[(size_t)v * w + u];
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    int qx = clampi(u + dx, 0, w - 1), qy = clampi(v + dy, 0, h - 1);
+                    int k = (dy + r) * W + (dx + r);
+                    if (img[(size_t)qy * w + qx] < centre) o[k >> 3] |= (uint8_t)(1u << (k & 7));
+                }
+        }
+}
+
+/* number of differing bits of two n-byte strings */
+static int hamming(const uint8_t *a, const uint8_t *b, int n)
+{
+    int s = 0;
+    for (int k = 0; k < n; k++)
+        for (int bit = 0; bit < 8; bit++) s += ((a[k] ^ b[k]) >> bit) & 1;
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Support points (Sec. III.A; Eq. 1-2 of Sec. VI.B for the ratio test)      */
 /* ------------------------------------------------------------------------ */
 
@@ -150,8 +184,10 @@ static int window_texture(const uint8_t *desc, int w, int u, int v)
 }
 
 static int window_cost(const uint8_t *ref, const uint8_t *oth, int w, int u_ref,
-                       int u_oth, int v)
+                       int u_oth, int v, const oracle_params *p)
 {
+    if (p->census_support_w > 0) /* the 32-byte support census of each pixel */
+        return hamming(ref + ((size_t)v * w + u_ref) * 32, oth + ((size_t)v * w + u_oth) * 32, 32);
     int s = 0;
     for (int c = 0; c < 4; c++)
         s += sad16(DESC(ref, w, u_ref + CORNERS[c][0], v + CORNERS[c][1]),
@@ -172,7 +208,7 @@ static int best_disparity(const uint8_t *ref, const uint8_t *oth, int w, int u, 
     for (int d = p->disp_min; d <= p->disp_max; d++) {
         int uo = u + dir * d;
         if (uo < 4 || uo > w - 5) continue;
-        int c = window_cost(ref, oth, w, u, uo, v);
+        int c = window_cost(ref, oth, w, u, uo, v, p);
         n_eval++;
         if (c < m1) { m1 = c; d1 = d; }
     }
@@ -181,7 +217,7 @@ static int best_disparity(const uint8_t *ref, const uint8_t *oth, int w, int u, 
     for (int d = p->disp_min; d <= p->disp_max; d++) {
         int uo = u + dir * d;
         if (uo < 4 || uo > w - 5 || d == d1) continue;
-        int c = window_cost(ref, oth, w, u, uo, v);
+        int c = window_cost(ref, oth, w, u, uo, v, p);
         if (c < m2) m2 = c;
     }
     if (m2 <= 0) return -1;
@@ -206,12 +242,13 @@ void oracle_support_match(const uint8_t *descL, const uint8_t *descR, int w, int
         for (int jc = 0; jc < wc; jc++) {
             int u = jc * step, v = ic * step;
             int16_t out = -1;
+            int census = p->census_support_w > 0;
             if (u >= 4 && u <= w - 5 && v >= 4 && v <= h - 5 &&
-                window_texture(descL, w, u, v) >= p->support_texture) {
+                (census || window_texture(descL, w, u, v) >= p->support_texture)) {
                 int d1 = best_disparity(descL, descR, w, u, v, -1, p);
                 if (d1 >= 0) {
                     int ur = u - d1;
-                    if (window_texture(descR, w, ur, v) >= p->support_texture) {
+                    if (census || window_texture(descR, w, ur, v) >= p->support_texture) {
                         int d2 = best_disparity(descR, descL, w, ur, v, +1, p);
                         if (d2 >= 0 && iabs(d1 - d2) <= p->lr_threshold) out = (int16_t)d1;
                     }
@@ -624,7 +661,8 @@ void oracle_dense(const uint8_t *descL, const uint8_t *descR, int w, int h,
             out[(size_t)v * w + u] = res;
             if (u < 2 || u > w - 3 || v < 2 || v > h - 3) continue;
             const uint8_t *dr = DESC(ref, w, u, v);
-            if (texture16(dr) < p->match_texture) continue;
+            int census = p->census_dense_w > 0;
+            if (!census && texture16(dr) < p->match_texture) continue;
             int dp = full ? -1 : dplane[(size_t)v * w + u];
             if (!full && dp < 0) continue;
             const uint32_t *cell = grid ? grid + ((size_t)(v / G) * gw + (u / G)) * nw : NULL;
@@ -635,7 +673,7 @@ void oracle_dense(const uint8_t *descL, const uint8_t *descR, int w, int h,
                 int in_plane = !full && iabs(d - dp) <= sr;
                 int in_grid = !full && ((cell[d >> 5] >> (d & 31)) & 1u);
                 if (!full && !in_plane && !in_grid) continue;
-                int c = sad16(dr, DESC(oth, w, uo, v));
+                int c = census ? hamming(dr, DESC(oth, w, uo, v), 16) : sad16(dr, DESC(oth, w, uo, v));
                 if (in_plane && !prior_off) c += P[iabs(d - dp)];
                 if (c < best_c) { best_c = c; best_d = d; }
             }

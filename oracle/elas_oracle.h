@@ -51,6 +51,10 @@ typedef struct {
     int32_t sradius, match_texture, lr_threshold;
     int32_t ipol_gap_width, filter_adaptive_mean;
     uint32_t flags;
+    /* Census variant (Sec. VI.A): window widths of the support and dense
+     * census descriptors; both 0 = Sobel descriptors with SAD (Sec. III.A),
+     * else both odd, 3 <= census_support_w <= 15, 3 <= census_dense_w <= 11. */
+    int32_t census_support_w, census_dense_w;
 } oracle_params;
 
 void oracle_params_default(oracle_params *p);
@@ -58,6 +62,23 @@ void oracle_params_default(oracle_params *p);
 /* Sec. III.A / Fig. 1(b-d): Sobel responses (int32) and 16-byte descriptors. */
 void oracle_sobel(const uint8_t *img, int w, int h, int32_t *du, int32_t *dv);
 void oracle_descriptors(const uint8_t *img, int w, int h, uint8_t *desc);
+
+/* Sec. VI.A: census transform over a W x W window (W odd).  Bit k of pixel p,
+ * k = (dy + W/2) * W + (dx + W/2) for the neighbour q = p + (dx, dy), is 1 iff
+ * I(q) < I(p); a neighbour outside the image takes the value of the nearest
+ * border pixel (coordinates clamped).  The centre bit is always 0, so the
+ * descriptor has W*W bits as the paper counts them.  Bits are packed from the
+ * least significant bit of byte 0 into nbytes bytes per pixel (W*W <= 8*nbytes),
+ * the rest zero: out is uint8 [h][w][nbytes].
+ *
+ * With census widths set in the parameters the support stage takes the
+ * 32-byte support census (W = census_support_w) of each image in place of the
+ * descriptors and costs a candidate by the Hamming distance between the two
+ * pixels' census bits; the dense stage takes the 16-byte dense census
+ * (W = census_dense_w) and costs by Hamming distance too.  Neither stage then
+ * applies a texture test (the texture measure belongs to the Sobel
+ * descriptors, which the census variant does not compute). */
+void oracle_census(const uint8_t *img, int w, int h, int W, int nbytes, uint8_t *out);
 
 /* Sec. III.A, Eq. 1-2: support matching on the candidate lattice with the
  * ratio test, the texture check and the left-right re-match. */
