@@ -79,7 +79,8 @@ typedef enum {
  * redun_max_dist 5, grid_size 20, beta 0.02, gamma 3, sigma 1, sradius 2,
  * match_texture 1, lr_threshold 2, ipol_gap_width 3, filter_adaptive_mean 1.
  * Limits: 0 <= disp_min <= disp_max <= 1023, candidate_stepsize >= 1,
- * grid_size >= 1, 0 <= sradius <= 15, 0 < support_threshold. */
+ * grid_size >= 1, 0 <= sradius <= 15, 0 < support_threshold; census
+ * windows 0 (Sobel descriptors, the default) or as stated below. */
 typedef struct {
     int32_t disp_min, disp_max;
     float support_threshold;     /* Eq. 2: accept iff m1 <= t * m2                  */
@@ -97,6 +98,16 @@ typedef struct {
     int32_t ipol_gap_width;      /* max gap length filled by interpolation (0=off)  */
     int32_t filter_adaptive_mean;/* 1 = adaptive mean after interpolation           */
     uint32_t test_flags;         /* ELAS_FLAG_* (tests only)                        */
+    /* The census variant of Sec. VI.A: census windows of the support and the
+     * dense stage.  Both 0 (default): Sobel descriptors with SAD costs.
+     * Otherwise both odd, 3 <= census_support_w <= 15, 3 <= census_dense_w
+     * <= 11: the support stage takes 32-byte support census records
+     * (elas_census with window census_support_w) in place of the
+     * descriptors and costs a candidate by the Hamming distance of the two
+     * pixels' records; the dense stage takes 16-byte dense census records
+     * (window census_dense_w) and costs by Hamming distance too; neither
+     * applies a texture test (support_texture and match_texture unused). */
+    int32_t census_support_w, census_dense_w;
 } elas_params;
 
 /* A cudaStream_t passed through the C ABI. */
@@ -128,6 +139,24 @@ elas_status elas_descriptors(const uint8_t *imgL, const uint8_t *imgR, int32_t w
                              int32_t pitch, uint8_t *descL, uint8_t *descR, elas_stream stream);
 
 /*
+ * Census transform (Sec. VI.A: census descriptors compared by Hamming
+ * distance replace the Sobel descriptors and SAD).  Bit k = (dy + W/2) * W +
+ * (dx + W/2) of pixel p, for the neighbour q = p + (dx, dy) of the W x W
+ * window, is 1 iff I(q) < I(p); neighbours outside the image take the value
+ * of the nearest border pixel, so the centre bit is the only one that is
+ * always 0 and every pixel has W*W bits.  Bits are packed from the least
+ * significant bit of byte 0 (word k/32, bit k%32 of little-endian 32-bit
+ * words) into nbytes bytes per pixel, the rest 0.  window odd; nbytes 32
+ * (window 3..15: the support record) or 16 (window 3..11: the dense record).
+ * imgL/imgR: device uint8 [h][pitch] (pitch >= w); outL/outR: device uint8
+ * [h][w][nbytes], 16-byte aligned.  imgR/outR may both be NULL.
+ * Errors: ELAS_ERR_INVALID_ARG for w,h < 1, pitch < w, a window that is even,
+ * below 3 or too large for nbytes, other nbytes, NULL or misaligned buffers.
+ */
+elas_status elas_census(const uint8_t *imgL, const uint8_t *imgR, int32_t w, int32_t h, int32_t pitch,
+                        int32_t window, int32_t nbytes, uint8_t *outL, uint8_t *outR, elas_stream stream);
+
+/*
  * Support points (Sec. III.A; Eq. 1-2).  For every lattice candidate
  * (u,v) = (jc*step, ic*step) with 4 <= u <= w-5, 4 <= v <= h-5: the 64-byte
  * window = descriptors at (u+-2, v+-2); cost(d) = window SAD against the
@@ -150,6 +179,11 @@ elas_status elas_descriptors(const uint8_t *imgL, const uint8_t *imgR, int32_t w
  * cap must be >= (w/step)*(h/step), so the list can never overflow.
  * workspace: device, >= elas_support_workspace_bytes(w,h,p), 256-byte
  * aligned.
+ * With census windows in p (Sec. VI.A), descL/descR are the 32-byte support
+ * census records [h][w][32] of elas_census (window census_support_w), the
+ * window of (u,v) is the record of (u,v) itself, cost(d) is the Hamming
+ * distance of the two records, and no texture test applies; everything else
+ * (bounds, search ranges, tests, filters) is unchanged.
  */
 size_t elas_support_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
 elas_status elas_support_points(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
@@ -250,7 +284,10 @@ elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri,
  * P[k] = trunc((ln gamma - ln(gamma + exp(-k^2/(2 sigma^2)))) / beta)
  * (computed on the host in double).  Output = smallest d of the minimum
  * cost, -1 if S is empty or the pixel is not matched.  d_plane and grid may
- * be NULL only with ELAS_FLAG_FULL_RANGE.
+ * be NULL only with ELAS_FLAG_FULL_RANGE.  With census windows in p
+ * (Sec. VI.A), descL/descR are the 16-byte dense census records of
+ * elas_census (window census_dense_w), the cost is their Hamming distance in
+ * place of the SAD, and no texture test applies.
  */
 elas_status elas_dense_argmin(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
                               const elas_params *p, const int16_t *d_plane, const uint32_t *grid,
@@ -371,6 +408,9 @@ void elas_pipeline_destroy(elas_pipeline *pl);
  * and the triangulation's CTA pass takes its work from one queue over all
  * pairs.  With use_graph the launch sequence is captured once into a CUDA
  * graph and replayed.  Results are identical to the per-pair path.
+ * Batches and the server take Sobel descriptors only: parameters with
+ * census windows return ELAS_ERR_INVALID_ARG there (the census variant runs
+ * through the per-pair calls and the pipeline).
  *
  * elas_batch_create: n pairs (1 <= n <= 256), pair i of w[i] x h[i] with
  *   params[i] (w, h >= candidate_stepsize).  Allocates every slot.

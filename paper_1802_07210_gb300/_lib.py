@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("sradius", C.c_int32), ("match_texture", C.c_int32), ("lr_threshold", C.c_int32),
         ("ipol_gap_width", C.c_int32), ("filter_adaptive_mean", C.c_int32),
         ("test_flags", C.c_uint32),
+        ("census_support_w", C.c_int32), ("census_dense_w", C.c_int32),
     ]
 
 
@@ -81,6 +82,7 @@ SIGNATURES = {
     "elas_last_error": (C.c_char_p, []),
     "elas_version": (C.c_char_p, []),
     "elas_descriptors": (C.c_int, [_P, _P, _I, _I, _I, _P, _P, _P]),
+    "elas_census": (C.c_int, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "elas_support_workspace_bytes": (_Z, [_I, _I, _P]),
     "elas_support_points": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P, _Z, _P]),
     "elas_support_points_static": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P, _P, _P]),

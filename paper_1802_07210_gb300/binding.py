@@ -61,6 +61,21 @@ def elas_descriptors(imgL, imgR=None, stream=None):
     return (descL, descR) if imgR is not None else descL
 
 
+def elas_census(imgL, imgR=None, window=9, nbytes=32, stream=None):
+    """Census records of one or two images (Sec. VI.A): uint8 [h][w][nbytes]."""
+    h, w = imgL.shape
+    pL = _dev(imgL, torch.uint8, "imgL")
+    outL = torch.empty((h, w, nbytes), dtype=torch.uint8, device=imgL.device)
+    outR = None
+    pR = None
+    if imgR is not None:
+        pR = _dev(imgR, torch.uint8, "imgR", (h, w))
+        outR = torch.empty_like(outL)
+    check(lib().elas_census(pL, pR, w, h, w, int(window), int(nbytes), C.c_void_p(outL.data_ptr()),
+                            None if outR is None else C.c_void_p(outR.data_ptr()), _stream(stream)))
+    return (outL, outR) if imgR is not None else outL
+
+
 def elas_support_points(descL, descR, prm=None, grids=True, stream=None):
     prm = as_params(prm)
     h, w = descL.shape[:2]
@@ -77,8 +92,9 @@ def elas_support_points(descL, descR, prm=None, grids=True, stream=None):
         gR = torch.empty_like(gL)
     nb = lib().elas_support_workspace_bytes(w, h, C.byref(prm))
     ws = _workspace(nb, dev)
+    rec = 32 if prm.census_support_w > 0 else 16  # support census records or descriptors
     check(lib().elas_support_points(
-        _dev(descL, torch.uint8, "descL", (h, w, 16)), _dev(descR, torch.uint8, "descR", (h, w, 16)), w, h,
+        _dev(descL, torch.uint8, "descL", (h, w, rec)), _dev(descR, torch.uint8, "descR", (h, w, rec)), w, h,
         C.byref(prm), C.c_void_p(d_can.data_ptr()), C.c_void_p(lst.data_ptr()), cap,
         C.c_void_p(count.data_ptr()), _opt(gL, torch.int32, "grid_L"), _opt(gR, torch.int32, "grid_R"),
         C.c_void_p(ws.data_ptr()), nb, _stream(stream)))

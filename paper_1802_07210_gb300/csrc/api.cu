@@ -46,6 +46,12 @@ elas_status check_params(const elas_params *p, int32_t w, int32_t h) {
         return fail(ELAS_ERR_INVALID_ARG, "negative window parameter");
     if (!(p->beta > 0.0f) || !(p->gamma > 0.0f) || !(p->sigma > 0.0f))
         return fail(ELAS_ERR_INVALID_ARG, "beta, gamma, sigma must be > 0");
+    const int cs = p->census_support_w, cd = p->census_dense_w;
+    if (cs != 0 || cd != 0) {
+        if (cs < 3 || cs > 15 || cs % 2 == 0 || cd < 3 || cd > 11 || cd % 2 == 0)
+            return fail(ELAS_ERR_INVALID_ARG,
+                        "census windows %d / %d: both 0, or odd with support 3..15 and dense 3..11", cs, cd);
+    }
     return ELAS_OK;
 }
 
@@ -84,6 +90,8 @@ elas_status elas_params_default(elas_params *p) {
     p->ipol_gap_width = 3;
     p->filter_adaptive_mean = 1;
     p->test_flags = 0;
+    p->census_support_w = 0;
+    p->census_dense_w = 0;
     return ELAS_OK;
 }
 

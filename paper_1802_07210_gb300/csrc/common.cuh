@@ -88,4 +88,9 @@ __device__ __forceinline__ uint32_t texture16(const uint4 &a) {
     return sad4_acc(a.w, m, s);
 }
 
+// Hamming distance of two 128-bit census strings (Sec. VI.A).
+__device__ __forceinline__ uint32_t ham16(const uint4 &a, const uint4 &b) {
+    return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
+}
+
 }  // namespace elas

@@ -240,7 +240,13 @@ constexpr int kListPad = 16;  // padding entries (2047) after the candidate list
 // TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
 // every TPP-th candidate of its list and of its plane window and merge their
 // keys with shuffles (min is order free, so every TPP gives the same result).
-template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
+// Dense matching cost of two 16-byte descriptors: the SAD of Sobel
+// descriptors, or the Hamming distance of dense census records (Sec. VI.A).
+template <bool CENSUS> __device__ __forceinline__ int dense_cost(const uint4 &a, const uint4 &b) {
+    return CENSUS ? (int)ham16(a, b) : (int)sad16_vacc(a, b);
+}
+
+template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + kListPad];
     __shared__ int s_P[kMaxSradius + 1];
     __shared__ int s_nlist;
@@ -314,7 +320,8 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
             if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
                 const uint4 r = __ldg(ref + row + x);
                 const int dp = full ? -1 : (int)__ldg(S.dplane + row + x);
-                if ((int)texture16(r) >= a.match_texture && (full || dp >= 0)) {
+                // census records have no texture measure: no texture test
+                if ((CENSUS || (int)texture16(r) >= a.match_texture) && (full || dp >= 0)) {
                     // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
                     // (the lower bound of the first condition is <= 0; the list's
                     // padding value 2047 exceeds every dmax)
@@ -322,7 +329,7 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
                     const uint4 *orow = oth + row + x;
                     if (full) {
                         for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
-                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
+                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d));
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     } else {
@@ -342,14 +349,14 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
 #pragma unroll 8
                         for (int k = sub; k < cnt; k += TPP) {
                             const int d = s_list[k];
-                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d));
+                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d));
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                         const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
                         const int pmask = a.prior_off ? 0 : -1;  // prior term on or off
 #pragma unroll 5
                         for (int d = lo + sub; d <= hi; d += TPP) {
-                            const int c = (int)sad16_vacc(r, __ldg(orow + dir * d)) + (s_P[abs(d - dp)] & pmask);
+                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d)) + (s_P[abs(d - dp)] & pmask);
                             best = min(best, ((c + kKeyBias) << 11) | d);
                         }
                     }
@@ -370,12 +377,15 @@ template <int TPP> __device__ __forceinline__ void cell_body(const CellArgs &a, 
     }
 }
 
-__global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) { cell_body<1>(a, vb_single()); }
+template <bool CENSUS> __global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) {
+    cell_body<1, CENSUS>(a, vb_single());
+}
 
+// Batched launches carry Sobel descriptors only.
 template <int TPP>
 __global__ void __launch_bounds__(1024) cell_kernel_b(const CellArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    cell_body<TPP>(slot_entry(tab, vm.stride, vb.slot), vb);
+    cell_body<TPP, false>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // ---------------------------------------------------------------------------
@@ -483,6 +493,7 @@ static CellArgs cell_args(int w, int h, const elas_params *p, const int *P) {
     a.match_texture = p->match_texture;
     a.full = (p->test_flags & ELAS_FLAG_FULL_RANGE) ? 1 : 0;
     a.prior_off = (p->test_flags & ELAS_FLAG_PRIOR_OFF) ? 1 : 0;
+    a.census = p->census_dense_w > 0 ? 1 : 0;
     for (int k = 0; k <= kMaxSradius; ++k) a.P[k] = P[k];
     return a;
 }
@@ -499,7 +510,10 @@ dim3 cell_grid(const CellArgs &a, int nsides) {
 }
 
 static elas_status launch_cells(const CellArgs &a, int nsides, cudaStream_t st) {
-    cell_kernel<<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
+    if (a.census)
+        cell_kernel<true><<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
+    else
+        cell_kernel<false><<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
     return launch_status("cell_kernel");
 }
 

@@ -1,5 +1,6 @@
 // Descriptors: Sobel gradient images quantised to uint8 and sampled into a
-// 16-byte descriptor per pixel (Sec. III.A, Fig. 1(b-d); Sec. VI.A).
+// 16-byte descriptor per pixel (Sec. III.A, Fig. 1(b-d); Sec. VI.A); and the
+// census transform of the paper's variant (Sec. VI.A, at the end).
 //
 // One CTA produces up to four 32xTH tiles of descriptors, one above the other
 // (TH = 8 for the one-pair launch; 4, 8 or 16 in batched launches, chosen by
@@ -147,7 +148,117 @@ elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, cons
     return launch_status("descriptor_kernel_b");
 }
 
+// ---------------------------------------------------------------------------
+// Census transform (Sec. VI.A).  Bit k = (dy + R) * W + (dx + R) of a pixel
+// is set iff its neighbour at (dx, dy) is darker than the pixel (R = W/2);
+// neighbours outside the image repeat the nearest border pixel, so every
+// pixel has a full W x W census.  One CTA per 32x8 tile of one image: the
+// tile and its R-pixel halo are staged in shared memory with clamped
+// coordinates, then each thread compares its W*W neighbours (the loops are
+// unrolled, so the bit positions are constants) and stores its NW 32-bit
+// words as 16-byte vectors: NW = 8 for the 32-byte support record, 4 for the
+// 16-byte dense record.
+// ---------------------------------------------------------------------------
+constexpr int kCensusTW = 32, kCensusTH = 8;
+
+struct CensusArgs {
+    const uint8_t *imgL, *imgR;
+    int w, h, pitch;
+    uint4 *outL, *outR;
+};
+
+template <int W, int NW> __global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel(CensusArgs a) {
+    constexpr int R = W / 2, SW = kCensusTW + 2 * R, SH = kCensusTH + 2 * R;
+    static_assert(W * W <= 32 * NW, "census window does not fit the record");
+    __shared__ uint8_t s[SH][SW];
+    const uint8_t *img = blockIdx.z ? a.imgR : a.imgL;
+    uint4 *out = blockIdx.z ? a.outR : a.outL;
+    const int w = a.w, h = a.h;
+    const int x0 = blockIdx.x * kCensusTW, y0 = blockIdx.y * kCensusTH;
+    const int tid = threadIdx.y * kCensusTW + threadIdx.x;
+    for (int i = tid; i < SW * SH; i += kCensusTW * kCensusTH) {
+        const int sx = i % SW, sy = i / SW;
+        const int x = min(max(x0 - R + sx, 0), w - 1), y = min(max(y0 - R + sy, 0), h - 1);
+        s[sy][sx] = img[(size_t)y * a.pitch + x];
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int cx = threadIdx.x + R, cy = threadIdx.y + R;
+    const uint32_t c = s[cy][cx];
+    uint32_t word[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) word[j] = 0u;
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) {
+            const int k = (dy + R) * W + (dx + R);
+            word[k >> 5] |= (uint32_t)((uint32_t)s[cy + dy][cx + dx] < c) << (k & 31);
+        }
+    }
+    uint4 *o = out + ((size_t)y * w + x) * (NW / 4);
+#pragma unroll
+    for (int j = 0; j < NW / 4; ++j) o[j] = make_uint4(word[4 * j], word[4 * j + 1], word[4 * j + 2], word[4 * j + 3]);
+}
+
+template <int W, int NW>
+static elas_status census_launch(const CensusArgs &a, int two, cudaStream_t st) {
+    const dim3 grid((a.w + kCensusTW - 1) / kCensusTW, (a.h + kCensusTH - 1) / kCensusTH, two ? 2 : 1);
+    census_kernel<W, NW><<<grid, dim3(kCensusTW, kCensusTH), 0, st>>>(a);
+    return launch_status("census_kernel");
+}
+
+bool census_shape_ok(int window, int nbytes) {
+    if (nbytes != 16 && nbytes != 32) return false;
+    if (window < 3 || window % 2 == 0) return false;
+    return window * window <= 8 * nbytes;
+}
+
+elas_status launch_census(const uint8_t *imgL, const uint8_t *imgR, int w, int h, int pitch, int window, int nbytes,
+                          uint8_t *outL, uint8_t *outR, cudaStream_t st) {
+    const CensusArgs a{imgL, imgR, w, h, pitch, reinterpret_cast<uint4 *>(outL), reinterpret_cast<uint4 *>(outR)};
+    const int two = imgR != nullptr;
+    if (nbytes == 32) {
+        switch (window) {
+        case 3: return census_launch<3, 8>(a, two, st);
+        case 5: return census_launch<5, 8>(a, two, st);
+        case 7: return census_launch<7, 8>(a, two, st);
+        case 9: return census_launch<9, 8>(a, two, st);
+        case 11: return census_launch<11, 8>(a, two, st);
+        case 13: return census_launch<13, 8>(a, two, st);
+        case 15: return census_launch<15, 8>(a, two, st);
+        }
+    } else if (nbytes == 16) {
+        switch (window) {
+        case 3: return census_launch<3, 4>(a, two, st);
+        case 5: return census_launch<5, 4>(a, two, st);
+        case 7: return census_launch<7, 4>(a, two, st);
+        case 9: return census_launch<9, 4>(a, two, st);
+        case 11: return census_launch<11, 4>(a, two, st);
+        }
+    }
+    return fail(ELAS_ERR_INVALID_ARG, "census window %d with %d bytes per pixel", window, nbytes);
+}
+
 }  // namespace elas
+
+extern "C" elas_status elas_census(const uint8_t *imgL, const uint8_t *imgR, int32_t w, int32_t h, int32_t pitch,
+                                   int32_t window, int32_t nbytes, uint8_t *outL, uint8_t *outR,
+                                   elas_stream stream) {
+    using namespace elas;
+    if (w < 1 || h < 1 || w > 16383 || h > 16383) return fail(ELAS_ERR_INVALID_ARG, "image size %dx%d", w, h);
+    if (pitch < w) return fail(ELAS_ERR_INVALID_ARG, "pitch %d < width %d", pitch, w);
+    if (!census_shape_ok(window, nbytes))
+        return fail(ELAS_ERR_INVALID_ARG, "census window %d with %d bytes per pixel (odd 3..15 in 32 bytes, 3..11 in 16)",
+                    window, nbytes);
+    if (!imgL || !outL) return fail(ELAS_ERR_INVALID_ARG, "NULL left image or census buffer");
+    if ((imgR == nullptr) != (outR == nullptr))
+        return fail(ELAS_ERR_INVALID_ARG, "imgR and outR must both be set or both be NULL");
+    if (!aligned(outL, 16) || (outR && !aligned(outR, 16)))
+        return fail(ELAS_ERR_INVALID_ARG, "census buffers must be 16-byte aligned");
+    return launch_census(imgL, imgR, w, h, pitch, window, nbytes, outL, outR, to_stream(stream));
+}
 
 extern "C" elas_status elas_descriptors(const uint8_t *imgL, const uint8_t *imgR, int32_t w, int32_t h,
                                         int32_t pitch, uint8_t *descL, uint8_t *descR,

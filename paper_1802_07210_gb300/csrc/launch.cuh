@@ -11,6 +11,10 @@ namespace elas {
 // ---- one pair per launch ----------------------------------------------------
 elas_status launch_descriptors(const uint8_t *imgL, const uint8_t *imgR, int w, int h, int pitch, uint8_t *descL,
                                uint8_t *descR, cudaStream_t st);
+// Census records: window odd, 3..15 in 32 bytes per pixel or 3..11 in 16.
+bool census_shape_ok(int window, int nbytes);
+elas_status launch_census(const uint8_t *imgL, const uint8_t *imgR, int w, int h, int pitch, int window, int nbytes,
+                          uint8_t *outL, uint8_t *outR, cudaStream_t st);
 size_t support_workspace(int w, int h, const elas_params *p);
 elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                            int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,

@@ -5,7 +5,7 @@
 // and the triangles (host -> device), and one helper thread so that the
 // left- and right-coordinate triangulations run concurrently.
 //
-// Per pair: descriptors -> support (GPU) | count+list to host | two
+// Per pair: descriptors (or the two census records) -> support (GPU) | count+list to host | two
 // triangulations (host, in parallel) | triangles to device | plane prior ->
 // dense -> LR check -> post-processing (GPU).
 #include <chrono>
@@ -79,7 +79,8 @@ struct elas_pipeline {
     elas::GridGeom g{};
     // device
     uint8_t *img = nullptr;  // L then R (host-input path)
-    uint8_t *descL = nullptr, *descR = nullptr;
+    uint8_t *descL = nullptr, *descR = nullptr;  // Sobel descriptors, or dense census records
+    uint8_t *sdescL = nullptr, *sdescR = nullptr;  // census variant: support census records
     int16_t *dcan = nullptr;
     char *countlist = nullptr;  // int32 count at offset 0, int16 list at offset 16
     uint32_t *gridL = nullptr, *gridR = nullptr;
@@ -138,7 +139,7 @@ void release(elas_pipeline *pl) {
     if (pl->work) cudaStreamDestroy(pl->work);
     for (cudaEvent_t &e : pl->marks)
         if (e) cudaEventDestroy(e);
-    void *dev[] = {pl->img, pl->descL, pl->descR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
+    void *dev[] = {pl->img, pl->descL, pl->descR, pl->sdescL, pl->sdescR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
                    pl->ws_support, pl->ws_dense, pl->ws_post, pl->dL, pl->dR, pl->post, pl->ws_dt};
     for (void *d : dev)
         if (d) cudaFree(d);
@@ -202,6 +203,8 @@ extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_par
               dalloc(&pl->ws_post, pl->ws_post_bytes) == cudaSuccess &&
               dalloc(&pl->dL, npx * 2) == cudaSuccess && dalloc(&pl->dR, npx * 2) == cudaSuccess &&
               dalloc(&pl->post, npx * 4) == cudaSuccess && dalloc(&pl->ws_dt, pl->ws_dt_bytes) == cudaSuccess &&
+              (p->census_support_w == 0 ||
+               (dalloc(&pl->sdescL, npx * 32) == cudaSuccess && dalloc(&pl->sdescR, npx * 32) == cudaSuccess)) &&
               cudaMallocHost(reinterpret_cast<void **>(&pl->h_countlist), pl->countlist_bytes) == cudaSuccess &&
               cudaMallocHost(reinterpret_cast<void **>(&pl->h_tri), sizeof(int32_t) * 3 * 2 * (size_t)pl->tri_cap) ==
                   cudaSuccess;
@@ -240,10 +243,19 @@ static elas_status run_step(elas_pipeline *pl, const uint8_t *imgL, const uint8_
     };
     pl->marked = prof;
     mark(0);
-    if ((s = launch_descriptors(imgL, imgR, w, h, pitch, pl->descL, pl->descR, st)) != ELAS_OK) return s;
+    const bool census = p->census_support_w > 0;
+    if (census) {
+        // Sec. VI.A: support and dense census records in place of the descriptors
+        if ((s = launch_census(imgL, imgR, w, h, pitch, p->census_support_w, 32, pl->sdescL, pl->sdescR, st)) !=
+                ELAS_OK ||
+            (s = launch_census(imgL, imgR, w, h, pitch, p->census_dense_w, 16, pl->descL, pl->descR, st)) != ELAS_OK)
+            return s;
+    } else if ((s = launch_descriptors(imgL, imgR, w, h, pitch, pl->descL, pl->descR, st)) != ELAS_OK) {
+        return s;
+    }
     mark(1);
-    if ((s = launch_support(pl->descL, pl->descR, w, h, p, pl->dcan, list, count, pl->gridL, pl->gridR,
-                            pl->ws_support, st)) != ELAS_OK)
+    if ((s = launch_support(census ? pl->sdescL : pl->descL, census ? pl->sdescR : pl->descR, w, h, p, pl->dcan,
+                            list, count, pl->gridL, pl->gridR, pl->ws_support, st)) != ELAS_OK)
         return s;
     mark(2);
     int16_t *outR = dR ? dR : pl->dR;

@@ -21,6 +21,7 @@ struct SupportArgs {
     float thr;
     int support_texture, lr_threshold;
     int shift_sum;  // Eq. 3 threshold instead of the ratio test
+    int census;     // descriptors are 32-byte support census records (Sec. VI.A)
 };
 
 struct MatchArgs {
@@ -133,6 +134,7 @@ struct CellSide {
 struct CellArgs {
     CellSide s[2];
     int w, h, G, gw, nw, dmin, dmax, sradius, match_texture, full, prior_off;
+    int census;  // descriptors are 16-byte dense census records, Hamming cost (Sec. VI.A)
     int P[kMaxSradius + 1];
 };
 

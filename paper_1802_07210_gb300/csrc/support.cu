@@ -37,13 +37,58 @@ __device__ __forceinline__ bool sup_unambiguous(uint32_t m1, uint32_t m2, float 
     return __uint2float_rn(m1) <= __fmul_rn(thr, __uint2float_rn(m2));
 }
 
-// Best disparity of the window (a0..a3 at (u+-2, v+-2)) against `oth`,
-// searching other position uo = u + dir*d with 4 <= uo <= w-5.  Warp
-// collective; returns d1 or -1 (ambiguous / not enough disparities).
-__device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth, int w, const uint4 &a0,
-                                                   const uint4 &a1, const uint4 &a2, const uint4 &a3, int u,
-                                                   int v, int dir, int dmin, int dmax, float thr, int shift_sum,
-                                                   int lane) {
+// The matching window of pixel (u, v).  With Sobel descriptors (Sec. III.A)
+// it is the four 16-byte descriptors at (u+-2, v+-2); with the census
+// variant (Sec. VI.A) the pixel's own 32-byte support census record in q[0],
+// q[1] (q[2], q[3] stay zero and take no part in the cost).
+struct Win {
+    uint4 q[4];
+};
+
+template <bool CENSUS>
+__device__ __forceinline__ Win load_win(const uint4 *__restrict__ d, int w, int u, int v) {
+    Win r;
+    if (CENSUS) {
+        const uint4 *p = d + 2 * ((size_t)v * w + u);
+        r.q[0] = __ldg(p);
+        r.q[1] = __ldg(p + 1);
+        r.q[2] = r.q[3] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        const size_t rt = (size_t)(v - 2) * w, rb = (size_t)(v + 2) * w;
+        r.q[0] = __ldg(d + rt + u - 2);
+        r.q[1] = __ldg(d + rt + u + 2);
+        r.q[2] = __ldg(d + rb + u - 2);
+        r.q[3] = __ldg(d + rb + u + 2);
+    }
+    return r;
+}
+
+// Window cost: the SAD of the four descriptors (VACC: the vabsdiff4 form,
+// else the dp4a form; the sums are equal), or the Hamming distance of the
+// census bits.  Both stay below 2^15.
+template <bool CENSUS, bool VACC>
+__device__ __forceinline__ uint32_t win_cost(const Win &a, const Win &b) {
+    if (CENSUS) return ham16(a.q[0], b.q[0]) + ham16(a.q[1], b.q[1]);
+    if (VACC)
+        return sad16_vacc(a.q[0], b.q[0]) + sad16_vacc(a.q[1], b.q[1]) + sad16_vacc(a.q[2], b.q[2]) +
+               sad16_vacc(a.q[3], b.q[3]);
+    return sad16(a.q[0], b.q[0]) + sad16(a.q[1], b.q[1]) + sad16(a.q[2], b.q[2]) + sad16(a.q[3], b.q[3]);
+}
+
+// The texture test of a window: Sobel windows need texture >= support_texture;
+// census windows have no texture measure and always pass.
+template <bool CENSUS> __device__ __forceinline__ bool win_textured(const Win &a, int support_texture) {
+    if (CENSUS) return true;
+    const uint32_t t = texture16(a.q[0]) + texture16(a.q[1]) + texture16(a.q[2]) + texture16(a.q[3]);
+    return (int)t >= support_texture;
+}
+
+// Best disparity of window `a` of pixel (u, v) against `oth`, searching
+// other position uo = u + dir*d with 4 <= uo <= w-5.  Warp collective;
+// returns d1 or -1 (ambiguous / not enough disparities).
+template <bool CENSUS>
+__device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth, int w, const Win &a, int u, int v,
+                                                   int dir, int dmin, int dmax, float thr, int shift_sum, int lane) {
     int lo, hi;
     if (dir < 0) {
         lo = max(dmin, u - w + 5);
@@ -53,16 +98,10 @@ __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth
         hi = min(dmax, w - 5 - u);
     }
     if (hi - lo + 1 < 2) return -1;
-    const uint4 *rowT = oth + (size_t)(v - 2) * w;
-    const uint4 *rowB = oth + (size_t)(v + 2) * w;
     uint32_t m1 = 0xFFFFFFFFu, m2 = 0xFFFFFFFFu;
     int d1 = -1;
     for (int d = lo + lane; d <= hi; d += 32) {
-        const int uo = u + dir * d;
-        uint32_t c = sad16(a0, __ldg(rowT + uo - 2));
-        c += sad16(a1, __ldg(rowT + uo + 2));
-        c += sad16(a2, __ldg(rowB + uo - 2));
-        c += sad16(a3, __ldg(rowB + uo + 2));
+        const uint32_t c = win_cost<CENSUS, false>(a, load_win<CENSUS>(oth, w, u + dir * d, v));
         if (c < m1) {
             m2 = m1;
             m1 = c;
@@ -84,7 +123,7 @@ __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth
     return sup_unambiguous(gm1, gm2, thr, shift_sum) ? gd1 : -1;
 }
 
-__device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB &vb) {
+template <bool CENSUS> __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB &vb) {
     const SupportArgs &a = m.a;
     const uint4 *__restrict__ dL = m.dL;
     const uint4 *__restrict__ dR = m.dR;
@@ -96,21 +135,16 @@ __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB 
     const int u = jc * a.step, v = ic * a.step;
     int out = -1;
     if (u >= 4 && u <= w - 5 && v >= 4 && v <= a.h - 5) {
-        const size_t rt = (size_t)(v - 2) * w, rb = (size_t)(v + 2) * w;
-        const uint4 l0 = __ldg(dL + rt + u - 2), l1 = __ldg(dL + rt + u + 2);
-        const uint4 l2 = __ldg(dL + rb + u - 2), l3 = __ldg(dL + rb + u + 2);
-        const uint32_t texL = texture16(l0) + texture16(l1) + texture16(l2) + texture16(l3);
-        if ((int)texL >= a.support_texture) {
+        const Win l = load_win<CENSUS>(dL, w, u, v);
+        if (win_textured<CENSUS>(l, a.support_texture)) {
             const int d1 =
-                warp_best_disparity(dR, w, l0, l1, l2, l3, u, v, -1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
+                warp_best_disparity<CENSUS>(dR, w, l, u, v, -1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
             if (d1 >= 0) {
                 const int ur = u - d1;
-                const uint4 r0 = __ldg(dR + rt + ur - 2), r1 = __ldg(dR + rt + ur + 2);
-                const uint4 r2 = __ldg(dR + rb + ur - 2), r3 = __ldg(dR + rb + ur + 2);
-                const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
-                if ((int)texR >= a.support_texture) {
+                const Win r = load_win<CENSUS>(dR, w, ur, v);
+                if (win_textured<CENSUS>(r, a.support_texture)) {
                     const int d2 =
-                        warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
+                        warp_best_disparity<CENSUS>(dL, w, r, ur, v, +1, a.dmin, a.dmax, a.thr, a.shift_sum, lane);
                     if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
                 }
             }
@@ -119,22 +153,24 @@ __device__ __forceinline__ void support_match_body(const MatchArgs &m, const VB 
     if (lane == 0) m.raw[warp] = (int16_t)out;
 }
 
-__global__ void __launch_bounds__(512) support_match_kernel(MatchArgs m) { support_match_body(m, vb_single()); }
+template <bool CENSUS> __global__ void __launch_bounds__(512) support_match_kernel(MatchArgs m) {
+    support_match_body<CENSUS>(m, vb_single());
+}
 
 // The same matching with one CTA per lattice row, organised around the
-// right-image positions: a right window s (its four descriptors at
-// (s+-2, v+-2)) meets the candidates u = s + d of every disparity d, so a
-// warp holds the windows of 32 consecutive s in registers and walks the
-// row's candidates once: per candidate each lane costs its own d = u - s
-// against the candidate's left window (shared memory, the same address on
-// every lane), and two warp minimum-reductions give the best (cost, d) of
-// those 32 disparities and the least other cost.  Each candidate collects
-// one such result per 32-disparity window in shared memory; their merge is
-// the same (best, second) as a search over the whole range: the least key
-// over the windows and, for the second, the least of the other windows'
-// best costs and the winning window's second.  The right-to-left re-match
-// of the candidates that pass runs with one warp per candidate as in
-// support_match_kernel.  Keys are (cost << 16) | d: least cost, then least d.
+// right-image positions: a right window s meets the candidates u = s + d of
+// every disparity d, so a warp holds the windows of 32 consecutive s in
+// registers and walks the row's candidates once: per candidate each lane
+// costs its own d = u - s against the candidate's left window (shared
+// memory, the same address on every lane), and two warp minimum-reductions
+// give the best (cost, d) of those 32 disparities and the least other cost.
+// Each candidate collects one such result per 32-disparity window in shared
+// memory; their merge is the same (best, second) as a search over the whole
+// range: the least key over the windows and, for the second, the least of
+// the other windows' best costs and the winning window's second.  The
+// right-to-left re-match of the candidates that pass runs with one warp per
+// candidate as in support_match_kernel.  Keys are (cost << 16) | d: least
+// cost, then least d.
 struct SupRowSmem {
     int slots;  // windows a candidate's range can meet
     size_t desc, res, lohi, d1;  // byte offsets
@@ -152,7 +188,7 @@ __host__ __device__ __forceinline__ SupRowSmem sup_row_smem(int wc, int dmin, in
     return o;
 }
 
-__device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const VB &vb) {
+template <bool CENSUS> __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const VB &vb) {
     const SupportArgs &a = m.a;
     const uint4 *__restrict__ dL = m.dL;
     const uint4 *__restrict__ dR = m.dR;
@@ -166,20 +202,15 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
     int2 *s_lohi = reinterpret_cast<int2 *>(s_raw + L.lohi);
     int *s_d1 = reinterpret_cast<int *>(s_raw + L.d1);
     const bool row_ok = v >= 4 && v <= a.h - 5;
-    const size_t rt = (size_t)(v - 2) * w, rb = (size_t)(v + 2) * w;
     // candidates: left windows, texture, disparity range (lo > hi: none)
     for (int k = tid; k < wc; k += blockDim.x) {
         const int u = k * step;
         int lo = 1, hi = 0;
         if (row_ok && u >= 4 && u <= w - 5) {
-            const uint4 l0 = __ldg(dL + rt + u - 2), l1 = __ldg(dL + rt + u + 2);
-            const uint4 l2 = __ldg(dL + rb + u - 2), l3 = __ldg(dL + rb + u + 2);
-            s_desc[4 * k] = l0;
-            s_desc[4 * k + 1] = l1;
-            s_desc[4 * k + 2] = l2;
-            s_desc[4 * k + 3] = l3;
-            const uint32_t texL = texture16(l0) + texture16(l1) + texture16(l2) + texture16(l3);
-            if ((int)texL >= a.support_texture) {
+            const Win l = load_win<CENSUS>(dL, w, u, v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s_desc[4 * k + i] = l.q[i];
+            if (win_textured<CENSUS>(l, a.support_texture)) {
                 lo = max(dmin, u - w + 5);
                 hi = min(dmax, u - 4);
                 if (hi - lo + 1 < 2) lo = 1, hi = 0;
@@ -194,12 +225,12 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
     for (int j = warp; j < nwin; j += nwarps) {
         const int s0 = 4 + 32 * j, sl = s0 + lane;
         const bool s_ok = sl <= w - 5;
-        uint4 r0 = make_uint4(0, 0, 0, 0), r1 = r0, r2 = r0, r3 = r0;
+        Win r;
         if (s_ok) {
-            r0 = __ldg(dR + rt + sl - 2);
-            r1 = __ldg(dR + rt + sl + 2);
-            r2 = __ldg(dR + rb + sl - 2);
-            r3 = __ldg(dR + rb + sl + 2);
+            r = load_win<CENSUS>(dR, w, sl, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r.q[i] = make_uint4(0u, 0u, 0u, 0u);
         }
         // candidates u = s + d with d in [dmin, dmax] for some s of the window
         const int k0 = max(0, (s0 + dmin + step - 1) / step), k1 = min(wc - 1, (s0 + 31 + dmax) / step);
@@ -209,11 +240,10 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
             if (lh.x > lh.y) continue;  // uniform over the warp
             const int d = k * step - sl;
             const bool in = s_ok && d >= lh.x && d <= lh.y;
-            const uint4 *lw = s_desc + 4 * k;
-            uint32_t c = sad16_vacc(lw[0], r0);
-            c += sad16_vacc(lw[1], r1);
-            c += sad16_vacc(lw[2], r2);
-            c += sad16_vacc(lw[3], r3);
+            Win lw;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) lw.q[i] = s_desc[4 * k + i];
+            const uint32_t c = win_cost<CENSUS, true>(lw, r);
             const uint32_t key = in ? ((c << 16) | (uint32_t)d) : 0xFFFFFFFFu;
             const uint32_t kmin = __reduce_min_sync(0xFFFFFFFFu, key);
             const uint32_t other = (in && key != kmin) ? c : 0xFFFFFFFFu;
@@ -254,28 +284,27 @@ __device__ __forceinline__ void support_match_row_body(const MatchArgs &m, const
         const int d1 = s_d1[k];
         if (d1 < 0) continue;
         const int ur = k * step - d1;
-        const uint4 r0 = __ldg(dR + rt + ur - 2), r1 = __ldg(dR + rt + ur + 2);
-        const uint4 r2 = __ldg(dR + rb + ur - 2), r3 = __ldg(dR + rb + ur + 2);
-        const uint32_t texR = texture16(r0) + texture16(r1) + texture16(r2) + texture16(r3);
+        const Win r = load_win<CENSUS>(dR, w, ur, v);
         int out = -1;
-        if ((int)texR >= a.support_texture) {
-            const int d2 = warp_best_disparity(dL, w, r0, r1, r2, r3, ur, v, +1, dmin, dmax, a.thr, a.shift_sum, lane);
+        if (win_textured<CENSUS>(r, a.support_texture)) {
+            const int d2 = warp_best_disparity<CENSUS>(dL, w, r, ur, v, +1, dmin, dmax, a.thr, a.shift_sum, lane);
             if (d2 >= 0 && abs(d1 - d2) <= a.lr_threshold) out = d1;
         }
         if (lane == 0) m.raw[ic * wc + k] = (int16_t)out;
     }
 }
 
-__global__ void __launch_bounds__(512) support_match_row_kernel(MatchArgs m) {
-    support_match_row_body(m, vb_single());
+template <bool CENSUS> __global__ void __launch_bounds__(512) support_match_row_kernel(MatchArgs m) {
+    support_match_row_body<CENSUS>(m, vb_single());
 }
+// Batched launches carry Sobel descriptors only.
 __global__ void __launch_bounds__(512) support_match_row_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    support_match_row_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    support_match_row_body<false>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 __global__ void __launch_bounds__(512) support_match_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    support_match_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    support_match_body<false>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // Consistency filter on a 32x8 tile of candidates staged with its halo in
@@ -498,6 +527,7 @@ elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int 
     a.dmax = p->disp_max;
     a.thr = p->support_threshold;
     a.shift_sum = (p->test_flags & ELAS_FLAG_SHIFT_SUM) ? 1 : 0;
+    a.census = p->census_support_w > 0 ? 1 : 0;
     a.support_texture = p->support_texture;
     a.lr_threshold = p->lr_threshold;
     const int nc = a.wc * a.hc;
@@ -573,13 +603,24 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     }
     const int warps_per_block = 8;
     const size_t row_smem = sup_row_smem(sa.match.a.wc, sa.match.a.dmin, sa.match.a.dmax).total;
+    const bool census = sa.match.a.census != 0;
     if (row_smem <= kSupRowSmemMax && sa.match.a.hc >= kSupRowMinRows) {
-        if ((s = sup_row_smem_attr((const void *)support_match_row_kernel, row_smem)) != ELAS_OK) return s;
-        support_match_row_kernel<<<lattice_row_grid(sa.match.a.hc), 32 * warps_per_block, row_smem, st>>>(sa.match);
+        const void *fn = census ? (const void *)support_match_row_kernel<true>
+                                : (const void *)support_match_row_kernel<false>;
+        if ((s = sup_row_smem_attr(fn, row_smem)) != ELAS_OK) return s;
+        if (census)
+            support_match_row_kernel<true><<<lattice_row_grid(sa.match.a.hc), 32 * warps_per_block, row_smem, st>>>(
+                sa.match);
+        else
+            support_match_row_kernel<false><<<lattice_row_grid(sa.match.a.hc), 32 * warps_per_block, row_smem, st>>>(
+                sa.match);
         if ((s = launch_status("support_match_row_kernel")) != ELAS_OK) return s;
     } else {
-        support_match_kernel<<<support_match_grid(sa.match, warps_per_block), 32 * warps_per_block, 0, st>>>(
-            sa.match);
+        const dim3 grid = support_match_grid(sa.match, warps_per_block);
+        if (census)
+            support_match_kernel<true><<<grid, 32 * warps_per_block, 0, st>>>(sa.match);
+        else
+            support_match_kernel<false><<<grid, 32 * warps_per_block, 0, st>>>(sa.match);
         if ((s = launch_status("support_match_kernel")) != ELAS_OK) return s;
     }
     const size_t smem = consistency_smem(sa.cons.r);

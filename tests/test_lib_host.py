@@ -55,6 +55,17 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.elas_median(None, 8, 8, 1, C.c_void_p(32), None) == 1
     assert L.elas_median(C.c_void_p(16), 8, 8, 1, C.c_void_p(16), None) == 1
     assert b"alias" in L.elas_last_error()
+    # census records: window parity, range and record size (no CUDA call)
+    for window, nbytes in ((4, 32), (1, 32), (17, 32), (13, 16), (9, 24)):
+        assert L.elas_census(C.c_void_p(16), None, 8, 8, 8, window, nbytes, C.c_void_p(32), None, None) == 1
+        assert b"census" in L.elas_last_error()
+    assert L.elas_census(C.c_void_p(16), C.c_void_p(64), 8, 8, 8, 9, 32, C.c_void_p(32), None, None) == 1
+    # census windows in the parameters: both 0, or odd support 3..15 and dense 3..11
+    for cs, cd in ((9, 0), (0, 5), (8, 5), (9, 13), (17, 5), (1, 1)):
+        bad = _lib.params(census_support_w=cs, census_dense_w=cd)
+        assert L.elas_support_workspace_bytes(64, 64, C.byref(bad)) == 0, (cs, cd)
+    good = _lib.params(census_support_w=15, census_dense_w=11)
+    assert L.elas_support_workspace_bytes(64, 64, C.byref(good)) > 0
 
 
 def test_batch_and_server_configs_are_checked_on_the_host():
