@@ -481,11 +481,19 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
                                       **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]},
                                       "with_3x3_median": {k: float(np.mean([a[k] for a in acc_med]))
                                                           for k in acc_med[0]}}
-        # the paper's FPGA-side rules as flags, at the default lattice step
-        flags = {"shift_sum_eq3": 8, "past_only_redundancy": 16, "both": 24}
+        # the paper's FPGA-side choices at the default lattice step: the
+        # shift-sum threshold and past-only redundancy as flags, and census
+        # descriptors with Hamming costs (9x9 / 5x5 as the paper compares,
+        # 13x13 / 7x7; with beta 0.1 the plane prior P = [-2, -1, 0] is
+        # scaled to Hamming costs of at most 25 instead of [-14, -9, -2])
+        variants = {"shift_sum_eq3": dict(flags=8), "past_only_redundancy": dict(flags=16),
+                    "both": dict(flags=24),
+                    "census_9x9_5x5": dict(census_support_w=9, census_dense_w=5),
+                    "census_13x13_7x7": dict(census_support_w=13, census_dense_w=7),
+                    "census_9x9_5x5_beta_0.1": dict(census_support_w=9, census_dense_w=5, beta=0.1)}
         var = {}
-        for key, fl in flags.items():
-            prm = dict(wl.params, flags=fl)
+        for key, ov in variants.items():
+            prm = dict(wl.params, **ov)
             pl = B.Pipeline(w, h, prm)
             dL = torch.empty((h, w), dtype=torch.int16, device=dev)
             acc, nsup = [], []
@@ -530,7 +538,79 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
         gbs = 4.0 * w * h / (us * 1e-6) / 1e9  # 2 B read + 2 B written per pixel
         timing["radius_%d" % r] = {"us": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs}
     out["median_kernel_1242x375"] = timing
+    out["census_640x480"] = census_timing(B, torch, dev, hbm_gbs)
     return out
+
+
+def _graph_us(torch, fn, n=20):
+    """Mean time of fn() over n launches replayed from one CUDA graph (host
+    launch latency left out), after warm-up."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(n):
+                fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_.record()
+    g.replay()
+    b_.record()
+    b_.synchronize()
+    return a_.elapsed_time(b_) * 1e3 / n
+
+
+def census_timing(B, torch, dev, hbm_gbs):
+    """The census variant at 640x480 D=256: the census kernel per record kind
+    (both images per launch; minimum bytes = 2 image bytes read + 2 records
+    written per pixel) and the whole one-pair pipeline per pair, next to the
+    Sobel/SAD pipeline on the same pairs (L2 flushed before every pair)."""
+    import ctypes as C
+    from paper_1802_07210_gb300 import _lib
+    lib = _lib.lib()
+    wl, cfg = WORKLOADS["vga_640"]
+    h, w = wl.spec.h, wl.spec.w
+    L, R, _ = synth.workload_pair(wl, 300, cfg)
+    tL, tR = torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev)
+    res = {}
+    for W, nb in ((9, 32), (13, 32), (5, 16), (7, 16)):
+        oL = torch.empty((h, w, nb), dtype=torch.uint8, device=dev)
+        oR = torch.empty_like(oL)
+
+        def launch():
+            rc = lib.elas_census(C.c_void_p(tL.data_ptr()), C.c_void_p(tR.data_ptr()), w, h, w, W, nb,
+                                 C.c_void_p(oL.data_ptr()), C.c_void_p(oR.data_ptr()),
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            assert rc == 0
+        us = _graph_us(torch, launch)
+        gbs = 2.0 * w * h * (1 + nb) / (us * 1e-6) / 1e9
+        res["census_%dx%d_%dB_us" % (W, W, nb)] = {"us": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for key, ov in (("sobel_sad", {}), ("census_9x9_5x5", dict(census_support_w=9, census_dense_w=5)),
+                    ("census_13x13_7x7", dict(census_support_w=13, census_dense_w=7))):
+        pl = B.Pipeline(w, h, dict(wl.params, **ov))
+        dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+        dR = torch.empty_like(dL)
+        post = torch.empty((h, w), dtype=torch.float32, device=dev)
+        ts = []
+        for i in range(13):
+            flush.fill_(i & 255)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            pl.run(tL, tR, dL, dR, post)
+            b_.record()
+            b_.synchronize()
+            if i >= 3:
+                ts.append(a_.elapsed_time(b_))
+        pl.close()
+        res["pipeline_ms_per_pair_" + key] = float(np.median(ts))
+    return res
 
 
 def run_only(args, B, torch, dev):
