@@ -69,6 +69,7 @@ def lib():
         L.oracle_lr_check.argtypes = [P, P, i, i, i, P, P, P, P]
         L.oracle_postprocess.argtypes = [P, i, i, P, P]
         L.oracle_median.argtypes = [P, i, i, i, P]
+        L.oracle_speckle.argtypes = [P, i, i, i, i, P]
         _lib = L
     return _lib
 
@@ -276,6 +277,16 @@ def median(d, r=1):
     h, w = d.shape
     out = np.empty((h, w), np.int16)
     lib().oracle_median(_ptr(d), w, h, int(r), _ptr(out))
+    return out
+
+
+def speckle(d, sim_threshold=1, min_size=200):
+    """Small-segment removal (ELAS post-processing; the reading is stated in
+    elas_oracle.h)."""
+    d = _c(d, np.int16)
+    h, w = d.shape
+    out = np.empty((h, w), np.int16)
+    lib().oracle_speckle(_ptr(d), w, h, int(sim_threshold), int(min_size), _ptr(out))
     return out
 
 

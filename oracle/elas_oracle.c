@@ -813,3 +813,43 @@ void oracle_median(const int16_t *d, int w, int h, int r, int16_t *out)
             out[(size_t)v * w + u] = vals[(n - 1) / 2];
         }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Small-segment removal (ELAS post-processing; reading in elas_oracle.h)     */
+/* ------------------------------------------------------------------------ */
+
+void oracle_speckle(const int16_t *d, int w, int h, int sim_threshold, int min_size, int16_t *out)
+{
+    size_t n = (size_t)w * h;
+    int32_t *seg = (int32_t *)malloc(n * sizeof(int32_t));     /* segment id, -1 = none yet */
+    int32_t *queue = (int32_t *)malloc(n * sizeof(int32_t));   /* breadth-first queue       */
+    for (size_t i = 0; i < n; i++) seg[i] = -1;
+    static const int NB[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    for (size_t s = 0; s < n; s++) {
+        if (d[s] < 0 || seg[s] >= 0) continue;
+        /* grow the segment of seed s breadth first */
+        size_t head = 0, tail = 0;
+        queue[tail++] = (int32_t)s;
+        seg[s] = (int32_t)s;
+        while (head < tail) {
+            int32_t p = queue[head++];
+            int u = p % w, v = p / w;
+            for (int k = 0; k < 4; k++) {
+                int x = u + NB[k][0], y = v + NB[k][1];
+                if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                size_t q = (size_t)y * w + x;
+                if (d[q] < 0 || seg[q] >= 0) continue;
+                if (iabs((int)d[q] - (int)d[p]) > sim_threshold) continue;
+                seg[q] = (int32_t)s;
+                queue[tail++] = (int32_t)q;
+            }
+        }
+        /* the queue now lists exactly the tail pixels of this segment */
+        int16_t keep = (int64_t)tail >= (int64_t)min_size;
+        for (size_t k = 0; k < tail; k++) out[queue[k]] = keep ? d[queue[k]] : (int16_t)-1;
+    }
+    for (size_t i = 0; i < n; i++)
+        if (d[i] < 0) out[i] = -1;
+    free(seg);
+    free(queue);
+}

@@ -137,4 +137,13 @@ void oracle_postprocess(const int16_t *d, int w, int h, const oracle_params *p, 
  * invalid pixels stay -1.  out must not alias d. */
 void oracle_median(const int16_t *d, int w, int h, int r, int16_t *out);
 
+/* Small-segment (speckle) removal of ELAS's post-processing (not described
+ * in the paper, whose Sec. III.A only names post-processing).  Reading: two
+ * 4-neighbouring valid pixels are linked iff their disparities differ by at
+ * most sim_threshold; a segment is a connected component of this relation
+ * (so it can drift by more than sim_threshold end to end); every pixel of a
+ * segment with fewer than min_size pixels becomes -1, the rest are copied.
+ * The partition is unique, so the output is. */
+void oracle_speckle(const int16_t *d, int w, int h, int sim_threshold, int min_size, int16_t *out);
+
 #endif
