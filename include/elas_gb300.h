@@ -17,6 +17,7 @@
  *   elas_lr_check         left-right consistency (occlusion invalidation)
  *   elas_postprocess      gap interpolation + adaptive mean (smoothing)
  *   elas_median           median filter of valid disparities (Sec. VII)
+ *   elas_speckle          small-segment removal (ELAS post-processing)
  *
  * Conventions shared by every call
  *   - All device pointers are owned by the caller.  Calls never allocate
@@ -347,6 +348,26 @@ elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, const elas_
  */
 elas_status elas_median(const int16_t *d, int32_t w, int32_t h, int32_t radius, int16_t *out,
                         elas_stream stream);
+
+/*
+ * Small-segment (speckle) removal, ELAS post-processing (the paper names
+ * post-processing in Sec. III.A without describing it).  Two 4-neighbouring
+ * valid pixels are linked iff their disparities differ by at most
+ * sim_threshold; a segment is a connected component of the links (it may
+ * drift by more than sim_threshold end to end); every pixel of a segment
+ * with fewer than min_size pixels becomes -1, the others and the invalid
+ * pixels are copied (invalid as -1).  The partition is unique, so the
+ * output is.  d, out: device int16 [h][w]; out may equal d (in place).
+ * workspace: device, 256-byte aligned, >= elas_speckle_workspace_bytes(w, h)
+ * (two int32 maps); its first int32 is a status the caller may read after
+ * the stream completes: 0, or 1 if a union-find loop reached its bound (the
+ * pixel count), which the construction excludes.  Errors:
+ * ELAS_ERR_INVALID_ARG for a size outside 1..16383, sim_threshold < 0, NULL
+ * or misaligned buffers; ELAS_ERR_CAPACITY for a short workspace.
+ */
+size_t elas_speckle_workspace_bytes(int32_t w, int32_t h);
+elas_status elas_speckle(const int16_t *d, int32_t w, int32_t h, int32_t sim_threshold, int32_t min_size,
+                         int16_t *out, void *workspace, size_t workspace_bytes, elas_stream stream);
 
 /*
  * Pipeline handle: owns device buffers, pinned staging and a host worker

@@ -99,6 +99,8 @@ SIGNATURES = {
     "elas_postprocess_workspace_bytes": (_Z, [_I, _I]),
     "elas_postprocess": (C.c_int, [_P, _I, _I, _P, _P, _P, _Z, _P]),
     "elas_median": (C.c_int, [_P, _I, _I, _I, _P, _P]),
+    "elas_speckle_workspace_bytes": (C.c_size_t, [_I, _I]),
+    "elas_speckle": (C.c_int, [_P, _I, _I, _I, _I, _P, _P, C.c_size_t, _P]),
     "elas_pipeline_create": (C.c_int, [_I, _I, _P, _P]),
     "elas_pipeline_run": (C.c_int, [_P, _P, _P, _I, _P, _P, _P, _P]),
     "elas_pipeline_run_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),

@@ -204,6 +204,20 @@ def elas_median(d, radius=1, out=None, stream=None):
     return out
 
 
+def elas_speckle(d, sim_threshold=1, min_size=200, out=None, stream=None, with_status=False):
+    """Small-segment removal; out may be d itself (in place)."""
+    h, w = d.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int16, device=d.device)
+    nb = lib().elas_speckle_workspace_bytes(w, h)
+    ws = _workspace(nb, d.device)
+    check(lib().elas_speckle(_dev(d, torch.int16, "d"), w, h, int(sim_threshold), int(min_size),
+                             _dev(out, torch.int16, "out"), C.c_void_p(ws.data_ptr()), nb, _stream(stream)))
+    if with_status:
+        return out, ws[:4].view(torch.int32)
+    return out
+
+
 class Pipeline:
     """Owner of an ``elas_pipeline`` handle for one image size."""
 

@@ -55,6 +55,14 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.elas_median(None, 8, 8, 1, C.c_void_p(32), None) == 1
     assert L.elas_median(C.c_void_p(16), 8, 8, 1, C.c_void_p(16), None) == 1
     assert b"alias" in L.elas_last_error()
+    # speckle removal: size, threshold, NULL, alignment and workspace checks
+    nb = L.elas_speckle_workspace_bytes(64, 48)
+    assert nb >= 2 * 64 * 48 * 4 and L.elas_speckle_workspace_bytes(0, 48) == 0
+    assert L.elas_speckle(C.c_void_p(16), 64, 48, -1, 10, C.c_void_p(16), C.c_void_p(256), nb, None) == 1
+    assert L.elas_speckle(C.c_void_p(16), 0, 48, 1, 10, C.c_void_p(16), C.c_void_p(256), nb, None) == 1
+    assert L.elas_speckle(None, 64, 48, 1, 10, C.c_void_p(16), C.c_void_p(256), nb, None) == 1
+    assert L.elas_speckle(C.c_void_p(16), 64, 48, 1, 10, C.c_void_p(16), C.c_void_p(128), nb, None) == 1
+    assert L.elas_speckle(C.c_void_p(16), 64, 48, 1, 10, C.c_void_p(16), C.c_void_p(256), nb - 1, None) == 3
     # census records: window parity, range and record size (no CUDA call)
     for window, nbytes in ((4, 32), (1, 32), (17, 32), (13, 16), (9, 24)):
         assert L.elas_census(C.c_void_p(16), None, 8, 8, 8, window, nbytes, C.c_void_p(32), None, None) == 1
