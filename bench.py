@@ -470,17 +470,20 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
             prm = dict(wl.params, candidate_stepsize=step)
             pl = B.Pipeline(w, h, prm)
             dL = torch.empty((h, w), dtype=torch.int16, device=dev)
-            acc, acc_med, nsup = [], [], []
+            acc, acc_med, acc_sp, nsup = [], [], [], []
             for L, R, gt in pairs:
                 pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
                 acc.append(kitti_outliers(dL.cpu().numpy(), gt))
                 acc_med.append(kitti_outliers(B.elas_median(dL, 1).cpu().numpy(), gt))
+                acc_sp.append(kitti_outliers(B.elas_speckle(dL, 1, 200).cpu().numpy(), gt))
                 nsup.append(pl.stats()["n_support"])
             pl.close()
             rows["step_%d" % step] = {"support_points": float(np.mean(nsup)),
                                       **{k: float(np.mean([a[k] for a in acc])) for k in acc[0]},
                                       "with_3x3_median": {k: float(np.mean([a[k] for a in acc_med]))
-                                                          for k in acc_med[0]}}
+                                                          for k in acc_med[0]},
+                                      "with_speckle_1_200": {k: float(np.mean([a[k] for a in acc_sp]))
+                                                             for k in acc_sp[0]}}
         # the paper's FPGA-side choices at the default lattice step: the
         # shift-sum threshold and past-only redundancy as flags, and census
         # descriptors with Hamming costs (9x9 / 5x5 as the paper compares,
@@ -538,6 +541,7 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
         gbs = 4.0 * w * h / (us * 1e-6) / 1e9  # 2 B read + 2 B written per pixel
         timing["radius_%d" % r] = {"us": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs}
     out["median_kernel_1242x375"] = timing
+    out["speckle"] = speckle_timing(B, torch, dev, hbm_gbs)
     out["census_640x480"] = census_timing(B, torch, dev, hbm_gbs)
     return out
 
@@ -564,6 +568,39 @@ def _graph_us(torch, fn, n=20):
     b_.record()
     b_.synchronize()
     return a_.elapsed_time(b_) * 1e3 / n
+
+
+def speckle_timing(B, torch, dev, hbm_gbs):
+    """Small-segment removal (threshold 1, 200 pixels) on the path's
+    LR-checked left map of one pair per workload, its four kernels replayed
+    from a graph; minimum bytes = 2 B read + 2 B written per pixel (the
+    label and size maps, 8 B per pixel more, stay in L2 at these sizes)."""
+    import ctypes as C
+    from paper_1802_07210_gb300 import _lib
+    lib = _lib.lib()
+    res = {}
+    for key in ("vga_640", "kitti_1242"):
+        wl, cfg = WORKLOADS[key]
+        h, w = wl.spec.h, wl.spec.w
+        L, R, _ = synth.workload_pair(wl, 400, cfg)
+        pl = B.Pipeline(w, h, wl.params)
+        dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+        pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
+        pl.close()
+        out = torch.empty_like(dL)
+        nb = lib.elas_speckle_workspace_bytes(w, h)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+
+        def launch():
+            rc = lib.elas_speckle(C.c_void_p(dL.data_ptr()), w, h, 1, 200, C.c_void_p(out.data_ptr()),
+                                  C.c_void_p(ws.data_ptr()), nb, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            assert rc == 0
+        us = _graph_us(torch, launch)
+        gbs = 4.0 * w * h / (us * 1e-6) / 1e9
+        removed = int(((out < 0) & (dL >= 0)).sum().item())
+        res["%dx%d" % (w, h)] = {"us": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs,
+                                 "pixels_removed": removed}
+    return res
 
 
 def census_timing(B, torch, dev, hbm_gbs):

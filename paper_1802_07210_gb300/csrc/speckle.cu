@@ -6,14 +6,19 @@
 // Connected components by union-find over pixel indices, every parent index
 // below its child's, so a root is the least pixel index of its tree:
 //   speckle_local_kernel   one CTA per 32x16 tile: union-find of the links
-//                          inside the tile in shared memory, then each
-//                          pixel's label = the global index of its tile-local
-//                          root; clears the size counters.
-//   speckle_border_kernel  links that cross a tile's right or bottom edge,
-//                          united in global memory (atomicMin on roots).
-//   speckle_count_kernel   label = root (path flattening), then segment sizes
-//                          with one atomicAdd per distinct root per warp.
-//   speckle_apply_kernel   out = d where the segment is large enough, else -1.
+//                          inside the tile in shared memory; each pixel's
+//                          label = the global index of its tile-local root,
+//                          and each tile-local root's size entry = its
+//                          pixel count in the tile (0 for other pixels).
+//   speckle_border_kernel  one thread per link across a tile's right or
+//                          bottom edge: union in global memory (atomicMin on
+//                          roots).
+//   speckle_resolve_kernel each tile-local root finds its final root, points
+//                          its label there and adds its count to the root's
+//                          (one atomic per tile-local segment).
+//   speckle_apply_kernel   two hops (pixel -> tile-local root -> final root)
+//                          give the segment size: out = d if large enough,
+//                          else -1.
 // The partition is unique, so the output is too.  Every loop is bounded by
 // the pixel count (each step moves to a strictly smaller index); a loop that
 // reaches its bound sets the status word instead of spinning on.
@@ -36,11 +41,15 @@ __device__ __forceinline__ bool sp_linked(int a, int b, int thr) { return a >= 0
 
 // Root of x in a forest whose parents are strictly smaller indices; reads
 // through L2 (`ld.cg`) because other CTAs relink roots during the kernel.
-__device__ __forceinline__ int sp_find_global(const int32_t *L, int x, int limit) {
+// Path halving: a visited non-root is pointed at its grandparent (an
+// ancestor, so the forest stays valid; roots are only changed by unions).
+__device__ __forceinline__ int sp_find_global(int32_t *L, int x, int limit) {
     for (int it = 0; it < limit; ++it) {
         const int p = __ldcg(L + x);
         if (p == x) return x;
-        x = p;
+        const int g = __ldcg(L + p);
+        if (g != p) __stcg(L + x, g);
+        x = g;
     }
     return -1;
 }
@@ -66,11 +75,25 @@ __device__ void sp_unite_global(int32_t *L, int a, int b, int limit, int32_t *st
     atomicExch(status, 1);
 }
 
+// The same walk without writes: after the unions, each tile-local root's
+// label is set to its final root by that root's own thread alone, which a
+// halving write from another walk could overwrite with an intermediate root.
+__device__ __forceinline__ int sp_find_readonly(const int32_t *L, int x, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        const int p = __ldcg(L + x);
+        if (p == x) return x;
+        x = p;
+    }
+    return -1;
+}
+
 __device__ __forceinline__ int sp_find_shared(volatile int *L, int x) {
     for (int it = 0; it < kSpThreads; ++it) {
         const int p = L[x];
         if (p == x) return x;
-        x = p;
+        const int g = L[p];
+        if (g != p) L[x] = g;
+        x = g;
     }
     return -1;
 }
@@ -93,8 +116,15 @@ __device__ void sp_unite_shared(int *L, int a, int b, int32_t *status) {
     atomicExch(status, 1);
 }
 
+// A tile row is one warp: the horizontal links of a row become runs from one
+// ballot (a pixel's run root is the nearest run start at or left of it), so
+// union-find only joins runs through vertical links, and a vertical link is
+// skipped where the link to its left, with the two horizontal links beside
+// it, already connects the same pixels (those links are processed or
+// skipped for the same reason further left, ending at a processed one).
 __global__ void __launch_bounds__(kSpThreads) speckle_local_kernel(SpeckleArgs a) {
     __shared__ int sL[kSpThreads];
+    __shared__ int sC[kSpThreads];
     __shared__ int16_t sD[kSpThreads];
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * kSpTX + tx;
     const int x0 = blockIdx.x * kSpTX, y0 = blockIdx.y * kSpTY;
@@ -103,65 +133,103 @@ __global__ void __launch_bounds__(kSpThreads) speckle_local_kernel(SpeckleArgs a
     const size_t i = (size_t)y * a.w + x;
     const int dv = in ? a.d[i] : -1;
     sD[t] = (int16_t)dv;
-    sL[t] = dv >= 0 ? t : -1;
-    if (in) a.size[i] = 0;
+    sC[t] = 0;
     __syncthreads();
+    const bool left = tx > 0 && sp_linked(sD[t - 1], dv, a.thr);
+    const unsigned linked_left = __ballot_sync(0xFFFFFFFFu, left);
+    // run starts at or left of this lane (lane 0 is never linked left)
+    const unsigned starts = ~linked_left & (0xFFFFFFFFu >> (31 - tx));
+    sL[t] = dv >= 0 ? ty * kSpTX + (31 - __clz(starts)) : -1;
+    __syncthreads();
+    if (dv >= 0 && ty + 1 < kSpTY && sp_linked(dv, sD[t + kSpTX], a.thr)) {
+        const bool redundant = left && sp_linked(sD[t - 1], sD[t - 1 + kSpTX], a.thr) &&
+                               sp_linked(sD[t - 1 + kSpTX], sD[t + kSpTX], a.thr);
+        if (!redundant) sp_unite_shared(sL, t, t + kSpTX, a.status);
+    }
+    __syncthreads();
+    int r = -1;
     if (dv >= 0) {
-        if (tx + 1 < kSpTX && sp_linked(dv, sD[t + 1], a.thr)) sp_unite_shared(sL, t, t + 1, a.status);
-        if (ty + 1 < kSpTY && sp_linked(dv, sD[t + kSpTX], a.thr)) sp_unite_shared(sL, t, t + kSpTX, a.status);
+        r = sp_find_shared(sL, t);
+        if (r < 0) {
+            atomicExch(a.status, 1);
+            r = t;
+        }
+        atomicAdd(sC + r, 1);
     }
     __syncthreads();
     if (in) {
-        int lab = -1;
-        if (dv >= 0) {
-            const int r = sp_find_shared(sL, t);
-            // the tile-local root's global index: local order is raster order
-            // inside the tile, so the label is still <= i
-            lab = r < 0 ? (int)i : (y0 + r / kSpTX) * a.w + (x0 + r % kSpTX);
-            if (r < 0) atomicExch(a.status, 1);
-        }
-        a.label[i] = lab;
+        // the tile-local root's global index: local order is raster order
+        // inside the tile, so the label is still <= i
+        a.label[i] = r < 0 ? -1 : (y0 + r / kSpTX) * a.w + (x0 + r % kSpTX);
+        a.size[i] = sC[t];  // the tile-local count at a tile-local root, else 0
     }
 }
 
+// Links across tile edges: first every right edge (x = 32k + 31, k =
+// 0..ntx-2) of every row, then every bottom edge (y = 16k + 15) of every
+// column.  A right-edge link is skipped where the link above it and the two
+// vertical links beside it connect the same pixels and those vertical links
+// lie inside a tile (not on a tile's first row); a bottom-edge link likewise
+// with the link to its left and horizontal links inside a tile.  Each skip
+// rests on a link one row up or one column left, so the chain ends at a
+// processed link and no component loses a connection.
 __global__ void __launch_bounds__(256) speckle_border_kernel(SpeckleArgs a) {
+    const int ntx = (a.w + kSpTX - 1) / kSpTX, nty = (a.h + kSpTY - 1) / kSpTY;
+    const int nr = (ntx - 1) * a.h, nb = (nty - 1) * a.w;
+    const int n = a.w * a.h, w = a.w, thr = a.thr;
+    const int16_t *d = a.d;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr + nb; k += gridDim.x * blockDim.x) {
+        int i, j;
+        bool redundant;
+        if (k < nr) {
+            const int y = k / (ntx - 1), e = k - y * (ntx - 1);
+            i = y * w + e * kSpTX + kSpTX - 1;
+            j = i + 1;
+            if (!sp_linked(d[i], d[j], thr)) continue;
+            redundant = (y % kSpTY) != 0 && sp_linked(d[i - w], d[j - w], thr) && sp_linked(d[i - w], d[i], thr) &&
+                        sp_linked(d[j - w], d[j], thr);
+        } else {
+            const int kb = k - nr, e = kb / w, x = kb - e * w;
+            i = (e * kSpTY + kSpTY - 1) * w + x;
+            j = i + w;
+            if (!sp_linked(d[i], d[j], thr)) continue;
+            redundant = (x % kSpTX) != 0 && sp_linked(d[i - 1], d[j - 1], thr) && sp_linked(d[i - 1], d[i], thr) &&
+                        sp_linked(d[j - 1], d[j], thr);
+        }
+        if (!redundant) sp_unite_global(a.label, i, j, n, a.status);
+    }
+}
+
+__global__ void __launch_bounds__(256) speckle_resolve_kernel(SpeckleArgs a) {
     const int n = a.w * a.h;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int y = i / a.w, x = i - y * a.w;
-        const bool right = (x % kSpTX) == kSpTX - 1 && x + 1 < a.w;
-        const bool down = (y % kSpTY) == kSpTY - 1 && y + 1 < a.h;
-        if (!right && !down) continue;
-        const int dv = a.d[i];
-        if (dv < 0) continue;
-        if (right && sp_linked(dv, a.d[i + 1], a.thr)) sp_unite_global(a.label, i, i + 1, n, a.status);
-        if (down && sp_linked(dv, a.d[i + a.w], a.thr)) sp_unite_global(a.label, i, i + a.w, n, a.status);
-    }
-}
-
-__global__ void __launch_bounds__(256) speckle_count_kernel(SpeckleArgs a) {
-    const int n = a.w * a.h;
-    const int lane = threadIdx.x & 31;
-    // whole warps iterate together so that the match below sees every lane
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int i = base + threadIdx.x;
-        int root = -1;
-        if (i < n && __ldcg(a.label + i) >= 0) {
-            root = sp_find_global(a.label, i, n);
-            if (root < 0) atomicExch(a.status, 1);
-            else a.label[i] = root;  // an ancestor: the forest stays valid
+        // tile-local roots hold their tile count (>= 1); adds only go to
+        // final roots, which are tile-local roots too, so the test is stable
+        const int c = __ldcg(a.size + i);
+        if (c <= 0) continue;
+        const int root = sp_find_readonly(a.label, i, n);
+        if (root < 0) {
+            atomicExch(a.status, 1);
+            continue;
         }
-        const unsigned same = __match_any_sync(0xFFFFFFFFu, root);
-        if (root >= 0 && lane == __ffs(same) - 1) atomicAdd(a.size + root, __popc(same));
+        if (root != i) {
+            __stcg(a.label + i, root);  // an ancestor: the forest stays valid
+            atomicAdd(a.size + root, c);
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) speckle_apply_kernel(SpeckleArgs a) {
     const int n = a.w * a.h;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int lab = a.label[i];
+        const int r = a.label[i];
         const int16_t dv = a.d[i];
-        a.out[i] = (lab >= 0 && a.size[lab] >= a.min_size) ? dv : (int16_t)-1;
+        bool keep = false;
+        if (r >= 0) {
+            const int root = a.label[r];  // r's final root (r itself if it is one)
+            keep = a.size[root] >= a.min_size;
+        }
+        a.out[i] = keep ? dv : (int16_t)-1;
     }
 }
 
@@ -192,8 +260,8 @@ elas_status launch_speckle(const int16_t *d, int w, int h, int thr, int min_size
     if (blocks > 152 * 8) blocks = 152 * 8;
     speckle_border_kernel<<<blocks, 256, 0, st>>>(a);
     if ((s = launch_status("speckle_border_kernel")) != ELAS_OK) return s;
-    speckle_count_kernel<<<blocks, 256, 0, st>>>(a);
-    if ((s = launch_status("speckle_count_kernel")) != ELAS_OK) return s;
+    speckle_resolve_kernel<<<blocks, 256, 0, st>>>(a);
+    if ((s = launch_status("speckle_resolve_kernel")) != ELAS_OK) return s;
     speckle_apply_kernel<<<blocks, 256, 0, st>>>(a);
     return launch_status("speckle_apply_kernel");
 }
