@@ -48,6 +48,7 @@ void oracle_params_default(oracle_params *p)
     p->flags = 0;
     p->census_support_w = 0;
     p->census_dense_w = 0;
+    p->support_downsample = 0;
 }
 
 static int iabs(int x) { return x < 0 ? -x : x; }
@@ -331,6 +332,15 @@ void oracle_support_points(const uint8_t *descL, const uint8_t *descR, int w, in
         memcpy(dcan, con, sizeof(int16_t) * nc);
     else
         oracle_filter_redundancy(con, wc, hc, p, dcan);
+    if (p->support_downsample > 1) {
+        /* keep the surviving points numbered 0, k, 2k, ... in raster order */
+        size_t rank = 0;
+        for (size_t i = 0; i < nc; i++) {
+            if (dcan[i] < 0) continue;
+            if (rank % (size_t)p->support_downsample != 0) dcan[i] = -1;
+            rank++;
+        }
+    }
     free(raw);
     free(con);
 }

@@ -55,6 +55,12 @@ typedef struct {
      * census descriptors; both 0 = Sobel descriptors with SAD (Sec. III.A),
      * else both odd, 3 <= census_support_w <= 15, 3 <= census_dense_w <= 11. */
     int32_t census_support_w, census_dense_w;
+    /* Support down-sampling (Sec. VII, the 1/8, 1/14, 1/32 of the extracted
+     * support points the paper sweeps): 0 or 1 keeps every point; k >= 2
+     * keeps the points numbered 0, k, 2k, ... in raster order of the
+     * filtered candidate grid (the others become -1), so the list, the grid
+     * vectors and the triangulation see 1/k of them. */
+    int32_t support_downsample;
 } oracle_params;
 
 void oracle_params_default(oracle_params *p);
@@ -89,7 +95,8 @@ void oracle_filter_consistency(const int16_t *in, int wc, int hc,
                                const oracle_params *p, int16_t *out);
 void oracle_filter_redundancy(const int16_t *in, int wc, int hc,
                               const oracle_params *p, int16_t *out);
-/* Whole support step: match, consistency, redundancy (unless disabled). */
+/* Whole support step: match, consistency, redundancy (unless disabled), then
+ * the down-sampling of support_downsample. */
 void oracle_support_points(const uint8_t *descL, const uint8_t *descR, int w, int h,
                            const oracle_params *p, int16_t *dcan);
 /* Raster-order compaction of the candidate grid; returns the count. */

@@ -233,3 +233,27 @@ def test_support_list_raster_order(orc):
     g = _grid(4, 5, {(0, 3): 7, (1, 0): 2, (1, 4): 9, (3, 2): 0})
     lst = orc.support_list(g, dict(candidate_stepsize=5))
     np.testing.assert_array_equal(lst, [[15, 0, 7], [0, 5, 2], [20, 5, 9], [10, 15, 0]])
+
+
+@pytest.mark.parametrize("k", [2, 3, 8, 14, 32])
+def test_support_downsampling(orc, k):
+    """The paper's down-sampling of the extracted support points (Sec. VII):
+    the points numbered 0, k, 2k, ... in raster order stay.  The down-sampled
+    list is every k-th entry of the full one, its length ceil(n / k), the
+    candidate grid keeps exactly those points, and the grid vectors of the
+    smaller list are a subset of the full ones."""
+    wl = synth.SMALL_320
+    L, R, _ = synth.workload_pair(wl, 0, 1)
+    dL, dR = orc.descriptors(L), orc.descriptors(R)
+    full = orc.support_points(dL, dR, wl.params)
+    prm = dict(wl.params, support_downsample=k)
+    down = orc.support_points(dL, dR, prm)
+    lf, ld = orc.support_list(full, wl.params), orc.support_list(down, prm)
+    assert len(ld) == -(-len(lf) // k) and len(lf) > 10 * k
+    np.testing.assert_array_equal(ld, lf[::k])
+    assert ((down == full) | (down == -1)).all() and int((down >= 0).sum()) == len(ld)
+    h, w = L.shape
+    gf, gd = orc.grid_vectors(lf, w, h, prm), orc.grid_vectors(ld, w, h, prm)
+    assert ((gd & ~gf) == 0).all() and (gd != gf).any()
+    for k0 in (0, 1):
+        np.testing.assert_array_equal(orc.support_points(dL, dR, dict(wl.params, support_downsample=k0)), full)
