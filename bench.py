@@ -508,6 +508,22 @@ def run_accuracy_section(B, torch, dev, npairs=4, steps=(5, 7, 10, 14)):
             var[key] = {"support_points": float(np.mean(nsup)),
                         **{k: float(np.mean([a_[k] for a_ in acc])) for k in acc[0]}}
         rows["step_5_variants"] = var
+        # the paper's down-sampling (Sec. VII): support extracted at every
+        # pixel, then 1/k of the filtered points kept
+        down = {}
+        for k in (8, 14, 32):
+            prm = dict(wl.params, candidate_stepsize=1, support_downsample=k)
+            pl = B.Pipeline(w, h, prm)
+            dL = torch.empty((h, w), dtype=torch.int16, device=dev)
+            acc, nsup = [], []
+            for L, R, gt in pairs:
+                pl.run(torch.from_numpy(L).to(dev), torch.from_numpy(R).to(dev), dL)
+                acc.append(kitti_outliers(dL.cpu().numpy(), gt))
+                nsup.append(pl.stats()["n_support"])
+            pl.close()
+            down["1_of_%d" % k] = {"support_points": float(np.mean(nsup)),
+                                   **{k_: float(np.mean([a_[k_] for a_ in acc])) for k_ in acc[0]}}
+        rows["every_pixel_downsampled"] = down
         out[wl.name] = rows
     # the median kernel alone on a 1242x375 map (inputs resident; radius 1
     # and 2), against the measured copy bandwidth at its minimum bytes

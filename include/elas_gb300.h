@@ -109,6 +109,13 @@ typedef struct {
      * (window census_dense_w) and costs by Hamming distance too; neither
      * applies a texture test (support_texture and match_texture unused). */
     int32_t census_support_w, census_dense_w;
+    /* Support down-sampling (Sec. VII sweeps 1/8, 1/14, 1/32 of the extracted
+     * support points): 0 or 1 keeps every point; k >= 2 keeps the filtered
+     * points numbered 0, k, 2k, ... in raster order of the candidate grid
+     * (d_can shows -1 for the others), and the list, its count, the grid
+     * vectors and so the triangulation and the dense prior see only those.
+     * Per-pair calls and the pipeline; batches and the server refuse k >= 2. */
+    int32_t support_downsample;
 } elas_params;
 
 /* A cudaStream_t passed through the C ABI. */
@@ -185,6 +192,10 @@ elas_status elas_census(const uint8_t *imgL, const uint8_t *imgR, int32_t w, int
  * window of (u,v) is the record of (u,v) itself, cost(d) is the Hamming
  * distance of the two records, and no texture test applies; everything else
  * (bounds, search ranges, tests, filters) is unchanged.
+ * With support_downsample k >= 2 in p, the filtered points numbered 0, k,
+ * 2k, ... in raster order are kept: d_can holds -1 for the others, the list
+ * holds the kept points in order, *count = ceil(n / k) for n filtered points,
+ * and the grid vectors are those of the kept points (one more launch).
  */
 size_t elas_support_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
 elas_status elas_support_points(const uint8_t *descL, const uint8_t *descR, int32_t w, int32_t h,
@@ -429,9 +440,10 @@ void elas_pipeline_destroy(elas_pipeline *pl);
  * and the triangulation's CTA pass takes its work from one queue over all
  * pairs.  With use_graph the launch sequence is captured once into a CUDA
  * graph and replayed.  Results are identical to the per-pair path.
- * Batches and the server take Sobel descriptors only: parameters with
- * census windows return ELAS_ERR_INVALID_ARG there (the census variant runs
- * through the per-pair calls and the pipeline).
+ * Batches and the server take Sobel descriptors only and no support
+ * down-sampling: parameters with census windows or support_downsample >= 2
+ * return ELAS_ERR_INVALID_ARG there (those variants run through the per-pair
+ * calls and the pipeline).
  *
  * elas_batch_create: n pairs (1 <= n <= 256), pair i of w[i] x h[i] with
  *   params[i] (w, h >= candidate_stepsize).  Allocates every slot.

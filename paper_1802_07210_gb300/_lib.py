@@ -43,6 +43,7 @@ class Params(C.Structure):
         ("ipol_gap_width", C.c_int32), ("filter_adaptive_mean", C.c_int32),
         ("test_flags", C.c_uint32),
         ("census_support_w", C.c_int32), ("census_dense_w", C.c_int32),
+        ("support_downsample", C.c_int32),
     ]
 
 

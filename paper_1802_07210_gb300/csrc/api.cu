@@ -46,6 +46,7 @@ elas_status check_params(const elas_params *p, int32_t w, int32_t h) {
         return fail(ELAS_ERR_INVALID_ARG, "negative window parameter");
     if (!(p->beta > 0.0f) || !(p->gamma > 0.0f) || !(p->sigma > 0.0f))
         return fail(ELAS_ERR_INVALID_ARG, "beta, gamma, sigma must be > 0");
+    if (p->support_downsample < 0) return fail(ELAS_ERR_INVALID_ARG, "support_downsample %d < 0", p->support_downsample);
     const int cs = p->census_support_w, cd = p->census_dense_w;
     if (cs != 0 || cd != 0) {
         if (cs < 3 || cs > 15 || cs % 2 == 0 || cd < 3 || cd > 11 || cd % 2 == 0)
@@ -92,6 +93,7 @@ elas_status elas_params_default(elas_params *p) {
     p->test_flags = 0;
     p->census_support_w = 0;
     p->census_dense_w = 0;
+    p->support_downsample = 0;
     return ELAS_OK;
 }
 

@@ -122,8 +122,9 @@ elas_status SlotPool::wait_mirror() {
 elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStream_t alloc_stream) {
     elas_status s = check_params(p, w, h);
     if (s != ELAS_OK) return s;
-    if (p->census_support_w != 0)
-        return fail(ELAS_ERR_INVALID_ARG, "the census variant runs through the per-pair calls and the pipeline only");
+    if (p->census_support_w != 0 || p->support_downsample > 1)
+        return fail(ELAS_ERR_INVALID_ARG,
+                    "the census variant and support down-sampling run through the per-pair calls and the pipeline only");
     if (w < p->candidate_stepsize || h < p->candidate_stepsize)
         return fail(ELAS_ERR_INVALID_ARG, "%dx%d has no lattice candidate at step %d", w, h, p->candidate_stepsize);
     int k = -1;

@@ -49,14 +49,25 @@ struct RedArgs {
     int16_t *dcan;
     uint32_t *gridL, *gridR;
     int32_t *rowcount;
+    int defer_grid;  // down-sampling: the grid vectors come from the list instead
 };
 
 struct CompactArgs {
-    const int16_t *dcan;
+    int16_t *dcan;  // down-sampling clears the points it drops
     int wc, hc, step;
     const int32_t *rowcount;
     int16_t *list;
     int32_t *count;
+    int keep_every;  // support down-sampling k (<= 1: every point)
+};
+
+// Grid vectors of a down-sampled support list.
+struct ListGridArgs {
+    const int16_t *list;
+    const int32_t *count;
+    int cap;
+    GridArgs g;
+    uint32_t *gridL, *gridR;
 };
 
 // The four launches of the support stage for one pair, and their tables.

@@ -421,8 +421,8 @@ __device__ __forceinline__ void redundancy_grid_body(const RedArgs &ra, const VB
             if (redundant) res = -1;
         }
         ra.dcan[(size_t)ic * wc + jc] = (int16_t)res;
-        if (res >= 0) {
-            ++mine;
+        if (res >= 0) ++mine;
+        if (res >= 0 && !ra.defer_grid) {
             const int u = jc * g.step;
             for (int side = 0; side < 2; ++side) {
                 uint32_t *grid = side ? ra.gridR : ra.gridL;
@@ -488,17 +488,45 @@ __device__ __forceinline__ void compact_rows_body(const CompactArgs &ca, const V
         int off = base + __popc(bal & ((1u << lane) - 1u));
         for (int k = 0; k < warp; ++k) off += s_w[k];
         if (d >= 0) {
-            list[3 * off + 0] = (int16_t)(jc * step);
-            list[3 * off + 1] = (int16_t)(ic * step);
-            list[3 * off + 2] = (int16_t)d;
+            // down-sampling keeps the points numbered 0, k, 2k, ... (raster order)
+            const int ke = ca.keep_every;
+            if (ke <= 1 || off % ke == 0) {
+                const int o = ke > 1 ? off / ke : off;
+                list[3 * o + 0] = (int16_t)(jc * step);
+                list[3 * o + 1] = (int16_t)(ic * step);
+                list[3 * o + 2] = (int16_t)d;
+            } else {
+                ca.dcan[ic * wc + jc] = -1;
+            }
         }
         base += s_w[0] + s_w[1] + s_w[2] + s_w[3];
         __syncthreads();
     }
-    if (ic == hc - 1 && tid == 0) *ca.count = base;
+    if (ic == hc - 1 && tid == 0) *ca.count = ca.keep_every > 1 ? (base + ca.keep_every - 1) / ca.keep_every : base;
 }
 
 __global__ void __launch_bounds__(128) compact_rows_kernel(CompactArgs ca) { compact_rows_body(ca, vb_single()); }
+
+// Grid vectors of a down-sampled list (the masks were cleared by the
+// consistency kernel): each point ORs its {d-1, d, d+1} bits into the 3x3
+// cells around its cell, as the redundancy kernel does for every point
+// without down-sampling.
+__global__ void __launch_bounds__(128) list_grid_kernel(ListGridArgs a) {
+    const int n = min(*a.count, a.cap);
+    const GridArgs g = a.g;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int u = a.list[3 * k], v = a.list[3 * k + 1], d = a.list[3 * k + 2];
+        const int cy = v / g.G;
+        for (int side = 0; side < 2; ++side) {
+            uint32_t *grid = side ? a.gridR : a.gridL;
+            if (!grid) continue;
+            const int cx = (side ? u - d : u) / g.G;
+            for (int y = max(0, cy - 1); y <= min(g.gh - 1, cy + 1); ++y)
+                for (int x = max(0, cx - 1); x <= min(g.gw - 1, cx + 1); ++x)
+                    or_bits(grid + ((size_t)y * g.gw + x) * g.nw, d, g.dmin, g.dmax);
+        }
+    }
+}
 __global__ void __launch_bounds__(128) compact_rows_kernel_b(const CompactArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     compact_rows_body(slot_entry(tab, vm.stride, vb.slot), vb);
@@ -542,8 +570,8 @@ elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int 
     o->red = RedArgs{con, a.wc, a.hc, p->redun_max_dist, (p->test_flags & ELAS_FLAG_REDUNDANCY_OFF) ? 0 : 1,
                      (p->test_flags & ELAS_FLAG_PAST_REDUNDANCY) ? 1 : 0,
                      GridArgs{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax}, d_can, grid_L, grid_R,
-                     rowcount};
-    o->compact = CompactArgs{d_can, a.wc, a.hc, a.step, rowcount, list, count};
+                     rowcount, p->support_downsample > 1 ? 1 : 0};
+    o->compact = CompactArgs{d_can, a.wc, a.hc, a.step, rowcount, list, count, p->support_downsample};
     return ELAS_OK;
 }
 
@@ -634,7 +662,14 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     redundancy_grid_kernel<<<lattice_row_grid(sa.red.hc), 128, red_smem, st>>>(sa.red, red_staged);
     if ((s = launch_status("redundancy_grid_kernel")) != ELAS_OK) return s;
     compact_rows_kernel<<<lattice_row_grid(sa.compact.hc), 128, 0, st>>>(sa.compact);
-    return launch_status("compact_rows_kernel");
+    if ((s = launch_status("compact_rows_kernel")) != ELAS_OK) return s;
+    if (sa.compact.keep_every <= 1) return ELAS_OK;
+    const int k = sa.compact.keep_every;
+    const ListGridArgs lg{list, count, (nc + k - 1) / k, sa.red.g, grid_L, grid_R};
+    int blocks = (lg.cap + 127) / 128;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    list_grid_kernel<<<blocks, 128, 0, st>>>(lg);
+    return launch_status("list_grid_kernel");
 }
 
 // Batched support stage: every pair of the launch must have at least one

@@ -72,6 +72,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     for cs, cd in ((9, 0), (0, 5), (8, 5), (9, 13), (17, 5), (1, 1)):
         bad = _lib.params(census_support_w=cs, census_dense_w=cd)
         assert L.elas_support_workspace_bytes(64, 64, C.byref(bad)) == 0, (cs, cd)
+    assert L.elas_support_workspace_bytes(64, 64, C.byref(_lib.params(support_downsample=-1))) == 0
+    assert L.elas_support_workspace_bytes(64, 64, C.byref(_lib.params(support_downsample=14))) > 0
     good = _lib.params(census_support_w=15, census_dense_w=11)
     assert L.elas_support_workspace_bytes(64, 64, C.byref(good)) > 0
 
