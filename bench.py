@@ -832,12 +832,22 @@ def main():
 
     extra = {}
     if rank == 0 and not args.skip_extra:
-        extra["batch"] = run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
-                                           args.batch_pairs, args.batch_distinct, peak, tune=not args.no_tune)
-        extra["mixed_batch"] = run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
-                                                 args.mixed_pairs, tune=not args.no_tune)
-        extra["serving"] = run_serve_section(B, torch, args.serve_seconds)
-        extra["accuracy"] = run_accuracy_section(B, torch, dev)
+        # each section reports on its own: an error in one is recorded in its
+        # object and leaves the headline and the other sections standing
+        sections = (
+            ("batch", lambda: run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
+                                                args.batch_pairs, args.batch_distinct, peak,
+                                                tune=not args.no_tune)),
+            ("mixed_batch", lambda: run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
+                                                      args.mixed_pairs, tune=not args.no_tune)),
+            ("serving", lambda: run_serve_section(B, torch, args.serve_seconds)),
+            ("accuracy", lambda: run_accuracy_section(B, torch, dev)),
+        )
+        for key, fn in sections:
+            try:
+                extra[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                extra[key] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
