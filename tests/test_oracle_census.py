@@ -189,3 +189,19 @@ def test_pipeline_is_blind_to_an_intensity_change_of_one_image(orc):
     sad = orc.support_points(orc.descriptors(L), orc.descriptors(R2), wl.params)
     sad0 = orc.support_points(orc.descriptors(L), orc.descriptors(R), wl.params)
     assert not np.array_equal(sad, sad0)
+
+
+def test_degenerate_images(orc):
+    """A 1x1 image clamps every neighbour onto the centre: no bits.  A single
+    row clamps every dy onto it, so each window row repeats the 1-D census of
+    the row (bits for dy equal the bits for dy = 0)."""
+    assert not orc.census(np.array([[200]], np.uint8), 15, 32).any()
+    row = np.array([[5, 9, 1, 7, 3, 8, 2]], np.uint8)
+    for W in (3, 5, 7):
+        c = orc.census(row, W, 16)
+        for u in range(row.shape[1]):
+            b = np.unpackbits(c[0, u], bitorder="little")[:W * W].reshape(W, W)
+            assert (b == b[W // 2]).all()
+            r = W // 2
+            exp = [int(row[0, min(max(u + dx, 0), row.shape[1] - 1)] < row[0, u]) for dx in range(-r, r + 1)]
+            assert list(b[W // 2]) == exp

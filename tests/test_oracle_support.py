@@ -257,3 +257,13 @@ def test_support_downsampling(orc, k):
     assert ((gd & ~gf) == 0).all() and (gd != gf).any()
     for k0 in (0, 1):
         np.testing.assert_array_equal(orc.support_points(dL, dR, dict(wl.params, support_downsample=k0)), full)
+
+
+def test_downsampling_of_an_empty_support_set(orc):
+    """A textureless pair has no support point: down-sampling keeps none and
+    the list is empty for every k."""
+    img = np.full((60, 80), 90, np.uint8)
+    d = orc.descriptors(img)
+    for k in (1, 2, 14):
+        prm = dict(disp_max=31, support_downsample=k)
+        assert len(orc.support_list(orc.support_points(d, d, prm), prm)) == 0
