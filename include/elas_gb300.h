@@ -19,6 +19,12 @@
  *   elas_median           median filter of valid disparities (Sec. VII)
  *   elas_speckle          small-segment removal (ELAS post-processing)
  *
+ * The paper's own variant (Sec. VI) as parameters: elas_census records with
+ * Hamming costs in place of the descriptors and SAD (census_support_w,
+ * census_dense_w), the shift-sum ambiguity test of Eq. 3 and the past-only
+ * redundancy rule (ELAS_FLAG_SHIFT_SUM, ELAS_FLAG_PAST_REDUNDANCY), and the
+ * support down-sampling of Sec. VII (support_downsample).
+ *
  * Conventions shared by every call
  *   - All device pointers are owned by the caller.  Calls never allocate
  *     device memory: scratch comes from a caller-provided workspace whose
@@ -31,7 +37,7 @@
  *   - No call aborts, traps or prints.  elas_last_error() returns a
  *     thread-local text for the last non-OK status of the calling thread.
  *   - Layouts: image uint8 [h][pitch]; descriptors uint8 [h][w][16] (16-byte
- *     aligned); candidate grid int16 [h/step][w/step] with candidate (jc,ic)
+ *     aligned; census records [h][w][32] or [h][w][16]); candidate grid int16 [h/step][w/step] with candidate (jc,ic)
  *     at pixel (jc*step, ic*step), -1 = none; support list int16 triples
  *     (u, v, d) in raster order of the candidate grid; grid vectors uint32
  *     [ceil(h/G)][ceil(w/G)][ceil((disp_max+1)/32)], bit d set = candidate d;
