@@ -67,7 +67,9 @@ typedef enum {
     ELAS_ERR_INTERNAL = 6     /* internal invariant broken                    */
 } elas_status;
 
-/* Test-only switches in elas_params.test_flags. */
+/* Switches in elas_params.test_flags: PRIOR_OFF, FULL_RANGE and
+ * REDUNDANCY_OFF are test modes; SHIFT_SUM and PAST_REDUNDANCY select the
+ * paper's variant rules (Sec. VI.B, VI.C). */
 #define ELAS_FLAG_PRIOR_OFF      1u /* dense: prior term forced to 0                  */
 #define ELAS_FLAG_FULL_RANGE     2u /* dense: every in-range d is a candidate and no
                                        plane is required                             */
@@ -104,7 +106,7 @@ typedef struct {
     int32_t lr_threshold;        /* left-right tolerance (support and dense)        */
     int32_t ipol_gap_width;      /* max gap length filled by interpolation (0=off)  */
     int32_t filter_adaptive_mean;/* 1 = adaptive mean after interpolation           */
-    uint32_t test_flags;         /* ELAS_FLAG_* (tests only)                        */
+    uint32_t test_flags;         /* ELAS_FLAG_* (test modes, variant rules)         */
     /* The census variant of Sec. VI.A: census windows of the support and the
      * dense stage.  Both 0 (default): Sobel descriptors with SAD costs.
      * Otherwise both odd, 3 <= census_support_w <= 15, 3 <= census_dense_w
