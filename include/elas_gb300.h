@@ -129,6 +129,13 @@ typedef struct {
 /* A cudaStream_t passed through the C ABI. */
 typedef void *elas_stream;
 
+/* One workspace size for every per-pair call that takes a workspace
+ * (support points, device triangulation of one side, plane prior, dense
+ * match, post-processing, speckle removal) when they run one after another
+ * on the same buffer: the largest of their *_workspace_bytes at this size.
+ * 0 if p is invalid for w x h.  Host only. */
+size_t elas_workspace_bytes(int32_t w, int32_t h, const elas_params *p);
+
 /* Fills `p` with the default parameter set listed above.  Host only. */
 elas_status elas_params_default(elas_params *p);
 

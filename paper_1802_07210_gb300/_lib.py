@@ -101,6 +101,7 @@ SIGNATURES = {
     "elas_postprocess": (C.c_int, [_P, _I, _I, _P, _P, _P, _Z, _P]),
     "elas_median": (C.c_int, [_P, _I, _I, _I, _P, _P]),
     "elas_speckle_workspace_bytes": (C.c_size_t, [_I, _I]),
+    "elas_workspace_bytes": (C.c_size_t, [_I, _I, _P]),
     "elas_speckle": (C.c_int, [_P, _I, _I, _I, _I, _P, _P, C.c_size_t, _P]),
     "elas_pipeline_create": (C.c_int, [_I, _I, _P, _P]),
     "elas_pipeline_run": (C.c_int, [_P, _P, _P, _I, _P, _P, _P, _P]),

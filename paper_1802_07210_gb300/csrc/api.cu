@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -68,6 +69,23 @@ void prior_table(const elas_params *p, int32_t *P) {
 }  // namespace elas
 
 extern "C" {
+
+// One workspace for the per-pair calls made one after another: the largest
+// of their own requirements at this size (the device triangulation of one
+// side with the full candidate count, the plane prior with the triangle
+// bound of one mesh).
+size_t elas_workspace_bytes(int32_t w, int32_t h, const elas_params *p) {
+    if (elas::check_params(p, w, h) != ELAS_OK) return 0;
+    const int32_t step = p->candidate_stepsize;
+    const int32_t cap = (w / step) * (h / step);
+    size_t m = elas_support_workspace_bytes(w, h, p);
+    m = std::max(m, elas_triangulate_device_workspace_bytes(cap > 0 ? cap : 1, w, h));
+    m = std::max(m, elas_plane_prior_workspace_bytes(2 * cap + 8));
+    m = std::max(m, elas_dense_workspace_bytes(w, h, p));
+    m = std::max(m, elas_postprocess_workspace_bytes(w, h));
+    m = std::max(m, elas_speckle_workspace_bytes(w, h));
+    return m;
+}
 
 elas_status elas_params_default(elas_params *p) {
     if (!p) return elas::fail(ELAS_ERR_INVALID_ARG, "params is NULL");

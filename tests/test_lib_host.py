@@ -152,3 +152,22 @@ def test_triangulation_capacity_error():
     nt = C.c_int32(0)
     st = _lib.lib().elas_triangulate(_lib.np_ptr(lst), 4, 0, _lib.np_ptr(tri), 1, C.byref(nt))
     assert st == 3 and nt.value == 2
+
+
+def test_one_workspace_for_every_call():
+    """elas_workspace_bytes is the largest per-call requirement at the size
+    (host arithmetic only), and 0 for invalid parameters."""
+    L = _lib.lib()
+    for w, h, kw in ((640, 480, {}), (1242, 375, {}), (8, 8, {}), (203, 117, dict(candidate_stepsize=3)),
+                     (320, 240, dict(census_support_w=9, census_dense_w=5, support_downsample=8))):
+        p = _lib.params(**kw)
+        step = p.candidate_stepsize
+        cap = (w // step) * (h // step)
+        parts = [L.elas_support_workspace_bytes(w, h, C.byref(p)),
+                 L.elas_triangulate_device_workspace_bytes(max(cap, 1), w, h),
+                 L.elas_plane_prior_workspace_bytes(2 * cap + 8),
+                 L.elas_dense_workspace_bytes(w, h, C.byref(p)),
+                 L.elas_postprocess_workspace_bytes(w, h),
+                 L.elas_speckle_workspace_bytes(w, h)]
+        assert L.elas_workspace_bytes(w, h, C.byref(p)) == max(parts) > 0
+    assert L.elas_workspace_bytes(64, 64, C.byref(_lib.params(disp_max=-3))) == 0
