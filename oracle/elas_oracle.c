@@ -395,8 +395,14 @@ void oracle_grid_vectors(const int16_t *list, int n, int w, int h,
  * Cocircular ties are broken by perturbing the lifted heights
  * |p_i|^2 + eps_i with eps_0 >> eps_1 >> ... (the lowest index dominates), so
  * the triangulation is the unique one of the perturbed point set, whatever
- * algorithm builds it.  Every insertion scans all triangles for conflicts:
- * O(n^2), deliberately plain. */
+ * algorithm builds it.  Every insertion scans all live triangles for
+ * conflicts.  A finite triangle whose circumcircle lies wholly above the
+ * lowest row any point still to come can occupy (every such point strictly
+ * outside it, so no perturbation is ever consulted) can never be destroyed
+ * again; it is set aside as final before the scan.  With the support list's
+ * raster order this keeps the scanned set to the triangles near the current
+ * row, and it changes no triangle: only triangles that could not conflict
+ * are skipped. */
 
 #define OINF (-1)
 
@@ -461,6 +467,27 @@ static int in_conflict(const int32_t *x, const int32_t *y, const int *t, int q)
     return incircle_sos(x, y, t[0], t[1], t[2], q) > 0;
 }
 
+/* Is every point (x, y) with y >= ymin strictly outside the circumcircle
+ * of the counter-clockwise finite triangle t?  With b', c' the vertices
+ * relative to a, O = orient(a, b, c) > 0 and D = 2 O, the centre is
+ * a + (Nx, Ny) / D with Nx = c'y |b'|^2 - b'y |c'|^2,
+ * Ny = b'x |c'|^2 - c'x |b'|^2, and the radius is sqrt(Nx^2 + Ny^2) / D, so
+ * the circle's lowest point lies above row ymin iff M = (ymin - ay) D - Ny > 0
+ * and Nx^2 + Ny^2 < M^2 (exact in 128-bit integers for 16-bit coordinates). */
+static int circle_above(const int32_t *x, const int32_t *y, const int *t, int64_t ymin)
+{
+    int64_t ax = x[t[0]], ay = y[t[0]];
+    int64_t bx = x[t[1]] - ax, by = y[t[1]] - ay, cx = x[t[2]] - ax, cy = y[t[2]] - ay;
+    int64_t O = bx * cy - by * cx;
+    if (O <= 0) return 0;
+    int64_t b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    __int128 Nx = (__int128)cy * b2 - (__int128)by * c2;
+    __int128 Ny = (__int128)bx * c2 - (__int128)cx * b2;
+    __int128 M = (__int128)(ymin - ay) * (2 * O) - Ny;
+    if (M <= 0) return 0;
+    return Nx * Nx + Ny * Ny < M * M;
+}
+
 static void put_tri(int *T, int k, int a, int b, int c)
 {
     /* keep the infinite vertex (if any) in the last slot, rotation preserved */
@@ -489,11 +516,33 @@ int oracle_delaunay(const int32_t *x, const int32_t *y, int n, int32_t *tri, int
     char *inserted = (char *)calloc((size_t)n, 1);
     char *dead = (char *)malloc((size_t)maxT);
     int *edges = (int *)malloc(sizeof(int) * 2 * 3 * (size_t)maxT);
+    int *F = (int *)malloc(sizeof(int) * 3 * (size_t)maxT); /* final (set-aside) triangles */
+    int nf = 0;
+    /* ylow[q] = lowest y among the points at positions q..n-1 */
+    int32_t *ylow = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    ylow[n - 1] = y[n - 1];
+    for (int k = n - 2; k >= 0; k--) ylow[k] = y[k] < ylow[k + 1] ? y[k] : ylow[k + 1];
     inserted[a] = inserted[b] = inserted[c] = 1;
 
+    int64_t swept = INT64_MIN;
     for (int q = 0; q < n; q++) {
         if (inserted[q]) continue;
         inserted[q] = 1;
+        if (ylow[q] > swept) {
+            /* set aside the triangles no remaining point can destroy */
+            swept = ylow[q];
+            int w = 0;
+            for (int k = 0; k < nt; k++) {
+                if (T[3 * k + 2] != OINF && circle_above(x, y, &T[3 * k], swept)) {
+                    F[3 * nf] = T[3 * k]; F[3 * nf + 1] = T[3 * k + 1]; F[3 * nf + 2] = T[3 * k + 2];
+                    nf++;
+                    continue;
+                }
+                if (w != k) { T[3 * w] = T[3 * k]; T[3 * w + 1] = T[3 * k + 1]; T[3 * w + 2] = T[3 * k + 2]; }
+                w++;
+            }
+            nt = w;
+        }
         for (int k = 0; k < nt; k++) dead[k] = (char)in_conflict(x, y, &T[3 * k], q);
         /* cavity boundary: directed edges of dead triangles whose reverse is
          * not an edge of another dead triangle */
@@ -523,13 +572,18 @@ int oracle_delaunay(const int32_t *x, const int32_t *y, int n, int32_t *tri, int
     }
 
     int out = 0;
-    for (int k = 0; k < nt; k++) {
+    for (int k = 0; k < nf && out >= 0; k++) {
+        if (out >= cap) { out = -1; break; }
+        tri[3 * out] = F[3 * k]; tri[3 * out + 1] = F[3 * k + 1]; tri[3 * out + 2] = F[3 * k + 2];
+        out++;
+    }
+    for (int k = 0; k < nt && out >= 0; k++) {
         if (T[3 * k + 2] == OINF) continue;
         if (out >= cap) { out = -1; break; }
         tri[3 * out] = T[3 * k]; tri[3 * out + 1] = T[3 * k + 1]; tri[3 * out + 2] = T[3 * k + 2];
         out++;
     }
-    free(T); free(inserted); free(dead); free(edges);
+    free(T); free(F); free(ylow); free(inserted); free(dead); free(edges);
     return out;
 }
 

@@ -127,6 +127,42 @@ def test_lattice_subsets_are_valid(orc, seed):
     _check_valid_dt(pts, tris.tolist())
 
 
+def test_row_sorted_lattice_is_valid(orc):
+    """Points in raster order over many rows (the support list's order), so
+    triangles whose circumcircles lie above every remaining row are set aside
+    during the insertion: the result must still be the valid, unique
+    triangulation (empty circumcircles, Euler count, hull area)."""
+    rng = np.random.default_rng(11)
+    lattice = [(5 * i, 5 * j) for j in range(18) for i in range(22)]
+    pts = [p for p in lattice if rng.random() < 0.7]
+    tris = orc.delaunay(pts)
+    _check_valid_dt(pts, tris.tolist())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_row_sorted_general_position_matches_brute_force(orc, seed):
+    """Random points in general position inserted in ascending y: equal to the
+    brute-force set of empty-circumcircle triangles."""
+    rng = np.random.default_rng(100 + seed)
+    while True:
+        pts = sorted({tuple(map(int, p)) for p in rng.integers(0, 4000, (18, 2))}, key=lambda p: (p[1], p[0]))
+        n = len(pts)
+        if any(_orient(*(pts[i] for i in t)) == 0 for t in itertools.combinations(range(n), 3)):
+            continue
+        if any(_orient(*(pts[i] for i in q[:3])) != 0 and _incircle(*(pts[i] for i in q)) == 0
+               for q in itertools.combinations(range(n), 4)):
+            continue
+        break
+    brute = []
+    for i, j, k in itertools.combinations(range(n), 3):
+        a, b, c = pts[i], pts[j], pts[k]
+        if _orient(a, b, c) < 0:
+            b, c = c, b
+        if all(_incircle(a, b, c, pts[m]) < 0 for m in range(n) if m not in (i, j, k)):
+            brute.append((i, j, k))
+    assert _canon(orc.delaunay(pts)) == sorted(brute)
+
+
 def _ear_rule(poly_ids):
     """Closed form of the symbolic tie-break on a cocircular convex polygon:
     the vertex with the smallest index is lifted highest, so it is an ear;
