@@ -28,8 +28,12 @@
  * Conventions shared by every call
  *   - All device pointers are owned by the caller.  Calls never allocate
  *     device memory: scratch comes from a caller-provided workspace whose
- *     size the matching *_workspace_bytes() call returns.  Only the pipeline
- *     handle (elas_pipeline_*) owns memory, created in elas_pipeline_create.
+ *     size the matching *_workspace_bytes() call returns.  Only the handles
+ *     own memory: the pipeline (elas_pipeline_*, created in
+ *     elas_pipeline_create), the batch and the server.  The one exception
+ *     to the workspace rule is elas_support_points_static, whose scratch is
+ *     a static device array of the library shared by all its calls (its own
+ *     comment gives the size limit and the race between overlapping calls).
  *   - Device calls are asynchronous on `stream` (a cudaStream_t; NULL = the
  *     legacy default stream).  Argument errors are detected on the host and
  *     returned synchronously; a launch failure returns ELAS_ERR_CUDA;
@@ -520,6 +524,11 @@ void elas_batch_destroy(elas_batch *b);
  *    one of `lanes` streams; a new wave starts whenever a lane is free, so
  *    pairs that arrive while others are on the GPU join the next wave and
  *    overlap with the running ones;
+ *  - out of device memory (an allocation refused although the budget
+ *    allows it, e.g. memory taken by other users of the GPU): idle slots are
+ *    released, least recently used first, and the allocation retried; with
+ *    nothing idle to release the request waits for running waves, and with
+ *    nothing running either its result is ELAS_ERR_NO_MEMORY;
  *  - plain = 1 instead runs one request at a time through the per-pair path
  *    (an elas_pipeline per shape), in arrival order: the comparison.
  * Results are bit-identical to the per-pair path.  Host buffers passed to
@@ -569,6 +578,13 @@ elas_status elas_server_submit(elas_server *s, uint64_t id, int32_t w, int32_t h
 int32_t elas_server_poll(elas_server *s, elas_server_result *out, int32_t max, int32_t timeout_ms);
 double elas_server_now_ms(const elas_server *s);
 elas_status elas_server_stats_get(elas_server *s, elas_server_stats *st);
+/* Waits until every request submitted so far has its result (polled or
+ * not), at most timeout_ms: ELAS_OK, or ELAS_ERR_TIMEOUT when the wait ran
+ * out (the requests stay queued or in flight and complete later). */
+elas_status elas_server_drain(elas_server *s, int32_t timeout_ms);
+/* Fault injection for tests: the next n slot allocations of the scheduler
+ * report out of memory, as a device whose memory other users took would. */
+elas_status elas_server_inject_alloc_failures(elas_server *s, int32_t n);
 /* Waits for every queued request, then stops the scheduler and frees all. */
 void elas_server_destroy(elas_server *s);
 

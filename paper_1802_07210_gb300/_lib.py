@@ -128,6 +128,8 @@ SIGNATURES = {
     "elas_server_poll": (C.c_int32, [_P, _P, _I, _I]),
     "elas_server_now_ms": (C.c_double, [_P]),
     "elas_server_stats_get": (C.c_int, [_P, _P]),
+    "elas_server_drain": (C.c_int, [_P, _I]),
+    "elas_server_inject_alloc_failures": (C.c_int, [_P, _I]),
     "elas_server_destroy": (None, [_P]),
     "elas_probe_sad16": (C.c_int, [_I, _I, _I, _I, _P, _P]),
 }

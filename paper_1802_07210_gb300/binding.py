@@ -442,6 +442,15 @@ class Server:
     def now_ms(self):
         return float(lib().elas_server_now_ms(self._h))
 
+    def drain(self, timeout_ms):
+        """Waits for every submitted request's result; ElasError with
+        ELAS_ERR_TIMEOUT when timeout_ms runs out first."""
+        check(lib().elas_server_drain(self._h, int(timeout_ms)))
+
+    def inject_alloc_failures(self, n):
+        """Testing: the next n slot allocations report out of memory."""
+        check(lib().elas_server_inject_alloc_failures(self._h, int(n)))
+
     def stats(self):
         st = ServerStats()
         check(lib().elas_server_stats_get(self._h, C.byref(st)))

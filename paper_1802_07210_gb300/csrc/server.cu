@@ -13,6 +13,7 @@
 // wave on a free lane, so waves overlap on the device.  The plain mode runs
 // one request at a time through the per-pair pipeline instead.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -84,6 +85,7 @@ struct elas_server {
     // plain mode
     std::map<std::vector<int>, elas_pipeline *> pipelines;
     std::thread th;
+    std::atomic<int> fail_allocs{0};  // injected slot-allocation refusals still to come
 
     double now() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
 };
@@ -152,11 +154,44 @@ int admit(elas_server *s, Request *r, cudaStream_t st, int *error) {
         s->stats.slot_bytes = s->pool.bytes_in_use();
     }
     int id = -1;
-    const elas_status e = s->pool.add(r->w, r->h, &r->p, &id, st);
-    if (e == ELAS_ERR_NO_MEMORY) return -1;  // try again once waves retire
-    if (e != ELAS_OK) {
-        *error = e;
-        return -1;
+    for (;;) {
+        elas_status e;
+        int inj = s->fail_allocs.load();
+        while (inj > 0 && !s->fail_allocs.compare_exchange_weak(inj, inj - 1)) {
+        }
+        if (inj > 0) {  // injected refusal (tests)
+            e = fail(ELAS_ERR_NO_MEMORY, "slot allocation refused (injected)");
+        } else {
+            e = s->pool.add(r->w, r->h, &r->p, &id, st);
+        }
+        if (e == ELAS_OK) break;
+        if (e != ELAS_ERR_NO_MEMORY) {
+            *error = e;
+            return -1;
+        }
+        // the device refused although the budget allows it (memory taken by
+        // others): release an idle slot, least recently used first, and retry
+        int victim = -1;
+        bool busy = false;
+        for (int i = 0; i < cap; ++i) {
+            if (!s->pool[i].used) continue;
+            if (s->slot_busy[i]) {
+                busy = true;
+            } else if (victim < 0 || s->slot_used_at[i] < s->slot_used_at[victim]) {
+                victim = i;
+            }
+        }
+        if (victim < 0) {
+            if (busy) return -1;  // running waves hold memory: try again once they retire
+            *error = ELAS_ERR_NO_MEMORY;  // nothing to release and nothing running
+            return -1;
+        }
+        s->pool.remove(victim, st);
+        s->slot_key[victim].clear();
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stats.slots_released++;
+        s->stats.slots_in_use--;
+        s->stats.slot_bytes = s->pool.bytes_in_use();
     }
     s->slot_key[id] = r->key;
     s->slot_used_at[id] = s->now();
@@ -535,6 +570,23 @@ extern "C" elas_status elas_server_stats_get(elas_server *s, elas_server_stats *
     if (!s || !st) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> g(s->mu);
     *st = s->stats;
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_server_drain(elas_server *s, int32_t timeout_ms) {
+    if (!s) return fail(ELAS_ERR_INVALID_ARG, "NULL server");
+    std::unique_lock<std::mutex> g(s->mu);
+    const bool done = s->cv_poll.wait_for(g, std::chrono::milliseconds(std::max(0, timeout_ms)),
+                                          [s] { return s->stats.completed >= s->stats.submitted; });
+    if (!done)
+        return fail(ELAS_ERR_TIMEOUT, "%lld of %lld requests done after %d ms", (long long)s->stats.completed,
+                    (long long)s->stats.submitted, timeout_ms);
+    return ELAS_OK;
+}
+
+extern "C" elas_status elas_server_inject_alloc_failures(elas_server *s, int32_t n) {
+    if (!s || n < 0) return fail(ELAS_ERR_INVALID_ARG, "NULL server or negative count");
+    s->fail_allocs.store(n);
     return ELAS_OK;
 }
 

@@ -185,3 +185,71 @@ def test_request_errors(requests):
         got = srv.poll(4, 200)
     assert got and got[0]["id"] == 2 and got[0]["status"] == 5  # ELAS_ERR_NO_MEMORY
     srv.close()
+
+
+def _one(srv, rid, r):
+    h, w = r["L"].shape
+    bufs = dict(L=torch.from_numpy(r["L"]).pin_memory(), R=torch.from_numpy(r["R"]).pin_memory(),
+                dL=torch.full((h, w), -7, dtype=torch.int16).pin_memory())
+    srv.submit(rid, bufs["L"], bufs["R"], bufs["dL"], r["prm"])
+    got = []
+    t0 = time.time()
+    while not got:
+        got = srv.poll(4, 200)
+        assert time.time() - t0 < 60, "no result"
+    return got[0], bufs
+
+
+def test_refused_allocation_releases_idle_slots(requests, alone):
+    """A slot allocation the device refuses (injected on the host, as when
+    other users hold the memory) releases an idle slot of another shape and
+    retries; with nothing idle and nothing running the request fails with
+    ELAS_ERR_NO_MEMORY instead of waiting forever, and the server goes on."""
+    B = _B()
+    srv = B.Server(lanes=1, max_wave=2)
+    a, b, c = requests[0], requests[4], requests[8]  # three shapes
+    res, bufs = _one(srv, 1, a)
+    assert res["status"] == 0
+    np.testing.assert_array_equal(bufs["dL"].numpy(), alone[a["id"]][0])
+    # one refusal: the idle slot of a's shape is released, b's is then created
+    srv.inject_alloc_failures(1)
+    res, bufs = _one(srv, 2, b)
+    assert res["status"] == 0
+    np.testing.assert_array_equal(bufs["dL"].numpy(), alone[b["id"]][0])
+    st = srv.stats()
+    assert st["slots_released"] >= 1 and st["slots_in_use"] == 1
+    # refusals beyond every idle slot: c fails with ELAS_ERR_NO_MEMORY
+    srv.inject_alloc_failures(100)
+    res, _ = _one(srv, 3, c)
+    assert res["status"] == 5  # ELAS_ERR_NO_MEMORY
+    assert srv.stats()["slots_in_use"] == 0
+    # the server still serves once allocations succeed again
+    srv.inject_alloc_failures(0)
+    res, bufs = _one(srv, 4, c)
+    assert res["status"] == 0
+    np.testing.assert_array_equal(bufs["dL"].numpy(), alone[c["id"]][0])
+    srv.close()
+
+
+def test_drain_times_out_then_completes(requests):
+    """elas_server_drain returns ELAS_ERR_TIMEOUT while requests are still in
+    flight, and ELAS_OK once every result is in."""
+    B = _B()
+    srv = B.Server(lanes=1, max_wave=1)
+    keep = []
+    for i in range(24):
+        r = requests[8 + i % 4]
+        h, w = r["L"].shape
+        bufs = (torch.from_numpy(r["L"]).pin_memory(), torch.from_numpy(r["R"]).pin_memory(),
+                torch.empty((h, w), dtype=torch.int16).pin_memory())
+        keep.append(bufs)
+        srv.submit(i, bufs[0], bufs[1], bufs[2], r["prm"])
+    with pytest.raises(B.ElasError) as ei:
+        srv.drain(0)
+    assert ei.value.status == 4  # ELAS_ERR_TIMEOUT
+    srv.drain(60000)
+    got = []
+    while len(got) < 24:
+        got += srv.poll(64, 200)
+    assert all(g["status"] == 0 for g in got)
+    srv.close()
