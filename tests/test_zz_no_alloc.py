@@ -73,6 +73,34 @@ def test_static_scratch_matches_workspace_entry_point():
     _same(_static_call(B, descL, descR, prm), B.elas_support_points(descL, descR, prm))
 
 
+def test_static_scratch_row_matcher_and_variants():
+    """Sizes that take the row-organised support matcher (2048x1536 at step
+    5: 307 lattice rows, 504,064 of the 524,288 scratch bytes) and the
+    paper's variants (census records, support down-sampling) through the
+    static entry point, each equal to elas_support_points."""
+    require_gpu()
+    from paper_1802_07210_gb300 import binding as B
+    lib = B.lib()
+    wl = synth.scaled_workload(2048, 1536, 128)
+    L, R, _ = synth.workload_pair(wl, 0, 12)
+    prm = B.as_params(wl.params)
+    assert 500_000 < lib.elas_support_workspace_bytes(2048, 1536, C.byref(prm)) <= 512 * 1024
+    descL, descR = B.elas_descriptors(dev(L), dev(R))
+    _same(_static_call(B, descL, descR, prm), B.elas_support_points(descL, descR, prm))
+    # the paper's census records (9x9, 32 bytes) and 1/8 down-sampling
+    wl2 = synth.VGA_640
+    L, R, _ = synth.workload_pair(wl2, 1, 2)
+    prm_c = B.as_params(dict(wl2.params, census_support_w=9, census_dense_w=5))
+    cL, cR = B.elas_census(dev(L), dev(R), 9, 32)
+    _same(_static_call(B, cL, cR, prm_c), B.elas_support_points(cL, cR, prm_c))
+    prm_d = B.as_params(dict(wl2.params, candidate_stepsize=1, support_downsample=8))
+    descL, descR = B.elas_descriptors(dev(L), dev(R))
+    if lib.elas_support_workspace_bytes(640, 480, C.byref(prm_d)) <= 512 * 1024:
+        _same(_static_call(B, descL, descR, prm_d), B.elas_support_points(descL, descR, prm_d))
+    prm_d = B.as_params(dict(wl2.params, support_downsample=8))
+    _same(_static_call(B, descL, descR, prm_d), B.elas_support_points(descL, descR, prm_d))
+
+
 def test_static_scratch_refuses_oversized_images():
     require_gpu()
     from paper_1802_07210_gb300 import binding as B
