@@ -1,8 +1,9 @@
 // Library-wide host entry points: defaults, errors, validation, prior table.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -16,6 +17,23 @@ void set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+int sm_count() {
+    static std::atomic<int> cached[64];  // 0 = not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 152;
+    }
+    cached[dev].store(n, std::memory_order_relaxed);
+    return n;
 }
 
 elas_status fail(elas_status st, const char *fmt, ...) {

@@ -15,6 +15,9 @@ elas_status fail(elas_status st, const char *fmt, ...);
 elas_status launch_status(const char *what);
 // Validates the parameter block against the image size.
 elas_status check_params(const elas_params *p, int32_t w, int32_t h);
+// Streaming multiprocessors of the current device (queried once per device;
+// launch grids are sized in multiples of it).
+int sm_count();
 
 inline cudaStream_t to_stream(elas_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -1280,13 +1280,13 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     const int nall = a.gw * a.gh + 1 + 2 * h + 4;
     dt_init_kernel<<<dim3((nall + 255) / 256, nsides), 256, 0, st>>>(a);
     const int tb = 256;
-    const int pblocks = max(1, min((cap + tb - 1) / tb, 152 * 8));
+    const int pblocks = max(1, min((cap + tb - 1) / tb, sm_count() * 8));
     dt_points_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_cell_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_scatter_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_dedup_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     const int gblocks =
-        max(1, min((cap + kDtGroupThreads / kDtGroupOne - 1) / (kDtGroupThreads / kDtGroupOne), 152 * 16));
+        max(1, min((cap + kDtGroupThreads / kDtGroupOne - 1) / (kDtGroupThreads / kDtGroupOne), sm_count() * 16));
     // one pair: the CTA pass takes the group pass's queue directly (its time
     // is that of the longest star, which the warp pass would not shorten)
     dt_pass1_kernel<<<dim3(gblocks, nsides), kDtGroupThreads, 0, st>>>(a);
@@ -1296,10 +1296,10 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel shared memory attribute");
     (void)smem2;
-    dt_pass_block_kernel<<<dim3(152 * kDtBlocksPerSM, nsides), kDtBlockThreads, smem3, st>>>(a, 0);
+    dt_pass_block_kernel<<<dim3(sm_count() * kDtBlocksPerSM, nsides), kDtBlockThreads, smem3, st>>>(a, 0);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
-    dt_emit_big_kernel<<<dim3(152, nsides), 256, 0, st>>>(a);
+    dt_emit_big_kernel<<<dim3(sm_count(), nsides), 256, 0, st>>>(a);
     return launch_status("triangulation kernels");
 }
 
@@ -1332,8 +1332,8 @@ static int dt_point_blocks(int cap, int threads, int npairs) {
     // grid-stride kernels: about a third of the capacity per sweep in a
     // batch (the support list holds a fraction of the lattice), capped
     const int full = (cap + threads - 1) / threads;
-    if (npairs <= 1) return max(1, min(full, 152 * 8));
-    return max(1, min((full + 2) / 3, 152 * 8));
+    if (npairs <= 1) return max(1, min(full, sm_count() * 8));
+    return max(1, min((full + 2) / 3, sm_count() * 8));
 }
 
 elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VMap &pairs, int nsides,
@@ -1359,8 +1359,8 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         vmap_add(m_grp, slot, dim3(dt_point_blocks(a.cap, gthreads, pairs.n), nsides));
         // the second group pass gets a warp per star of a queue of a few
         // percent of the points
-        vmap_add(m_grp2, slot, dim3(max(1, min(152, a.cap / 256)), nsides));
-        vmap_add(m_big, slot, dim3(pairs.n == 1 ? 152 : 64, nsides));
+        vmap_add(m_grp2, slot, dim3(max(1, min(sm_count(), a.cap / 256)), nsides));
+        vmap_add(m_big, slot, dim3(pairs.n == 1 ? sm_count() : 64, nsides));
         max_gh = max(max_gh, a.gh);
     }
     const int smem3 = kDtCandCap2 * (int)sizeof(int4) + (2 * max_gh + 1) * (int)sizeof(int);
@@ -1382,8 +1382,7 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
         dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
     }
-    int dev = 0, nsm = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nsm = sm_count();
     dt_pass_block_kernel_b<<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter,
                                                                                  one ? 0 : 1);
     dt_tri_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);

@@ -460,7 +460,8 @@ static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
     const size_t n = (size_t)a.w * a.h * a.nsides;  // int16 entries
     if (aligned(a.s[0].dplane, 16)) {
         const size_t blocks = (n / 8 + 255) / 256;
-        raster_init_kernel<<<(unsigned)(blocks < 152 * 8 ? (blocks > 0 ? blocks : 1) : 152 * 8), 256, 0, st>>>(a);
+        const size_t cap_blocks = (size_t)sm_count() * 8;
+        raster_init_kernel<<<(unsigned)(blocks < cap_blocks ? (blocks > 0 ? blocks : 1) : cap_blocks), 256, 0, st>>>(a);
         elas_status s0 = launch_status("raster_init_kernel");
         if (s0 != ELAS_OK) return s0;
     } else if (cudaMemsetAsync(a.s[0].dplane, 0xFF, n * sizeof(int16_t), st) != cudaSuccess ||
@@ -471,11 +472,11 @@ static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
     if (maxt == 0) return ELAS_OK;
     const int wpb = 256 / kRasterGroup;  // triangles per CTA pass
     int blocks = (maxt + wpb - 1) / wpb;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > sm_count() * 4) blocks = sm_count() * 4;
     plane_raster_kernel<<<dim3(blocks, a.nsides), 256, 0, st>>>(a);
     elas_status s = launch_status("plane_raster_kernel");
     if (s != ELAS_OK) return s;
-    plane_raster_big_kernel<<<2 * 152, 256, 0, st>>>(a);
+    plane_raster_big_kernel<<<2 * sm_count(), 256, 0, st>>>(a);
     return launch_status("plane_raster_big_kernel");
 }
 
@@ -599,15 +600,15 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         const int slot = pairs.slot[i];
         const DenseStage &d = slot_entry(host, pairs.stride, slot);
         const size_t n8 = ((size_t)d.raster.nsides * d.raster.w * d.raster.h + 7) / 8;
-        vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)152 * 4)));
+        vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)sm_count() * 4)));
         const int maxt = raster_max_ntri(d.raster);
         const int wpb = 256 / kRasterGroup;
         int blocks = (maxt + wpb - 1) / wpb;
         if (pairs.n > 1) blocks = (blocks + 2) / 3;
-        blocks = max(1, min(blocks, 152 * 16));
+        blocks = max(1, min(blocks, sm_count() * 16));
         vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
         // big triangles: the one-pair launch's 2 CTAs per SM, shared by the pairs
-        vmap_add(m_big, slot, dim3(max(32, 2 * 152 / pairs.n)));
+        vmap_add(m_big, slot, dim3(max(32, 2 * sm_count() / pairs.n)));
         vmap_add(m_cell, slot, cell_grid(d.cell, 2));
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }

@@ -257,7 +257,7 @@ elas_status launch_speckle(const int16_t *d, int w, int h, int thr, int min_size
     if (s != ELAS_OK) return s;
     const int n = w * h;
     int blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     speckle_border_kernel<<<blocks, 256, 0, st>>>(a);
     if ((s = launch_status("speckle_border_kernel")) != ELAS_OK) return s;
     speckle_resolve_kernel<<<blocks, 256, 0, st>>>(a);

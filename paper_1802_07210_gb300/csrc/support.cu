@@ -598,7 +598,7 @@ static elas_status red_smem_attr(const void *fn, size_t smem) {
 // per-candidate kernel, and so do launches of fewer lattice rows than two
 // per SM (one CTA per row would leave SMs idle).
 constexpr size_t kSupRowSmemMax = 160 * 1024;
-constexpr int kSupRowMinRows = 2 * 152;
+inline int sup_row_min_rows() { return 2 * sm_count(); }
 
 static elas_status sup_row_smem_attr(const void *fn, size_t smem) {
     if (smem > 48 * 1024 &&
@@ -632,7 +632,7 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     const int warps_per_block = 8;
     const size_t row_smem = sup_row_smem(sa.match.a.wc, sa.match.a.dmin, sa.match.a.dmax).total;
     const bool census = sa.match.a.census != 0;
-    if (row_smem <= kSupRowSmemMax && sa.match.a.hc >= kSupRowMinRows) {
+    if (row_smem <= kSupRowSmemMax && sa.match.a.hc >= sup_row_min_rows()) {
         const void *fn = census ? (const void *)support_match_row_kernel<true>
                                 : (const void *)support_match_row_kernel<false>;
         if ((s = sup_row_smem_attr(fn, row_smem)) != ELAS_OK) return s;
@@ -667,7 +667,7 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     const int k = sa.compact.keep_every;
     const ListGridArgs lg{list, count, (nc + k - 1) / k, sa.red.g, grid_L, grid_R};
     int blocks = (lg.cap + 127) / 128;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > sm_count() * 4) blocks = sm_count() * 4;
     list_grid_kernel<<<blocks, 128, 0, st>>>(lg);
     return launch_status("list_grid_kernel");
 }
@@ -698,7 +698,7 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
     }
     if (pairs.n == 0) return ELAS_OK;
     elas_status s;
-    if (row_smem <= kSupRowSmemMax && vmap_total(m_rows) >= kSupRowMinRows) {
+    if (row_smem <= kSupRowSmemMax && vmap_total(m_rows) >= sup_row_min_rows()) {
         if ((s = sup_row_smem_attr((const void *)support_match_row_kernel_b, row_smem)) != ELAS_OK) return s;
         support_match_row_kernel_b<<<vmap_total(m_rows), 32 * match_warps, row_smem, st>>>(t.match, m_rows);
         if ((s = launch_status("support_match_row_kernel_b")) != ELAS_OK) return s;
