@@ -9,8 +9,9 @@ LR check, post-processing), inputs resident in HBM, L2 flushed before every
 step.  The same line carries:
   e2e          the same metric through the host-buffer call (copies timed);
   roofline     the dense argmin kernel (one launch covers both reference
-               images) against the measured SAD16 ceiling, timed by events
-               inside the timed steps;
+               images) against its binding roof (HBM bytes or the measured
+               SAD16 ceiling, whichever bounds the launch from below), both
+               shown, timed by events inside the timed steps;
   batch        64 pairs of 1242x375 with 256 disparities in one batched wave
                (one launch per kernel for all pairs, CUDA graph, tuned tile
                shapes) against 64 runs of the plain path, with the batched
@@ -18,9 +19,12 @@ step.  The same line carries:
   mixed_batch  128 pairs of mixed sizes and disparity ranges in one wave
                against 128 plain runs;
   serving      8 simulated cameras with Poisson arrivals (600 pairs/s in
-               total): the continuous-batching server against the plain
-               per-pair loop, p50/p99 latency and pairs/s;
-  cpu_baseline the oracle on the host cores.
+               total, 60 s): the continuous-batching server against the
+               plain per-pair loop, p50/p99 latency and pairs/s;
+  serving_saturated  the same cameras at 4000 pairs/s offered (above the
+               plain path's rate): served pairs/s and latency of both;
+  cpu_baseline the oracle on the host cores;
+  summary      the figures of every section, last on the line.
 N > 1 runs N independent replicas, one per GPU (pairs are independent; no
 collective on the data path); the extra sections run on rank 0.
 ``--impl reference`` times the CPU oracle instead.
@@ -289,7 +293,7 @@ def pair_dense_evals(B, torch, wl, L, R, dev):
     return dense_work(work, prm, w, h)
 
 
-def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad, tune=True):
+def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad, hbm, tune=True):
     """64 x 1242x375 D=256 through one batched wave vs the plain path."""
     wl, cfg = synth.KITTI_1242, 3
     w, h = wl.spec.w, wl.spec.h
@@ -316,17 +320,16 @@ def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, pea
     evals = sum(pair_dense_evals(B, torch, wl, L, R, dev) for L, R in pool) * (npairs // distinct)
     evals += sum(pair_dense_evals(B, torch, wl, *pool[i], dev) for i in range(npairs % distinct))
     t_b, t_p = float(np.mean(ms)), float(np.mean(ms_plain))
-    ach = evals / (stage["dense_argmin"] * 1e-3) / 1e9
+    roof = {"kernel": "cell_kernel_b (dense argmin, every pair and both reference images in one launch)"}
+    roof.update(dense_roofline(evals, DENSE_MIN_BYTES_PER_PX * w * h * npairs, stage["dense_argmin"], peak_gsad,
+                               hbm[0], hbm[1]))
+    roof["time_source"] = "CUDA events around the launch in an eager run of the same batch"
     return {"workload": "%d x %s" % (npairs, wl.name), "pairs": npairs, "distinct_pairs": distinct,
             "ms_per_batch": t_b, "pairs_per_s": npairs / (t_b * 1e-3), "mpix_per_s": npairs * w * h / (t_b * 1e-3) / 1e6,
             "plain_ms_per_batch": t_p, "plain_pairs_per_s": npairs / (t_p * 1e-3),
             "speedup_vs_plain": t_p / t_b, "tuned": tuned, "stages_ms": stage, "support_points_first": nsup[:4],
             "launches_per_batch": 21, "graph": True,
-            "l2": "flushed before every timed batch",
-            "roofline_dense": {"kernel": "cell_kernel_b (dense argmin, every pair and both reference images in one launch)",
-                               "bound": "alu", "achieved": ach, "peak": peak_gsad, "unit": "G SAD16/s",
-                               "frac": ach / peak_gsad, "algorithmic_evals": evals,
-                               "time_source": "CUDA events around the launch in an eager run of the same batch"}}
+            "l2": "flushed before every timed batch", "roofline_dense": roof}
 
 
 def run_mixed_section(B, torch, dev, stream, flush, steps, npairs, tune=True):
@@ -428,6 +431,7 @@ def run_serve_section(B, torch, seconds, rate_per_camera=75.0, seed=5):
     out = {"cameras": "2x640x480 D=128, 4x1242x375 D=256, 2x1920x1080 D=256",
            "arrivals": "Poisson, %.0f pairs/s per camera, %.0f pairs/s in total, seeded" % (rate_per_camera,
                                                                                           rate_per_camera * len(cams)),
+           "offered_pairs_per_s": rate_per_camera * len(cams),
            "seconds": seconds, "requests": len(arr),
            "latency": "submit to outputs on the host (host copies included)",
            "continuous_batching": run(False), "plain_per_pair": run(True)}
@@ -679,12 +683,13 @@ def run_only(args, B, torch, dev):
     if args.only == "batch":
         peak = alu_peak(B, torch, dev, stream)[KERNEL_SAD_VARIANT] / 1e9
         return run_batch_section(B, torch, dev, stream, _Flush(), steps, args.batch_pairs, args.batch_distinct, peak,
-                                 tune=not args.no_tune)
+                                 _peaks(), tune=not args.no_tune)
     if args.only == "mixed":
         return run_mixed_section(B, torch, dev, stream, _Flush(), steps, args.mixed_pairs, tune=not args.no_tune)
     if args.only == "accuracy":
         return run_accuracy_section(B, torch, dev)
-    return run_serve_section(B, torch, args.serve_seconds)
+    return {"offered": run_serve_section(B, torch, args.serve_seconds),
+            "saturated": run_serve_section(B, torch, args.saturate_seconds, rate_per_camera=500.0, seed=6)}
 
 
 def main():
@@ -697,9 +702,11 @@ def main():
     ap.add_argument("--pool", type=int, default=4, help="distinct pairs cycled through")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=64)
-    ap.add_argument("--batch-distinct", type=int, default=8)
+    ap.add_argument("--batch-distinct", type=int, default=64)
     ap.add_argument("--mixed-pairs", type=int, default=128)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--saturate-seconds", type=float, default=3.0,
+                    help="length of the saturated serving schedule (offered load above the plain path's rate)")
     ap.add_argument("--skip-extra", action="store_true", help="only the plain-path line")
     ap.add_argument("--only", default=None, choices=["batch", "mixed", "serve", "accuracy"],
                     help="run only this section (its JSON object is printed alone)")
@@ -815,33 +822,31 @@ def main():
     evals_pool = [pair_dense_evals(B, torch, wl, L, R, dev) for L, R, _ in pool]
     evals = float(np.mean([evals_pool[i % len(pool)] for i in range(args.steps)]))
     t_dense = stages["dense_argmin"]
-    achieved = evals / (t_dense * 1e-3) / 1e9
     dense_bytes = DENSE_MIN_BYTES_PER_PX * px
-    roof = {"kernel": "cell_kernel (dense argmin, both reference images in one launch)",
-            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SAD16/s", "frac": achieved / peak,
-            "traffic": DENSE_TRAFFIC_BYTES.get(wl.name), "traffic_source": DENSE_TRAFFIC_SOURCE,
-            "algorithmic_evals_per_launch": evals,
-            "time": "mean of CUDA events around the launch, recorded by the library in a second pass of the timed steps (same pairs, same L2 flush)",
-            "peak_source": "measured: probe kernel running the dense matcher's SAD16 sequence (variant %d, the "
+    roof = {"kernel": "cell_kernel (dense argmin, both reference images in one launch)"}
+    roof.update(dense_roofline(evals, dense_bytes, t_dense, peak, hbm_gbs, peak_kind))
+    roof.update({
+        "traffic": DENSE_TRAFFIC_BYTES.get(wl.name), "traffic_source": DENSE_TRAFFIC_SOURCE,
+        "time": "mean of CUDA events around the launch, recorded by the library in a second pass of the timed "
+                "steps (same pairs, same L2 flush)",
+        "alu_peak_source": "measured: probe kernel running the dense matcher's SAD16 sequence (variant %d, the "
                            "fastest of the three) on registers over all SMs" % KERNEL_SAD_VARIANT,
-            "probe_variants_gsad16": {str(k): v / 1e9 for k, v in probe.items()},
-            "hbm": {"achieved_gbs": dense_bytes / (t_dense * 1e-3) / 1e9, "peak_gbs": hbm_gbs,
-                    "frac": dense_bytes / (t_dense * 1e-3) / 1e9 / hbm_gbs,
-                    "min_bytes_per_launch": dense_bytes,
-                    "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_kind}}
+        "probe_variants_gsad16": {str(k): v / 1e9 for k, v in probe.items()}})
 
     extra = {}
     if rank == 0 and not args.skip_extra:
         # each section reports on its own: an error in one is recorded in its
         # object and leaves the headline and the other sections standing
         sections = (
+            ("accuracy", lambda: run_accuracy_section(B, torch, dev)),
             ("batch", lambda: run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
-                                                args.batch_pairs, args.batch_distinct, peak,
+                                                args.batch_pairs, args.batch_distinct, peak, (hbm_gbs, peak_kind),
                                                 tune=not args.no_tune)),
             ("mixed_batch", lambda: run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
                                                       args.mixed_pairs, tune=not args.no_tune)),
             ("serving", lambda: run_serve_section(B, torch, args.serve_seconds)),
-            ("accuracy", lambda: run_accuracy_section(B, torch, dev)),
+            ("serving_saturated", lambda: run_serve_section(B, torch, args.saturate_seconds, rate_per_camera=500.0,
+                                                            seed=6)),
         )
         for key, fn in sections:
             try:
@@ -861,13 +866,44 @@ def main():
                 "support_points": st["n_support"], "triangles": [st["n_tri_left"], st["n_tri_right"]],
                 "stages_ms": stages, "clocks": clk, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_STEP[bool(wl.postprocess)] * args.steps, "roofline": roof}
-        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, cfg)
+        # the long accuracy object first; the throughput sections and a
+        # compact summary close the line
+        line.update(extra)
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def summary(line):
+    """The figures of every section in one small object."""
+    out = {"plain_mpix_per_s": line["value"], "plain_pairs_per_s": line["pairs_per_s"],
+           "e2e_mpix_per_s": line["e2e"]["value"],
+           "dense": {"bound": line["roofline"]["bound"], "frac": line["roofline"]["frac"],
+                     "frac_alu": line["roofline"]["alu"]["frac"], "frac_hbm": line["roofline"]["hbm"]["frac"],
+                     "launch_us": line["roofline"]["launch_us"]}}
+    b = line.get("batch", {})
+    if "pairs_per_s" in b:
+        out["batch_64x1242x375"] = {"pairs_per_s": b["pairs_per_s"], "plain_pairs_per_s": b["plain_pairs_per_s"],
+                                    "speedup": b["speedup_vs_plain"], "distinct_pairs": b["distinct_pairs"],
+                                    "dense_bound": b["roofline_dense"]["bound"],
+                                    "dense_frac": b["roofline_dense"]["frac"],
+                                    "dense_frac_alu": b["roofline_dense"]["alu"]["frac"]}
+    m = line.get("mixed_batch", {})
+    if "pairs_per_s" in m:
+        out["mixed_128"] = {"pairs_per_s": m["pairs_per_s"], "plain_pairs_per_s": m["plain_pairs_per_s"],
+                            "speedup": m["speedup_vs_plain"]}
+    for key in ("serving", "serving_saturated"):
+        sv = line.get(key, {})
+        if "continuous_batching" in sv:
+            cb, pp = sv["continuous_batching"], sv["plain_per_pair"]
+            out[key] = {"offered_pairs_per_s": sv["offered_pairs_per_s"], "seconds": sv["seconds"],
+                        "batched": {k: cb[k] for k in ("pairs_per_s", "p50_ms", "p99_ms")},
+                        "plain": {k: pp[k] for k in ("pairs_per_s", "p50_ms", "p99_ms")}}
+    return out
 
 
 def dense_work(work, prm, w, h):
@@ -911,13 +947,33 @@ def dense_work(work, prm, w, h):
 # DRAM bytes (read + write) of one cell_kernel launch, from one ncu capture of
 # the kernel as it is now (dram__bytes_read.sum + dram__bytes_write.sum);
 # to be taken again whenever the kernel changes.
-DENSE_TRAFFIC_BYTES = {"640x480_D256": 11032320}
-DENSE_TRAFFIC_SOURCE = ("ncu --set full --clock-control none -k regex:cell_kernel -s 2 -c 1 on "
-                        "python bench.py --steps 3 --warmup 3 --no-cpu-baseline --skip-extra (L2 flushed before "
-                        "each step; below the minimum bytes because the descriptors written just before stay "
-                        "partly in L2)")
+DENSE_TRAFFIC_BYTES = {"640x480_D256": 11037440}
+DENSE_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                        "--clock-control none -k regex:cell_kernel -s 2 -c 1 on python bench.py --steps 3 --warmup 3 "
+                        "--no-cpu-baseline --skip-extra (L2 flushed before each step; reads only, below the minimum "
+                        "bytes because the descriptors written just before stay partly in L2 and the two maps "
+                        "written stay there too)")
 
 KERNEL_SAD_VARIANT = 2  # the probe variant whose instruction sequence the dense matcher uses
+
+
+def dense_roofline(evals, min_bytes, t_ms, peak_gsad, hbm_gbs, peak_kind):
+    """Both roofs of a dense launch (algorithmic work over its measured time)
+    and the binding one: the roof whose own lower bound on the time is the
+    larger (HBM at these candidate counts: about 10 SAD16 per pixel and
+    image against 40 bytes per pixel)."""
+    t = t_ms * 1e-3
+    alu = {"achieved": evals / t / 1e9, "peak": peak_gsad, "unit": "G SAD16/s",
+           "frac": evals / t / 1e9 / peak_gsad, "algorithmic_evals": evals,
+           "lower_bound_us": evals / (peak_gsad * 1e9) * 1e6}
+    hbm = {"achieved": min_bytes / t / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+           "frac": min_bytes / t / 1e9 / hbm_gbs, "algorithmic_bytes": min_bytes,
+           "lower_bound_us": min_bytes / (hbm_gbs * 1e9) * 1e6,
+           "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_kind}
+    bound = "hbm" if hbm["lower_bound_us"] >= alu["lower_bound_us"] else "alu"
+    top = hbm if bound == "hbm" else alu
+    return {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "launch_us": t_ms * 1e3, "alu": alu, "hbm": hbm}
 
 
 def alu_peak(B, torch, dev, stream):
