@@ -126,7 +126,7 @@ typedef struct {
      * points numbered 0, k, 2k, ... in raster order of the candidate grid
      * (d_can shows -1 for the others), and the list, its count, the grid
      * vectors and so the triangulation and the dense prior see only those.
-     * Per-pair calls and the pipeline; batches and the server refuse k >= 2. */
+     * Every route takes it: per-pair calls, the pipeline, batches, server. */
     int32_t support_downsample;
 } elas_params;
 
@@ -459,10 +459,10 @@ void elas_pipeline_destroy(elas_pipeline *pl);
  * and the triangulation's CTA pass takes its work from one queue over all
  * pairs.  With use_graph the launch sequence is captured once into a CUDA
  * graph and replayed.  Results are identical to the per-pair path.
- * Batches and the server take Sobel descriptors only and no support
- * down-sampling: parameters with census windows or support_downsample >= 2
- * return ELAS_ERR_INVALID_ARG there (those variants run through the per-pair
- * calls and the pipeline).
+ * Pairs of the paper's variant (census windows, support down-sampling) mix
+ * with the others: each stage whose kernel depends on the cost kind (the
+ * descriptors or census records of each window size, support matching, the
+ * dense argmin) is launched once per kind present in the batch.
  *
  * elas_batch_create: n pairs (1 <= n <= 256), pair i of w[i] x h[i] with
  *   params[i] (w, h >= candidate_stepsize).  Allocates every slot.

@@ -381,11 +381,22 @@ template <bool CENSUS> __global__ void __launch_bounds__(1024) cell_kernel(CellA
     cell_body<1, CENSUS>(a, vb_single());
 }
 
-// Batched launches carry Sobel descriptors only.
-template <int TPP>
+// Batched launches: one launch per cost kind among the pairs.
+template <int TPP, bool CENSUS>
 __global__ void __launch_bounds__(1024) cell_kernel_b(const CellArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    cell_body<TPP, false>(slot_entry(tab, vm.stride, vb.slot), vb);
+    cell_body<TPP, CENSUS>(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+template <bool CENSUS>
+static void cell_launch_b(const CellArgs *tab, const VMap &m, int tpp, int threads, cudaStream_t st) {
+    const int total = vmap_total(m);
+    if (tpp == 1)
+        cell_kernel_b<1, CENSUS><<<total, threads, 0, st>>>(tab, m);
+    else if (tpp == 2)
+        cell_kernel_b<2, CENSUS><<<total, threads, 0, st>>>(tab, m);
+    else
+        cell_kernel_b<4, CENSUS><<<total, threads, 0, st>>>(tab, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -590,11 +601,12 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
     if (pairs.n == 0) return ELAS_OK;
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
     if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return fail(ELAS_ERR_INVALID_ARG, "dense pixels per thread %d", ppt);
-    VMap m_init, m_tri, m_big, m_cell;
+    VMap m_init, m_tri, m_big, m_cell[2];
     vmap_clear(m_init, pairs.stride);
     vmap_clear(m_tri, pairs.stride);
     vmap_clear(m_big, pairs.stride);
-    vmap_clear(m_cell, pairs.stride);
+    vmap_clear(m_cell[0], pairs.stride);
+    vmap_clear(m_cell[1], pairs.stride);
     int threads = 32;
     for (int i = 0; i < pairs.n; ++i) {
         const int slot = pairs.slot[i];
@@ -609,7 +621,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
         // big triangles: the one-pair launch's 2 CTAs per SM, shared by the pairs
         vmap_add(m_big, slot, dim3(max(32, 2 * sm_count() / pairs.n)));
-        vmap_add(m_cell, slot, cell_grid(d.cell, 2));
+        vmap_add(m_cell[d.cell.census ? 1 : 0], slot, cell_grid(d.cell, 2));
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }
     raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
@@ -619,13 +631,8 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
     if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");
-    const int total = vmap_total(m_cell);
-    if (tpp == 1)
-        cell_kernel_b<1><<<total, threads, 0, st>>>(t.cell, m_cell);
-    else if (tpp == 2)
-        cell_kernel_b<2><<<total, threads, 0, st>>>(t.cell, m_cell);
-    else
-        cell_kernel_b<4><<<total, threads, 0, st>>>(t.cell, m_cell);
+    if (m_cell[0].n > 0) cell_launch_b<false>(t.cell, m_cell[0], tpp, threads, st);
+    if (m_cell[1].n > 0) cell_launch_b<true>(t.cell, m_cell[1], tpp, threads, st);
     return launch_status("cell_kernel_b");
 }
 

@@ -161,20 +161,14 @@ elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, cons
 // ---------------------------------------------------------------------------
 constexpr int kCensusTW = 32, kCensusTH = 8;
 
-struct CensusArgs {
-    const uint8_t *imgL, *imgR;
-    int w, h, pitch;
-    uint4 *outL, *outR;
-};
-
-template <int W, int NW> __global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel(CensusArgs a) {
+template <int W, int NW> __device__ __forceinline__ void census_body(const CensusArgs &a, const VB &vb) {
     constexpr int R = W / 2, SW = kCensusTW + 2 * R, SH = kCensusTH + 2 * R;
     static_assert(W * W <= 32 * NW, "census window does not fit the record");
     __shared__ uint8_t s[SH][SW];
-    const uint8_t *img = blockIdx.z ? a.imgR : a.imgL;
-    uint4 *out = blockIdx.z ? a.outR : a.outL;
+    const uint8_t *img = vb.z ? a.imgR : a.imgL;
+    uint4 *out = vb.z ? a.outR : a.outL;
     const int w = a.w, h = a.h;
-    const int x0 = blockIdx.x * kCensusTW, y0 = blockIdx.y * kCensusTH;
+    const int x0 = vb.x * kCensusTW, y0 = vb.y * kCensusTH;
     const int tid = threadIdx.y * kCensusTW + threadIdx.x;
     for (int i = tid; i < SW * SH; i += kCensusTW * kCensusTH) {
         const int sx = i % SW, sy = i / SW;
@@ -202,11 +196,27 @@ template <int W, int NW> __global__ void __launch_bounds__(kCensusTW *kCensusTH)
     for (int j = 0; j < NW / 4; ++j) o[j] = make_uint4(word[4 * j], word[4 * j + 1], word[4 * j + 2], word[4 * j + 3]);
 }
 
+template <int W, int NW> __global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel(CensusArgs a) {
+    census_body<W, NW>(a, vb_single());
+}
+template <int W, int NW>
+__global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel_b(const CensusArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    census_body<W, NW>(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+static dim3 census_grid(int w, int h, int two) {
+    return dim3((w + kCensusTW - 1) / kCensusTW, (h + kCensusTH - 1) / kCensusTH, two ? 2 : 1);
+}
+
 template <int W, int NW>
 static elas_status census_launch(const CensusArgs &a, int two, cudaStream_t st) {
-    const dim3 grid((a.w + kCensusTW - 1) / kCensusTW, (a.h + kCensusTH - 1) / kCensusTH, two ? 2 : 1);
-    census_kernel<W, NW><<<grid, dim3(kCensusTW, kCensusTH), 0, st>>>(a);
+    census_kernel<W, NW><<<census_grid(a.w, a.h, two), dim3(kCensusTW, kCensusTH), 0, st>>>(a);
     return launch_status("census_kernel");
+}
+
+template <int W, int NW> static void census_launch_b(const CensusArgs *tab, const VMap &m, cudaStream_t st) {
+    census_kernel_b<W, NW><<<vmap_total(m), dim3(kCensusTW, kCensusTH), 0, st>>>(tab, m);
 }
 
 bool census_shape_ok(int window, int nbytes) {
@@ -217,7 +227,8 @@ bool census_shape_ok(int window, int nbytes) {
 
 elas_status launch_census(const uint8_t *imgL, const uint8_t *imgR, int w, int h, int pitch, int window, int nbytes,
                           uint8_t *outL, uint8_t *outR, cudaStream_t st) {
-    const CensusArgs a{imgL, imgR, w, h, pitch, reinterpret_cast<uint4 *>(outL), reinterpret_cast<uint4 *>(outR)};
+    const CensusArgs a{imgL, imgR, w, h, pitch, reinterpret_cast<uint4 *>(outL), reinterpret_cast<uint4 *>(outR),
+                       window};
     const int two = imgR != nullptr;
     if (nbytes == 32) {
         switch (window) {
@@ -239,6 +250,47 @@ elas_status launch_census(const uint8_t *imgL, const uint8_t *imgR, int w, int h
         }
     }
     return fail(ELAS_ERR_INVALID_ARG, "census window %d with %d bytes per pixel", window, nbytes);
+}
+
+// Batched census records: one launch per window size among the pairs (a
+// batch of the paper's variant normally has one), every pair's tiles in it.
+elas_status launch_census_b(const CensusArgs *tab, const CensusArgs *host, const VMap &pairs, int nbytes,
+                            cudaStream_t st) {
+    bool done[16] = {};
+    for (int i = 0; i < pairs.n; ++i) {
+        const int win = slot_entry(host, pairs.stride, pairs.slot[i]).window;
+        if (!census_shape_ok(win, nbytes)) return fail(ELAS_ERR_INVALID_ARG, "census window %d, %d bytes", win, nbytes);
+        if (done[win]) continue;
+        done[win] = true;
+        VMap m;
+        vmap_clear(m, pairs.stride);
+        for (int j = i; j < pairs.n; ++j) {
+            const CensusArgs &c = slot_entry(host, pairs.stride, pairs.slot[j]);
+            if (c.window == win) vmap_add(m, pairs.slot[j], census_grid(c.w, c.h, c.imgR != nullptr));
+        }
+        if (nbytes == 32) {
+            switch (win) {
+            case 3: census_launch_b<3, 8>(tab, m, st); break;
+            case 5: census_launch_b<5, 8>(tab, m, st); break;
+            case 7: census_launch_b<7, 8>(tab, m, st); break;
+            case 9: census_launch_b<9, 8>(tab, m, st); break;
+            case 11: census_launch_b<11, 8>(tab, m, st); break;
+            case 13: census_launch_b<13, 8>(tab, m, st); break;
+            case 15: census_launch_b<15, 8>(tab, m, st); break;
+            }
+        } else {
+            switch (win) {
+            case 3: census_launch_b<3, 4>(tab, m, st); break;
+            case 5: census_launch_b<5, 4>(tab, m, st); break;
+            case 7: census_launch_b<7, 4>(tab, m, st); break;
+            case 9: census_launch_b<9, 4>(tab, m, st); break;
+            case 11: census_launch_b<11, 4>(tab, m, st); break;
+            }
+        }
+        elas_status s = launch_status("census_kernel_b");
+        if (s != ELAS_OK) return s;
+    }
+    return ELAS_OK;
 }
 
 }  // namespace elas

@@ -71,6 +71,10 @@ dim3 fused_post_grid(int w, int h, int tile);
 // host copy.  Pair i of `pairs` runs on slot pairs.slot[i].
 elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, const VMap &pairs, int tile_rows,
                                  cudaStream_t st);
+// Census records (nbytes 32 or 16 per pixel) of the pairs, each with the
+// window of its own table entry.
+elas_status launch_census_b(const CensusArgs *tab, const CensusArgs *host, const VMap &pairs, int nbytes,
+                            cudaStream_t st);
 elas_status launch_support_b(const SupportTables &t, const SupportStage *host, const VMap &pairs, int match_warps,
                              cudaStream_t st);
 // counter: one device int, the CTA pass's queue position.

@@ -521,9 +521,6 @@ extern "C" elas_status elas_server_submit(elas_server *s, uint64_t id, int32_t w
     if (!s || !p || !imgL || !imgR || !dL) return fail(ELAS_ERR_INVALID_ARG, "NULL argument");
     elas_status e = check_params(p, w, h);
     if (e != ELAS_OK) return e;
-    if (p->census_support_w != 0 || p->support_downsample > 1)
-        return fail(ELAS_ERR_INVALID_ARG,
-                    "the census variant and support down-sampling run through the per-pair calls and the pipeline only");
     if (w < p->candidate_stepsize || h < p->candidate_stepsize)
         return fail(ELAS_ERR_INVALID_ARG, "%dx%d has no lattice candidate at step %d", w, h, p->candidate_stepsize);
     Request *r = new (std::nothrow) Request();

@@ -21,7 +21,7 @@ struct Carve {
 
 struct Layout {
     uint8_t *img;
-    uint8_t *descL, *descR;
+    uint8_t *descL, *descR, *sdescL, *sdescR;
     int16_t *dcan, *list;
     uint32_t *gridL, *gridR;
     int32_t *tri;
@@ -42,6 +42,9 @@ Layout layout(char *base, int w, int h, const elas_params *p) {
     l.img = c.take<uint8_t>(2 * align_up(npx, 256));
     l.descL = c.take<uint8_t>(npx * 16);
     l.descR = c.take<uint8_t>(npx * 16);
+    const bool census = p->census_support_w > 0;  // 32-byte support census records
+    l.sdescL = census ? c.take<uint8_t>(npx * 32) : nullptr;
+    l.sdescR = census ? c.take<uint8_t>(npx * 32) : nullptr;
     l.dcan = c.take<int16_t>((size_t)nc * 2 + 16);
     l.list = c.take<int16_t>((size_t)nc * 6 + 16);
     l.gridL = c.take<uint32_t>(gbytes);
@@ -122,9 +125,6 @@ elas_status SlotPool::wait_mirror() {
 elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStream_t alloc_stream) {
     elas_status s = check_params(p, w, h);
     if (s != ELAS_OK) return s;
-    if (p->census_support_w != 0 || p->support_downsample > 1)
-        return fail(ELAS_ERR_INVALID_ARG,
-                    "the census variant and support down-sampling run through the per-pair calls and the pipeline only");
     if (w < p->candidate_stepsize || h < p->candidate_stepsize)
         return fail(ELAS_ERR_INVALID_ARG, "%dx%d has no lattice candidate at step %d", w, h, p->candidate_stepsize);
     int k = -1;
@@ -160,6 +160,8 @@ elas_status SlotPool::add(int w, int h, const elas_params *p, int *id, cudaStrea
     sl.img = l.img;
     sl.descL = l.descL;
     sl.descR = l.descR;
+    sl.sdescL = l.sdescL;
+    sl.sdescR = l.sdescR;
     sl.dcan = l.dcan;
     sl.list = l.list;
     sl.gridL = l.gridL;
@@ -212,8 +214,15 @@ elas_status SlotPool::write_records(int id) {
     const elas_params *p = &sl.p;
     t.desc = DescArgs{sl.io_imgL, sl.io_imgR, w, h, sl.io_pitch, reinterpret_cast<uint4 *>(sl.descL),
                       reinterpret_cast<uint4 *>(sl.descR)};
-    elas_status s0 = support_args(sl.descL, sl.descR, w, h, p, sl.dcan, sl.list, sl.counters, sl.gridL, sl.gridR,
-                                  sl.ws_support, &t.sup);
+    const bool census = p->census_support_w > 0;
+    if (census) {
+        t.cs = CensusArgs{sl.io_imgL, sl.io_imgR, w, h, sl.io_pitch, reinterpret_cast<uint4 *>(sl.sdescL),
+                          reinterpret_cast<uint4 *>(sl.sdescR), p->census_support_w};
+        t.cd = CensusArgs{sl.io_imgL, sl.io_imgR, w, h, sl.io_pitch, reinterpret_cast<uint4 *>(sl.descL),
+                          reinterpret_cast<uint4 *>(sl.descR), p->census_dense_w};
+    }
+    elas_status s0 = support_args(census ? sl.sdescL : sl.descL, census ? sl.sdescR : sl.descR, w, h, p, sl.dcan,
+                                  sl.list, sl.counters, sl.gridL, sl.gridR, sl.ws_support, &t.sup);
     if (s0 != ELAS_OK) return s0;
     int32_t *tris[2] = {sl.tri, sl.tri + 3 * (size_t)sl.tri_cap};
     int32_t *nts[2] = {sl.counters + 1, sl.counters + 2};
@@ -277,13 +286,16 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     if (n > kMaxBatch) return fail(ELAS_ERR_CAPACITY, "%d pairs in one wave (at most %d)", n, kMaxBatch);
     if (dirty_hi_ >= dirty_lo_) return fail(ELAS_ERR_INTERNAL, "slot records changed without an upload");
     if (!counter) counter = dev_counters_ + 4 * ids[0] + 3;
-    VMap pairs;
+    VMap pairs, sobel, census;
     vmap_clear(pairs, (int)sizeof(SlotTables));
+    vmap_clear(sobel, (int)sizeof(SlotTables));
+    vmap_clear(census, (int)sizeof(SlotTables));
     int npass[kMaxBatch], fused[kMaxBatch];
     for (int i = 0; i < n; ++i) {
         const int id = ids[i];
         if (id < 0 || id >= (int)slots_.size() || !slots_[id].used) return fail(ELAS_ERR_INVALID_ARG, "slot %d", id);
         vmap_add(pairs, id, dim3(0));
+        vmap_add(slots_[id].p.census_support_w > 0 ? census : sobel, id, dim3(0));
         npass[i] = slots_[id].npass;
         fused[i] = slots_[id].fused;
     }
@@ -294,9 +306,12 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     const SlotTables *H = host_tab_;
     elas_status s;
     mark(0);
-    if ((s = launch_descriptors_b(&D->desc, &H->desc, pairs, k.desc_rows, st)) != ELAS_OK) return s;
+    if (sobel.n > 0 && (s = launch_descriptors_b(&D->desc, &H->desc, sobel, k.desc_rows, st)) != ELAS_OK) return s;
+    if (census.n > 0 && ((s = launch_census_b(&D->cs, &H->cs, census, 32, st)) != ELAS_OK ||
+                         (s = launch_census_b(&D->cd, &H->cd, census, 16, st)) != ELAS_OK))
+        return s;
     mark(1);
-    const SupportTables sup{&D->sup.match, &D->sup.cons, &D->sup.red, &D->sup.compact};
+    const SupportTables sup{&D->sup.match, &D->sup.cons, &D->sup.red, &D->sup.compact, &D->sup.lg};
     if ((s = launch_support_b(sup, &H->sup, pairs, k.support_warps, st)) != ELAS_OK) return s;
     mark(2);
     if ((s = launch_triangulate_b(&D->dt, &H->dt, pairs, 2, counter, st)) != ELAS_OK) return s;

@@ -26,6 +26,7 @@ struct Knobs {
 // The stage arguments of one slot, one record per slot in the tables.
 struct SlotTables {
     DescArgs desc;
+    CensusArgs cs, cd;  // the paper's variant: support and dense census records
     SupportStage sup;
     DtArgs dt;
     DenseStage dense;
@@ -42,7 +43,8 @@ struct Slot {
     char *mem = nullptr;  // one device allocation holding every buffer below
     size_t bytes = 0;
     uint8_t *img = nullptr;  // internal inputs: left then right plane
-    uint8_t *descL = nullptr, *descR = nullptr;
+    uint8_t *descL = nullptr, *descR = nullptr;  // descriptors, or the dense census records
+    uint8_t *sdescL = nullptr, *sdescR = nullptr;  // support census records (census slots only)
     int16_t *dcan = nullptr, *list = nullptr;
     uint32_t *gridL = nullptr, *gridR = nullptr;
     int32_t *tri = nullptr;

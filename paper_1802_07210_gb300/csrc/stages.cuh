@@ -14,6 +14,15 @@ struct DescArgs {
     uint4 *descL, *descR;
 };
 
+// Census records of one pair (Sec. VI.A): window x window comparisons in
+// 32-byte (support) or 16-byte (dense) records per pixel.
+struct CensusArgs {
+    const uint8_t *imgL, *imgR;
+    int w, h, pitch;
+    uint4 *outL, *outR;
+    int window;
+};
+
 // ---- support points ---------------------------------------------------------
 struct SupportArgs {
     int w, h, step, wc, hc;
@@ -70,18 +79,21 @@ struct ListGridArgs {
     uint32_t *gridL, *gridR;
 };
 
-// The four launches of the support stage for one pair, and their tables.
+// The launches of the support stage for one pair, and their tables (the
+// list-grid launch only with down-sampling).
 struct SupportStage {
     MatchArgs match;
     ConsArgs cons;
     RedArgs red;
     CompactArgs compact;
+    ListGridArgs lg;
 };
 struct SupportTables {
     const MatchArgs *match;
     const ConsArgs *cons;
     const RedArgs *red;
     const CompactArgs *compact;
+    const ListGridArgs *lg;
 };
 
 // ---- triangulation ----------------------------------------------------------

@@ -297,14 +297,16 @@ template <bool CENSUS> __device__ __forceinline__ void support_match_row_body(co
 template <bool CENSUS> __global__ void __launch_bounds__(512) support_match_row_kernel(MatchArgs m) {
     support_match_row_body<CENSUS>(m, vb_single());
 }
-// Batched launches carry Sobel descriptors only.
+// Batched launches: one launch per cost kind among the pairs.
+template <bool CENSUS>
 __global__ void __launch_bounds__(512) support_match_row_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    support_match_row_body<false>(slot_entry(tab, vm.stride, vb.slot), vb);
+    support_match_row_body<CENSUS>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
+template <bool CENSUS>
 __global__ void __launch_bounds__(512) support_match_kernel_b(const MatchArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    support_match_body<false>(slot_entry(tab, vm.stride, vb.slot), vb);
+    support_match_body<CENSUS>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 // Consistency filter on a 32x8 tile of candidates staged with its halo in
@@ -511,10 +513,10 @@ __global__ void __launch_bounds__(128) compact_rows_kernel(CompactArgs ca) { com
 // consistency kernel): each point ORs its {d-1, d, d+1} bits into the 3x3
 // cells around its cell, as the redundancy kernel does for every point
 // without down-sampling.
-__global__ void __launch_bounds__(128) list_grid_kernel(ListGridArgs a) {
+__device__ __forceinline__ void list_grid_body(const ListGridArgs &a, const VB &vb) {
     const int n = min(*a.count, a.cap);
     const GridArgs g = a.g;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    for (int k = vb.x * blockDim.x + threadIdx.x; k < n; k += vb.gx * blockDim.x) {
         const int u = a.list[3 * k], v = a.list[3 * k + 1], d = a.list[3 * k + 2];
         const int cy = v / g.G;
         for (int side = 0; side < 2; ++side) {
@@ -526,6 +528,11 @@ __global__ void __launch_bounds__(128) list_grid_kernel(ListGridArgs a) {
                     or_bits(grid + ((size_t)y * g.gw + x) * g.nw, d, g.dmin, g.dmax);
         }
     }
+}
+__global__ void __launch_bounds__(128) list_grid_kernel(ListGridArgs a) { list_grid_body(a, vb_single()); }
+__global__ void __launch_bounds__(128) list_grid_kernel_b(const ListGridArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    list_grid_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 __global__ void __launch_bounds__(128) compact_rows_kernel_b(const CompactArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
@@ -572,6 +579,8 @@ elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int 
                      GridArgs{a.step, p->grid_size, g.gw, g.gh, g.nw, a.dmin, a.dmax}, d_can, grid_L, grid_R,
                      rowcount, p->support_downsample > 1 ? 1 : 0};
     o->compact = CompactArgs{d_can, a.wc, a.hc, a.step, rowcount, list, count, p->support_downsample};
+    const int k = p->support_downsample > 1 ? p->support_downsample : 1;
+    o->lg = ListGridArgs{list, count, (nc + k - 1) / k, o->red.g, grid_L, grid_R};
     return ELAS_OK;
 }
 
@@ -664,11 +673,9 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
     compact_rows_kernel<<<lattice_row_grid(sa.compact.hc), 128, 0, st>>>(sa.compact);
     if ((s = launch_status("compact_rows_kernel")) != ELAS_OK) return s;
     if (sa.compact.keep_every <= 1) return ELAS_OK;
-    const int k = sa.compact.keep_every;
-    const ListGridArgs lg{list, count, (nc + k - 1) / k, sa.red.g, grid_L, grid_R};
-    int blocks = (lg.cap + 127) / 128;
+    int blocks = (sa.lg.cap + 127) / 128;
     if (blocks > sm_count() * 4) blocks = sm_count() * 4;
-    list_grid_kernel<<<blocks, 128, 0, st>>>(lg);
+    list_grid_kernel<<<blocks, 128, 0, st>>>(sa.lg);
     return launch_status("list_grid_kernel");
 }
 
@@ -678,33 +685,56 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
                              cudaStream_t st) {
     if (match_warps != 4 && match_warps != 8 && match_warps != 16)
         return fail(ELAS_ERR_INVALID_ARG, "support warps per CTA %d", match_warps);
-    VMap m_match, m_cons, m_rows;
-    size_t row_smem = 0, red_smem = 0;
-    vmap_clear(m_match, pairs.stride);
+    // matching: the pairs of each cost kind (descriptor SAD, census Hamming)
+    VMap m_match[2], m_krows[2], m_cons, m_rows, m_lg;
+    size_t row_smem[2] = {0, 0}, red_smem = 0;
+    for (int c = 0; c < 2; ++c) {
+        vmap_clear(m_match[c], pairs.stride);
+        vmap_clear(m_krows[c], pairs.stride);
+    }
     vmap_clear(m_cons, pairs.stride);
     vmap_clear(m_rows, pairs.stride);
+    vmap_clear(m_lg, pairs.stride);
     size_t cons_smem = 0;
     for (int i = 0; i < pairs.n; ++i) {
         const int slot = pairs.slot[i];
         const SupportStage &h = slot_entry(host, pairs.stride, slot);
         if (h.match.a.wc * h.match.a.hc == 0)
             return fail(ELAS_ERR_INVALID_ARG, "pair %d has no lattice candidate", i);
-        vmap_add(m_match, slot, support_match_grid(h.match, match_warps));
-        row_smem = max(row_smem, sup_row_smem(h.match.a.wc, h.match.a.dmin, h.match.a.dmax).total);
+        const int c = h.match.a.census ? 1 : 0;
+        vmap_add(m_match[c], slot, support_match_grid(h.match, match_warps));
+        vmap_add(m_krows[c], slot, lattice_row_grid(h.red.hc));
+        row_smem[c] = max(row_smem[c], sup_row_smem(h.match.a.wc, h.match.a.dmin, h.match.a.dmax).total);
         red_smem = max(red_smem, red_smem_bytes(h.red.wc, h.red.maxd, h.red.g.gw, h.red.g.nw));
         vmap_add(m_cons, slot, consistency_grid(h.cons));
         vmap_add(m_rows, slot, lattice_row_grid(h.red.hc));
         cons_smem = cons_smem > consistency_smem(h.cons.r) ? cons_smem : consistency_smem(h.cons.r);
+        if (h.compact.keep_every > 1)
+            vmap_add(m_lg, slot, dim3(max(1, min((h.lg.cap + 127) / 128, sm_count() * 4 / pairs.n + 1))));
     }
     if (pairs.n == 0) return ELAS_OK;
     elas_status s;
-    if (row_smem <= kSupRowSmemMax && vmap_total(m_rows) >= sup_row_min_rows()) {
-        if ((s = sup_row_smem_attr((const void *)support_match_row_kernel_b, row_smem)) != ELAS_OK) return s;
-        support_match_row_kernel_b<<<vmap_total(m_rows), 32 * match_warps, row_smem, st>>>(t.match, m_rows);
-        if ((s = launch_status("support_match_row_kernel_b")) != ELAS_OK) return s;
-    } else {
-        support_match_kernel_b<<<vmap_total(m_match), 32 * match_warps, 0, st>>>(t.match, m_match);
-        if ((s = launch_status("support_match_kernel_b")) != ELAS_OK) return s;
+    for (int c = 0; c < 2; ++c) {
+        if (m_match[c].n == 0) continue;
+        if (row_smem[c] <= kSupRowSmemMax && vmap_total(m_krows[c]) >= sup_row_min_rows()) {
+            const void *fn = c ? (const void *)support_match_row_kernel_b<true>
+                               : (const void *)support_match_row_kernel_b<false>;
+            if ((s = sup_row_smem_attr(fn, row_smem[c])) != ELAS_OK) return s;
+            if (c)
+                support_match_row_kernel_b<true>
+                    <<<vmap_total(m_krows[c]), 32 * match_warps, row_smem[c], st>>>(t.match, m_krows[c]);
+            else
+                support_match_row_kernel_b<false>
+                    <<<vmap_total(m_krows[c]), 32 * match_warps, row_smem[c], st>>>(t.match, m_krows[c]);
+            if ((s = launch_status("support_match_row_kernel_b")) != ELAS_OK) return s;
+        } else {
+            if (c)
+                support_match_kernel_b<true><<<vmap_total(m_match[c]), 32 * match_warps, 0, st>>>(t.match, m_match[c]);
+            else
+                support_match_kernel_b<false><<<vmap_total(m_match[c]), 32 * match_warps, 0, st>>>(t.match,
+                                                                                                  m_match[c]);
+            if ((s = launch_status("support_match_kernel_b")) != ELAS_OK) return s;
+        }
     }
     if ((s = consistency_smem_attr((const void *)consistency_kernel_b, cons_smem)) != ELAS_OK) return s;
     consistency_kernel_b<<<vmap_total(m_cons), dim3(kConsTX, kConsTY), cons_smem, st>>>(t.cons, m_cons);
@@ -715,7 +745,11 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
     redundancy_grid_kernel_b<<<vmap_total(m_rows), 128, red_smem, st>>>(t.red, m_rows, red_staged);
     if ((s = launch_status("redundancy_grid_kernel_b")) != ELAS_OK) return s;
     compact_rows_kernel_b<<<vmap_total(m_rows), 128, 0, st>>>(t.compact, m_rows);
-    return launch_status("compact_rows_kernel_b");
+    if ((s = launch_status("compact_rows_kernel_b")) != ELAS_OK) return s;
+    // down-sampled pairs: grid vectors from the kept points
+    if (m_lg.n == 0) return ELAS_OK;
+    list_grid_kernel_b<<<vmap_total(m_lg), 128, 0, st>>>(t.lg, m_lg);
+    return launch_status("list_grid_kernel_b");
 }
 
 }  // namespace elas

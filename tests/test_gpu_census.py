@@ -1,8 +1,7 @@
 """Parity of the census variant (Sec. VI.A: census descriptors over full
 W x W windows, Hamming costs) with the CPU oracle through the C-ABI: the
 census records bit for bit, the support points (both matchers), the dense
-argmin and the whole one-pair pipeline; batches and the server refuse it."""
-import ctypes as C
+argmin and the whole one-pair pipeline (batches and the server: test_gpu_variants_batched.py)."""
 
 import numpy as np
 import pytest
@@ -130,15 +129,3 @@ def test_census_pipeline(refs, name):
             assert np.abs(host(post) - ref["post"]).max() <= 1e-4
     assert pl.stats()["n_support"] == len(ref["list"])
     pl.close()
-
-
-def test_census_refused_by_batches_and_the_server():
-    B = _B()
-    from paper_1802_07210_gb300 import _lib
-    prm = (_lib.Params * 1)(_lib.params(census_support_w=9, census_dense_w=5))
-    w = (C.c_int32 * 1)(64)
-    h = (C.c_int32 * 1)(48)
-    out = C.c_void_p()
-    assert _lib.lib().elas_batch_create(1, w, h, prm, C.byref(out)) == 1 and not out.value
-    assert b"census" in _lib.lib().elas_last_error()
-    del B

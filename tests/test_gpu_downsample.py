@@ -2,8 +2,7 @@
 extracted support points) with the oracle through the C-ABI: the candidate
 grid, the list and its count, the grid vectors, and the whole one-pair path,
 on the default lattice and on the every-pixel lattice the paper's variant
-extracts from; batches refuse it."""
-import ctypes as C
+extracts from (batches and the server: test_gpu_variants_batched.py)."""
 
 import numpy as np
 import pytest
@@ -75,13 +74,3 @@ def test_pipeline_downsampled(k):
             np.testing.assert_array_equal(host(dR), ref["lrR"])
         assert pl.stats()["n_support"] == len(ref["list"])
         pl.close()
-
-
-def test_downsampling_refused_by_batches():
-    from paper_1802_07210_gb300 import _lib
-    prm = (_lib.Params * 1)(_lib.params(support_downsample=8))
-    w = (C.c_int32 * 1)(64)
-    h = (C.c_int32 * 1)(48)
-    out = C.c_void_p()
-    assert _lib.lib().elas_batch_create(1, w, h, prm, C.byref(out)) == 1 and not out.value
-    assert b"down-sampling" in _lib.lib().elas_last_error()
