@@ -16,6 +16,8 @@ step.  The same line carries:
                (one launch per kernel for all pairs, CUDA graph, tuned tile
                shapes) against 64 runs of the plain path, with the batched
                dense kernel's roofline;
+  batch_census the same batch with the paper's census variant (9x9
+               support and 5x5 dense census windows, Hamming costs);
   mixed_batch  128 pairs of mixed sizes and disparity ranges in one wave
                against 128 plain runs;
   serving      8 simulated cameras with Poisson arrivals (600 pairs/s in
@@ -293,9 +295,14 @@ def pair_dense_evals(B, torch, wl, L, R, dev):
     return dense_work(work, prm, w, h)
 
 
-def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad, hbm, tune=True):
-    """64 x 1242x375 D=256 through one batched wave vs the plain path."""
+def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, peak_gsad, hbm, tune=True,
+                      overrides=None):
+    """64 x 1242x375 D=256 through one batched wave vs the plain path
+    (overrides: parameters of the paper's variant, without the dense
+    roofline)."""
     wl, cfg = synth.KITTI_1242, 3
+    if overrides:
+        wl = synth.Workload(wl.name, wl.spec, wl.disp_max, wl.postprocess, dict(wl.params, **overrides))
     w, h = wl.spec.w, wl.spec.h
     pool = [synth.workload_pair(wl, 500 + i, cfg)[:2] for i in range(distinct)]
     imgL = [torch.from_numpy(pool[i % distinct][0]).to(dev) for i in range(npairs)]
@@ -317,9 +324,15 @@ def run_batch_section(B, torch, dev, stream, flush, steps, npairs, distinct, pea
     ms_plain = _timed(torch, stream, flush, lambda i: [pl.run(imgL[k], imgR[k], dL[k], dR[k]) for k in range(npairs)],
                       max(3, steps // 3))
     pl.close()
+    t_b, t_p = float(np.mean(ms)), float(np.mean(ms_plain))
+    if overrides:
+        return {"workload": "%d x %s" % (npairs, wl.name), "parameters": overrides, "pairs": npairs,
+                "distinct_pairs": distinct, "ms_per_batch": t_b, "pairs_per_s": npairs / (t_b * 1e-3),
+                "mpix_per_s": npairs * w * h / (t_b * 1e-3) / 1e6, "plain_ms_per_batch": t_p,
+                "plain_pairs_per_s": npairs / (t_p * 1e-3), "speedup_vs_plain": t_p / t_b, "tuned": tuned,
+                "stages_ms": stage, "support_points_first": nsup[:4], "l2": "flushed before every timed batch"}
     evals = sum(pair_dense_evals(B, torch, wl, L, R, dev) for L, R in pool) * (npairs // distinct)
     evals += sum(pair_dense_evals(B, torch, wl, *pool[i], dev) for i in range(npairs % distinct))
-    t_b, t_p = float(np.mean(ms)), float(np.mean(ms_plain))
     roof = {"kernel": "cell_kernel_b (dense argmin, every pair and both reference images in one launch)"}
     roof.update(dense_roofline(evals, DENSE_MIN_BYTES_PER_PX * w * h * npairs, stage["dense_argmin"], peak_gsad,
                                hbm[0], hbm[1]))
@@ -842,6 +855,10 @@ def main():
             ("batch", lambda: run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
                                                 args.batch_pairs, args.batch_distinct, peak, (hbm_gbs, peak_kind),
                                                 tune=not args.no_tune)),
+            ("batch_census", lambda: run_batch_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
+                                                       args.batch_pairs, args.batch_distinct, peak,
+                                                       (hbm_gbs, peak_kind), tune=not args.no_tune,
+                                                       overrides=dict(census_support_w=9, census_dense_w=5))),
             ("mixed_batch", lambda: run_mixed_section(B, torch, dev, stream, flush, max(5, min(args.steps, 10)),
                                                       args.mixed_pairs, tune=not args.no_tune)),
             ("serving", lambda: run_serve_section(B, torch, args.serve_seconds)),
@@ -892,6 +909,10 @@ def summary(line):
                                     "dense_bound": b["roofline_dense"]["bound"],
                                     "dense_frac": b["roofline_dense"]["frac"],
                                     "dense_frac_alu": b["roofline_dense"]["alu"]["frac"]}
+    bc = line.get("batch_census", {})
+    if "pairs_per_s" in bc:
+        out["batch_census_9x9_5x5"] = {"pairs_per_s": bc["pairs_per_s"], "plain_pairs_per_s": bc["plain_pairs_per_s"],
+                                       "speedup": bc["speedup_vs_plain"]}
     m = line.get("mixed_batch", {})
     if "pairs_per_s" in m:
         out["mixed_128"] = {"pairs_per_s": m["pairs_per_s"], "plain_pairs_per_s": m["plain_pairs_per_s"],

@@ -103,19 +103,27 @@ __global__ void dt_points_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     dt_points_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-// One CTA per side: exclusive scan of the cell counts.
+// One CTA per side: exclusive scan of the cell counts, each thread taking
+// kCellScanItems consecutive cells of a chunk (their loads go out together).
 __device__ __forceinline__ void dt_cell_scan_body(const DtArgs &a, const VB &vb) {
+    constexpr int kCellScanItems = 4;
     __shared__ int s_w[32];
     __shared__ int s_carry;
     const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int ncell = dt_ncell(a);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int chunk = kCellScanItems * (int)blockDim.x;
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base <= ncell; base += 1024) {
-        const int i = base + tid;
-        const int v = i < ncell ? S.cell_cnt[i] : 0;
-        int incl = v;
+    for (int base = 0; base <= ncell; base += chunk) {
+        const int i0 = base + kCellScanItems * tid;
+        int v[kCellScanItems];
+#pragma unroll
+        for (int k = 0; k < kCellScanItems; ++k) v[k] = i0 + k < ncell ? S.cell_cnt[i0 + k] : 0;
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < kCellScanItems; ++k) tot += v[k];
+        int incl = tot;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
             if (lane >= o) incl += y;
@@ -123,7 +131,7 @@ __device__ __forceinline__ void dt_cell_scan_body(const DtArgs &a, const VB &vb)
         if (lane == 31) s_w[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            int x = s_w[lane];
+            int x = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
                 if (lane >= o) x += y;
@@ -131,10 +139,14 @@ __device__ __forceinline__ void dt_cell_scan_body(const DtArgs &a, const VB &vb)
             s_w[lane] = x;
         }
         __syncthreads();
-        const int excl = s_carry + (wid ? s_w[wid - 1] : 0) + incl - v;
-        if (i <= ncell) {
-            S.cell_start[i] = excl;
-            S.cell_fill[i] = excl;
+        int excl = s_carry + (wid ? s_w[wid - 1] : 0) + incl - tot;
+#pragma unroll
+        for (int k = 0; k < kCellScanItems; ++k) {
+            if (i0 + k <= ncell) {  // entry ncell receives the total
+                S.cell_start[i0 + k] = excl;
+                S.cell_fill[i0 + k] = excl;
+            }
+            excl += v[k];
         }
         __syncthreads();
         if (tid == 0) s_carry += s_w[31];
@@ -1113,17 +1125,26 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM)
 
 // One CTA per side: exclusive scan of the owned counts, total = ntri.
 __device__ __forceinline__ void dt_tri_scan_body(const DtArgs &a, const VB &vb) {
+    // each thread scans kScanItems consecutive counts of a chunk (their loads
+    // go out together), then the threads' totals are scanned across the CTA
+    constexpr int kScanItems = 8;
     __shared__ int s_w[32];
     __shared__ int s_carry;
     const DtSide S = vb.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int chunk = kScanItems * (int)blockDim.x;
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += 1024) {
-        const int i = base + tid;
-        const int v = i < n ? S.owned[i] : 0;
-        int incl = v;
+    for (int base = 0; base < n; base += chunk) {
+        const int i0 = base + kScanItems * tid;
+        int v[kScanItems];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = i0 + k < n ? S.owned[i0 + k] : 0;
+        int tot = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) tot += v[k];
+        int incl = tot;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
             if (lane >= o) incl += y;
@@ -1131,7 +1152,7 @@ __device__ __forceinline__ void dt_tri_scan_body(const DtArgs &a, const VB &vb) 
         if (lane == 31) s_w[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            int x = s_w[lane];
+            int x = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
                 if (lane >= o) x += y;
@@ -1139,7 +1160,12 @@ __device__ __forceinline__ void dt_tri_scan_body(const DtArgs &a, const VB &vb) 
             s_w[lane] = x;
         }
         __syncthreads();
-        if (i < n) S.offset[i] = s_carry + (wid ? s_w[wid - 1] : 0) + incl - v;
+        int run = s_carry + (wid ? s_w[wid - 1] : 0) + incl - tot;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < n) S.offset[i0 + k] = run;
+            run += v[k];
+        }
         __syncthreads();
         if (tid == 0) s_carry += s_w[31];
         __syncthreads();

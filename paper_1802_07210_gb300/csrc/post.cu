@@ -365,12 +365,38 @@ extern "C" elas_status elas_postprocess(const int16_t *d, int32_t w, int32_t h, 
 // invalid pixels stay -1.  A 32x8 tile with its halo in shared memory (cells
 // outside the image read -1, so they drop out as invalid values).  For a
 // 3x3 window the nine values are sorted in registers by odd-even
-// transposition (invalid -1 first); for larger ones the median is found by
-// rank: the window value v with #{values < v} <= (n-1)/2 < #{values <= v}.
+// transposition (invalid -1 first); for larger ones the window is loaded
+// into registers and the median is selected bit by bit: disparities are
+// below 1024, so from bit 9 down, the count of valid values that share the
+// bits chosen so far and have a 0 at the current bit decides that bit of the
+// k-th smallest value (k = (n-1)/2).
 // ---------------------------------------------------------------------------
 namespace elas {
 
 constexpr int kMedTX = 32, kMedTY = 8, kMedMaxR = 3;
+
+template <int R> __device__ __forceinline__ int median_select(const int16_t *c, int SW) {
+    constexpr int N = (2 * R + 1) * (2 * R + 1);
+    int v[N];
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        v[j] = c[(j / (2 * R + 1) - R) * SW + (j % (2 * R + 1) - R)];
+        n += v[j] >= 0;
+    }
+    int k = (n - 1) / 2, val = 0;
+#pragma unroll
+    for (int b = 9; b >= 0; --b) {
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) cnt += (v[j] >= 0) & ((v[j] >> b) == (val >> b));
+        if (k >= cnt) {
+            k -= cnt;
+            val |= 1 << b;
+        }
+    }
+    return val;
+}
 
 __global__ void __launch_bounds__(kMedTX *kMedTY) median_kernel(const int16_t *__restrict__ d, int w, int h, int r,
                                                                 int16_t *__restrict__ out) {
@@ -409,22 +435,7 @@ __global__ void __launch_bounds__(kMedTX *kMedTY) median_kernel(const int16_t *_
         for (int j = 0; j < 9; ++j)
             if (j == m) res = v[j];
     } else if (c[0] >= 0) {
-        int n = 0;
-        for (int dy = -r; dy <= r; ++dy)
-            for (int dx = -r; dx <= r; ++dx) n += c[dy * SW + dx] >= 0;
-        const int k = (n - 1) / 2;
-        for (int j = 0; j < (2 * r + 1) * (2 * r + 1) && res < 0; ++j) {
-            const int vj = c[(j / (2 * r + 1) - r) * SW + (j % (2 * r + 1) - r)];
-            if (vj < 0) continue;
-            int lt = 0, le = 0;
-            for (int dy = -r; dy <= r; ++dy)
-                for (int dx = -r; dx <= r; ++dx) {
-                    const int q = c[dy * SW + dx];
-                    lt += q >= 0 && q < vj;
-                    le += q >= 0 && q <= vj;
-                }
-            if (lt <= k && k < le) res = vj;
-        }
+        res = r == 0 ? c[0] : (r == 2 ? median_select<2>(c, SW) : median_select<3>(c, SW));
     }
     out[(size_t)y * w + x] = (int16_t)res;
 }

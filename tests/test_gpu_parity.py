@@ -236,11 +236,12 @@ def test_median_filter(size):
     B = _B()
     w, h = size
     rng = np.random.default_rng(w * h)
-    d = rng.integers(-1, 90, size=(h, w)).astype(np.int16)
-    d[rng.random((h, w)) < 0.2] = -1
-    for r in range(4):
-        out = host(B.elas_median(dev(d), r))
-        np.testing.assert_array_equal(out, oracle.median(d, r), err_msg="radius %d" % r)
+    for top in (90, 1024):  # small values, and the whole range of disparities (kMaxDisp 1023)
+        d = rng.integers(-1, top, size=(h, w)).astype(np.int16)
+        d[rng.random((h, w)) < 0.2] = -1
+        for r in range(4):
+            out = host(B.elas_median(dev(d), r))
+            np.testing.assert_array_equal(out, oracle.median(d, r), err_msg="radius %d values < %d" % (r, top))
 
 
 def test_median_filter_on_a_disparity_map(pairs):
