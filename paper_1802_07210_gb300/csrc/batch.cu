@@ -140,7 +140,7 @@ bool knob_ok(const Knobs &k) {
     return (k.desc_rows == 4 || k.desc_rows == 8 || k.desc_rows == 16) &&
            (k.support_warps == 4 || k.support_warps == 8 || k.support_warps == 16) &&
            (k.dense_tpp == 1 || k.dense_tpp == 2 || k.dense_tpp == 4) &&
-           (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8);
+           (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8 || k.dense_ppt == 16);
 }
 
 }  // namespace
@@ -288,7 +288,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
     Axis axes[4] = {{&k.desc_rows, 0, {4, 8, 16}},
                     {&k.support_warps, 1, {4, 8, 16}},
                     {&k.dense_tpp, 4, {1, 2, 4}},
-                    {&k.dense_ppt, 4, {2, 4, 8}}};
+                    {&k.dense_ppt, 4, {4, 8, 16}}};
     const int reps = 3;
     for (Axis &ax : axes) {
         float best_ms = 1e30f;

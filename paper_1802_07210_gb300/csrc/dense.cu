@@ -600,7 +600,8 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
                            cudaStream_t st, cudaEvent_t after_prior) {
     if (pairs.n == 0) return ELAS_OK;
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
-    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return fail(ELAS_ERR_INVALID_ARG, "dense pixels per thread %d", ppt);
+    if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8 && ppt != 16)
+        return fail(ELAS_ERR_INVALID_ARG, "dense pixels per thread %d", ppt);
     VMap m_init, m_tri, m_big, m_cell[2];
     vmap_clear(m_init, pairs.stride);
     vmap_clear(m_tri, pairs.stride);

@@ -169,7 +169,7 @@ def test_tuner_picks_valid_knobs(mix):
     assert cfg["desc_tile_rows"] in (4, 8, 16)
     assert cfg["support_warps"] in (4, 8, 16)
     assert cfg["dense_threads_per_pixel"] in (1, 2, 4)
-    assert cfg["dense_pixels_per_thread"] in (1, 2, 4, 8)
+    assert cfg["dense_pixels_per_thread"] in (1, 2, 4, 8, 16)
     assert b.config()["desc_tile_rows"] == cfg["desc_tile_rows"]
     b.run(imgL, imgR, dL, dR, post)
     _check(mix, dL, dR, post, "tuned")
