@@ -14,10 +14,11 @@
 //      the symbolic tie-break: a strict total order, so a warp min-reduction
 //      finds it); continue with (p, b) until the star closes at a0 or no
 //      point is left of the edge (p on the hull), then wrap clockwise from a0.
-// Pass 1 (a group of 8 lanes per point) lists the points within 32 pixels
-// of p from a 16-pixel grid and wraps the star among them with the pencil
-// key; it is accepted when every triangle's circumdisc lies inside that disc
-// (4 r^2 <= 32^2 in exact arithmetic, so no farther point can matter) and,
+// Pass 1 (a group of 16 lanes per point, 4 in batches) lists the points
+// within R = 24 pixels (18 in batches) of p from a 16-pixel grid and wraps
+// the star among them with the pencil key; it is accepted when every
+// triangle's circumdisc lies inside that disc (4 r^2 <= R^2 in exact
+// arithmetic, so no farther point can matter) and,
 // where the star stays open (p on the hull), nothing lies beyond either open
 // edge (checked against the extreme points of every image row).  The other
 // stars go through the same group pass once more with one warp per star and
@@ -335,7 +336,7 @@ __device__ __forceinline__ bool dt_key_better(const DtKey<T> &k1, const DtKey<T>
 // (4 r^2 <= R^2, exact) and, for an open star (p on the hull), nothing lies
 // beyond either open edge (checked against the extreme points of every image
 // row).  Other stars are queued for the next pass.
-constexpr int kDtGroup = 8;       // lanes per star in batched launches (issue-bound: less divergence waste)
+constexpr int kDtGroup = 4;       // lanes per star in batched launches (issue-bound: less divergence waste)
 constexpr int kDtGroupOne = 16;   // lanes per star for one pair (latency-bound: shorter star chains)
 constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (a radius-24 disc holds at most ~75 lattice points at step 5)
