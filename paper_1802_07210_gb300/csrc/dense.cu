@@ -2,9 +2,10 @@
 // dense per-pixel argmin of descriptor SAD plus tabulated prior over the
 // grid-vector and plane-neighbourhood candidates (Sec. III.A, Fig. 1(h)).
 //
-// plane_raster_kernel  eight lanes per triangle (grid-stride), both meshes in
-//                      one launch.  Every lane evaluates the FP32 plane in
-//                      the fixed order.  The lanes tile the bounding box
+// plane_raster_kernel  eight lanes per triangle (four in batches of two or
+//                      more pairs; grid-stride), both meshes in one launch.
+//                      Every lane evaluates the FP32 plane in the fixed
+//                      order.  The lanes tile the bounding box
 //                      (up to eight across x, the rest over rows) and
 //                      write a pixel when the three integer edge functions
 //                      own it (E >= 0 on owned edges, E >= 1 otherwise), so
@@ -68,7 +69,7 @@ __device__ __forceinline__ int side_ntri(const RasterSide &S) {
 // bounding-box pixels above which a triangle is "big": one pair (latency:
 // shorter tails in the small-triangle kernel) and batches (throughput)
 constexpr int kBigAreaOne = 384;
-constexpr int kBigAreaBatch = 1024;
+constexpr int kBigAreaBatch = 2048;
 
 // Plane and positively oriented integer edges of one triangle.
 struct TriGeom {
@@ -172,16 +173,17 @@ __device__ __forceinline__ void raster_box(const TriGeom &g, int gl, int w, int 
     }
 }
 
-constexpr int kRasterGroup = 8;  // lanes per small triangle
-constexpr int kBigSplit = 8;      // CTAs a big triangle is spread over, at most
+constexpr int kRasterGroup = 8;       // lanes per small triangle (one pair: shorter chains)
+constexpr int kRasterGroupBatch = 4;  // lanes per small triangle in batches (more triangles in flight)
+constexpr int kBigSplit = 8;          // CTAs a big triangle is spread over, at most
 
-__device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb, int big_area) {
+template <int RG> __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb, int big_area) {
     const int side = vb.y;
     const RasterSide S = side ? a.s[1] : a.s[0];
-    const int gl = threadIdx.x & (kRasterGroup - 1);
-    const int gpb = blockDim.x / kRasterGroup;  // triangles per CTA pass
+    const int gl = threadIdx.x & (RG - 1);
+    const int gpb = blockDim.x / RG;  // triangles per CTA pass
     const int ntri = side_ntri(S);
-    for (int t = vb.x * gpb + (int)threadIdx.x / kRasterGroup; t < ntri; t += vb.gx * gpb) {
+    for (int t = vb.x * gpb + (int)threadIdx.x / RG; t < ntri; t += vb.gx * gpb) {
         const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
         if (g.empty) continue;
         const int rows = g.ymax - g.ymin + 1;
@@ -194,17 +196,18 @@ __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB 
             }
             continue;
         }
-        raster_box<kRasterGroup>(g, gl, a.w, a.dmin, a.dmax, S.dplane);
+        raster_box<RG>(g, gl, a.w, a.dmin, a.dmax, S.dplane);
     }
 }
 
 __global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
-    plane_raster_body(a, vb_single(), kBigAreaOne);
+    plane_raster_body<kRasterGroup>(a, vb_single(), kBigAreaOne);
 }
+template <int RG>
 __global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *__restrict__ tab, VMap vm,
                                                              int big_area) {
     const VB vb = vb_batch(vm);
-    plane_raster_body(slot_entry(tab, vm.stride, vb.slot), vb, big_area);
+    plane_raster_body<RG>(slot_entry(tab, vm.stride, vb.slot), vb, big_area);
 }
 
 // Big triangles: each list entry is one of the nsub parts of a triangle, one
@@ -615,7 +618,7 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         const size_t n8 = ((size_t)d.raster.nsides * d.raster.w * d.raster.h + 7) / 8;
         vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)sm_count() * 4)));
         const int maxt = raster_max_ntri(d.raster);
-        const int wpb = 256 / kRasterGroup;
+        const int wpb = 256 / (pairs.n == 1 ? kRasterGroup : kRasterGroupBatch);
         int blocks = (maxt + wpb - 1) / wpb;
         if (pairs.n > 1) blocks = (blocks + 2) / 3;
         blocks = max(1, min(blocks, sm_count() * 16));
@@ -626,8 +629,10 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }
     raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
-    plane_raster_kernel_b<<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri,
-                                                             pairs.n == 1 ? kBigAreaOne : kBigAreaBatch);
+    if (pairs.n == 1)
+        plane_raster_kernel_b<kRasterGroup><<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri, kBigAreaOne);
+    else
+        plane_raster_kernel_b<kRasterGroupBatch><<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri, kBigAreaBatch);
     plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
