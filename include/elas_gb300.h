@@ -482,7 +482,7 @@ void elas_pipeline_destroy(elas_pipeline *pl);
  */
 typedef struct elas_batch elas_batch;
 typedef struct {
-    int32_t desc_tile_rows;          /* descriptor tile height: 4, 8, 16      */
+    int32_t desc_tile_rows;          /* descriptor rows per warp: 12, 24, 36  */
     int32_t support_warps;           /* candidates per support CTA: 4, 8, 16  */
     int32_t dense_threads_per_pixel; /* dense argmin threads per pixel: 1, 2, 4 */
     int32_t use_graph;               /* capture and replay a CUDA graph       */

@@ -137,7 +137,7 @@ elas_status run_bound(elas_batch *b, cudaStream_t st) {
 }
 
 bool knob_ok(const Knobs &k) {
-    return (k.desc_rows == 4 || k.desc_rows == 8 || k.desc_rows == 16) &&
+    return (k.desc_rows == 12 || k.desc_rows == 24 || k.desc_rows == 36) &&
            (k.support_warps == 4 || k.support_warps == 8 || k.support_warps == 16) &&
            (k.dense_tpp == 1 || k.dense_tpp == 2 || k.dense_tpp == 4) &&
            (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8 || k.dense_ppt == 16);
@@ -285,7 +285,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
         int values[3];
     };
     Knobs k = b->knobs;
-    Axis axes[4] = {{&k.desc_rows, 0, {4, 8, 16}},
+    Axis axes[4] = {{&k.desc_rows, 0, {12, 24, 36}},
                     {&k.support_warps, 1, {4, 8, 16}},
                     {&k.dense_tpp, 4, {1, 2, 4}},
                     {&k.dense_ppt, 4, {4, 8, 16}}};

@@ -45,7 +45,7 @@ elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, fl
 int64_t delaunay_points(const int32_t *x, const int32_t *y, int n, std::vector<int32_t> &tri);
 
 // ---- argument blocks (shared by one-pair and batched launches) --------------
-dim3 descriptor_grid(int w, int h, int two, int tile_rows);
+dim3 descriptor_grid(int w, int h, int two, int rows);
 elas_status support_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                          int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
                          void *ws, SupportStage *o);
@@ -69,7 +69,7 @@ dim3 fused_post_grid(int w, int h, int tile);
 // Tables are arrays of per-slot records `pairs.stride` bytes apart: `tab`
 // points at slot 0's entry on the device, `host` at the same entry of the
 // host copy.  Pair i of `pairs` runs on slot pairs.slot[i].
-elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, const VMap &pairs, int tile_rows,
+elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, const VMap &pairs, int rows,
                                  cudaStream_t st);
 // Census records (nbytes 32 or 16 per pixel) of the pairs, each with the
 // window of its own table entry.

@@ -17,7 +17,7 @@ namespace elas {
 
 // Tile shapes of the batched kernels (picked by the tuner).
 struct Knobs {
-    int desc_rows = 8;      // descriptor tile height: 4, 8, 16
+    int desc_rows = 24;     // image rows a descriptor warp walks: 12, 24, 36
     int support_warps = 8;  // lattice candidates (warps) per support CTA: 4, 8, 16
     int dense_tpp = 1;      // threads per pixel in the dense argmin: 1, 2, 4
     int dense_ppt = 4;      // pixels per thread (per pixel group) in the dense argmin: 1, 2, 4, 8

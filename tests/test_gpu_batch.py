@@ -138,12 +138,12 @@ def test_mixed_batch_equals_per_pair_path(mix):
 
 
 KNOBS = [
-    dict(desc_tile_rows=4, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=1),
-    dict(desc_tile_rows=16, support_warps=16, dense_threads_per_pixel=2, dense_pixels_per_thread=2),
-    dict(desc_tile_rows=8, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=1),
-    dict(desc_tile_rows=16, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=4),
-    dict(desc_tile_rows=4, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=4),
-    dict(desc_tile_rows=8, support_warps=16, dense_threads_per_pixel=1, dense_pixels_per_thread=8),
+    dict(desc_tile_rows=36, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=1),
+    dict(desc_tile_rows=24, support_warps=16, dense_threads_per_pixel=2, dense_pixels_per_thread=2),
+    dict(desc_tile_rows=12, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=1),
+    dict(desc_tile_rows=24, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=4),
+    dict(desc_tile_rows=36, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=4),
+    dict(desc_tile_rows=12, support_warps=16, dense_threads_per_pixel=1, dense_pixels_per_thread=8),
 ]
 
 
@@ -166,7 +166,7 @@ def test_tuner_picks_valid_knobs(mix):
     imgR = [dev(it["R"]) for it in mix]
     dL, dR, post = _alloc(mix)
     cfg = b.tune(imgL, imgR, dL)
-    assert cfg["desc_tile_rows"] in (4, 8, 16)
+    assert cfg["desc_tile_rows"] in (12, 24, 36)
     assert cfg["support_warps"] in (4, 8, 16)
     assert cfg["dense_threads_per_pixel"] in (1, 2, 4)
     assert cfg["dense_pixels_per_thread"] in (1, 2, 4, 8, 16)
