@@ -243,11 +243,22 @@ constexpr int kListPad = 16;  // padding entries (2047) after the candidate list
 // TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
 // every TPP-th candidate of its list and of its plane window and merge their
 // keys with shuffles (min is order free, so every TPP gives the same result).
-// Dense matching cost of two 16-byte descriptors: the SAD of Sobel
-// descriptors, or the Hamming distance of dense census records (Sec. VI.A).
-template <bool CENSUS> __device__ __forceinline__ int dense_cost(const uint4 &a, const uint4 &b) {
-    return CENSUS ? (int)ham16(a, b) : (int)sad16_vacc(a, b);
+// Dense matching cost of two 16-byte descriptors added to acc: the SAD of
+// Sobel descriptors, or the Hamming distance of dense census records
+// (Sec. VI.A).  acc carries the key bias and, in the plane neighbourhood, the
+// prior term, so the packed key is one multiply-add away.
+template <bool CENSUS> __device__ __forceinline__ int dense_cost(const uint4 &a, const uint4 &b, int acc) {
+    if (CENSUS) return acc + (int)ham16(a, b);
+    uint32_t s = sad4_vacc(a.x, b.x, (uint32_t)acc);
+    s = sad4_vacc(a.y, b.y, s);
+    s = sad4_vacc(a.z, b.z, s);
+    return (int)sad4_vacc(a.w, b.w, s);
 }
+
+// Packed key of a candidate: (cost + bias) * kKeyMul + d orders by (cost, d)
+// as d <= kMaxDisp < kKeyMul; the multiplier is not a power of two so that
+// the packing stays one integer multiply-add.
+constexpr int kKeyMul = 2047;
 
 template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + kListPad];
@@ -267,11 +278,16 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
     const uint4 *__restrict__ oth = S.oth;
     const int dir = S.dir;
 
+    // the key bias with the prior term (none with the prior switched off)
+    if (tid <= kMaxSradius) s_P[tid] = kKeyBias + (a.prior_off ? 0 : a.P[tid]);
     // ---- candidate list of the cell, ascending ---------------------------------
-    if (tid <= kMaxSradius) s_P[tid] = a.P[tid];
     if (!full && warp == 0) {
         const int nw = a.nw;
         const uint32_t *g = S.grid + (size_t)cell * nw;
+        // the words are taken one at a time: lane l places bit l of the word
+        // after the set bits below it, so the list comes out sorted with no
+        // per-lane bit loop
+        const uint32_t below = (1u << lane) - 1u;
         int base = 0;
         for (int w0 = 0; w0 < nw; w0 += 32) {
             const int wi = w0 + lane;
@@ -280,19 +296,12 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
             const int lo = dmin - 32 * wi, hi = dmax - 32 * wi;
             if (lo > 0) m &= lo >= 32 ? 0u : (0xFFFFFFFFu << lo);
             if (hi < 31) m &= hi < 0 ? 0u : (0xFFFFFFFFu >> (31 - hi));
-            const int c = __popc(m);
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
+            const int nk = min(32, nw - w0);
+            for (int k = 0; k < nk; ++k) {
+                const uint32_t mk = __shfl_sync(0xFFFFFFFFu, m, k);
+                if ((mk >> lane) & 1u) s_list[base + __popc(mk & below)] = (uint16_t)(32 * (w0 + k) + lane);
+                base += __popc(mk);
             }
-            int pos = base + incl - c;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                s_list[pos++] = (uint16_t)(32 * wi + b);
-            }
-            base += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         // pad with a disparity above every dmax
         if (lane < kListPad) s_list[base + lane] = (uint16_t)2047;
@@ -332,8 +341,7 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
                     const uint4 *orow = oth + row + x;
                     if (full) {
                         for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
-                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d));
-                            best = min(best, ((c + kKeyBias) << 11) | d);
+                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                         }
                     } else {
                         // the admissible entries are a prefix of the ascending list
@@ -352,16 +360,13 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
 #pragma unroll 8
                         for (int k = sub; k < cnt; k += TPP) {
                             const int d = s_list[k];
-                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d));
-                            best = min(best, ((c + kKeyBias) << 11) | d);
+                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                         }
+                        // the plane neighbourhood, the prior term in the accumulator
                         const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
-                        const int pmask = a.prior_off ? 0 : -1;  // prior term on or off
 #pragma unroll 5
-                        for (int d = lo + sub; d <= hi; d += TPP) {
-                            const int c = dense_cost<CENSUS>(r, __ldg(orow + dir * d)) + (s_P[abs(d - dp)] & pmask);
-                            best = min(best, ((c + kKeyBias) << 11) | d);
-                        }
+                        for (int d = lo + sub; d <= hi; d += TPP)
+                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), s_P[abs(d - dp)]) * kKeyMul + d);
                     }
                 }
             }
@@ -370,7 +375,7 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
         }
-        if (live && sub == 0) S.out[row + x] = (int16_t)(best != 0x7FFFFFFF ? (best & 2047) : -1);
+        if (live && sub == 0) S.out[row + x] = (int16_t)(best != 0x7FFFFFFF ? (best % kKeyMul) : -1);
         px += sdx;
         py += sdy;
         if (px >= cw) {
