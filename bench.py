@@ -52,7 +52,7 @@ WORKLOADS = {"vga_640": (synth.VGA_640, 2), "small_320": (synth.SMALL_320, 1),
 # kernels of one plain step: descriptors 1; support 4 (match, consistency,
 # redundancy + grids, compaction); triangulation 10 (init, points, cell scan,
 # scatter, dedup, group pass, CTA pass, triangle scan, emit, emit big); plane
-# prior 3 (init, raster, big triangles); dense 1; LR 1; post-processing 1
+# prior 3 (setup, extra-unit list, draw); dense 1; LR 1; post-processing 1
 # (fused) or 0.  No memsets.
 KERNELS_PER_STEP = {True: 21, False: 20}
 STAGES = ("descriptors", "support", "triangulation", "plane_prior", "dense_argmin", "lr_post")

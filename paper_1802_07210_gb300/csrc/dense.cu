@@ -2,21 +2,24 @@
 // dense per-pixel argmin of descriptor SAD plus tabulated prior over the
 // grid-vector and plane-neighbourhood candidates (Sec. III.A, Fig. 1(h)).
 //
-// plane_raster_kernel  eight lanes per triangle (four in batches of two or
-//                      more pairs; grid-stride), both meshes in one launch.
-//                      Every lane evaluates the FP32 plane in the fixed
-//                      order.  The lanes tile the bounding box
-//                      (up to eight across x, the rest over rows) and
-//                      write a pixel when the three integer edge functions
-//                      own it (E >= 0 on owned edges, E >= 1 otherwise), so
-//                      ownership is exactly the top-left rule.  Triangles
-//                      whose bounding box exceeds kBigAreaOne (one pair) or
-//                      kBigAreaBatch pixels are listed
-//                      instead (in up to kBigSplit parts) and drawn by
-//                      plane_raster_big_kernel, one CTA per part (rows over
-//                      warps, lanes across x; there the owned x-range of a
-//                      row, widened by one, follows from the edge functions
-//                      first), so they leave no tail.
+// The prior is drawn in three launches:
+// raster_setup_kernel  fills the maps with -1 and, one thread per triangle,
+//                      writes a 64-byte record: the plane in the fixed FP32
+//                      order, the three integer edge functions with the
+//                      top-left rule folded into their constants, and the
+//                      pixel bounding box; and the triangle's count of
+//                      kUnitPx-pixel chunks of that box; it also clears the
+//                      mesh's count of extra units;
+// raster_list_kernel   one thread per triangle: the chunks after the first
+//                      of a box go to the mesh's list of extra units (one
+//                      atomicAdd per triangle of more than one chunk);
+// raster_draw_kernel   one warp per unit (grid-stride; unit t < ntri is
+//                      the first chunk of triangle t, the rest come from the
+//                      list), its lanes on 32 pixels of the box at a time: a
+//                      pixel owned by the triangle (at most one owner: the
+//                      top-left rule) takes clamp(floor(plane + 0.5)).  A
+//                      full list makes the warp of a triangle's first chunk
+//                      draw the whole box instead.
 // cell_kernel          one CTA per grid-vector cell (G x G pixels, which share
 //                      one candidate mask) and per reference image.  It
 //                      expands the cell's mask into an ascending candidate
@@ -38,50 +41,31 @@ __device__ __forceinline__ bool edge_owned(int px, int py, int qx, int qy) {
     return (qy == py && qx > px) || (qy < py);
 }
 
-__device__ __forceinline__ int floor_div(int n, int d) {  // d > 0
-    const int q = n / d;
-    return (n % d != 0 && n < 0) ? q - 1 : q;
-}
-__device__ __forceinline__ int ceil_div(int n, int d) {  // d > 0
-    const int q = n / d;
-    return (n % d != 0 && n > 0) ? q + 1 : q;
-}
-
-// Narrows [lo, hi] to the x where edge (px,py)->(qx,qy) admits row y.
-__device__ __forceinline__ void edge_span(int px, int py, int qx, int qy, int own, int y, int &lo, int &hi) {
-    const int A = py - qy;
-    const int B = (qx - px) * (y - py) + (qy - py) * px;
-    const int t = own ? 0 : 1;
-    if (A > 0)
-        lo = max(lo, ceil_div(t - B, A));
-    else if (A < 0)
-        hi = min(hi, floor_div(B - t, -A));
-    else if (B < t)
-        hi = lo - 1;
-}
-
-
 __device__ __forceinline__ int side_ntri(const RasterSide &S) {
     return S.ntri_dev ? max(0, *S.ntri_dev) : S.ntri;
 }
 
+constexpr int kUnitPx = 256;  // pixels of a triangle's bounding box per work unit
 
-// bounding-box pixels above which a triangle is "big": one pair (latency:
-// shorter tails in the small-triangle kernel) and batches (throughput)
-constexpr int kBigAreaOne = 384;
-constexpr int kBigAreaBatch = 2048;
-
-// Plane and positively oriented integer edges of one triangle.
-struct TriGeom {
-    float fa, fb, fc;
-    int ex0, ey0, ex1, ey1, ex2, ey2, o0, o1, o2;
+// Rasteriser record of one triangle: pixel (x, y) is owned iff
+// A[k] x + B[k] y + C[k] > 0 for k = 0, 1, 2 (the edge function of edge k,
+// positively oriented, plus 1 on an owned edge, so E >= 0 there and E >= 1
+// elsewhere), and then d_plane = clamp(floor((fa x + fb y) + fc + 0.5)).
+// A degenerate triangle (det = 0) gets A = B = C = 0: it owns nothing.
+struct TriBox {
     int xmin, xmax, ymin, ymax;
-    bool empty;
 };
+struct TriRec {
+    int A[3], B[3], C[3];
+    float fa, fb, fc;
+};
+constexpr int kRecWords = 4;  // 16-byte words of a stored record: edges, plane, box
 
-__device__ __forceinline__ TriGeom tri_geom(const int16_t *__restrict__ list, const int32_t *__restrict__ tri, int t,
-                                            int right, int w, int h) {
-    TriGeom g;
+// Plane and edge record of triangle t (vertices taken in ascending list
+// index), and its pixel bounding box clipped to the image (empty: xmax <
+// xmin).
+__device__ __forceinline__ TriRec tri_record(const int16_t *__restrict__ list, const int32_t *__restrict__ tri, int t,
+                                             int right, int w, int h, TriBox &box) {
     int i0 = __ldg(tri + 3 * t), i1 = __ldg(tri + 3 * t + 1), i2 = __ldg(tri + 3 * t + 2);
     // canonical vertex order: ascending list index
     if (i1 < i0) { const int q = i0; i0 = i1; i1 = q; }
@@ -100,149 +84,159 @@ __device__ __forceinline__ TriGeom tri_geom(const int16_t *__restrict__ list, co
     const int det = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
     const int na = (Z[1] - Z[0]) * (Y[2] - Y[0]) - (Z[2] - Z[0]) * (Y[1] - Y[0]);
     const int nb = (X[1] - X[0]) * (Z[2] - Z[0]) - (X[2] - X[0]) * (Z[1] - Z[0]);
-    g.empty = det == 0;
+    TriRec r;
     const float fdet = __int2float_rn(det == 0 ? 1 : det);
-    g.fa = __fdiv_rn(__int2float_rn(na), fdet);
-    g.fb = __fdiv_rn(__int2float_rn(nb), fdet);
-    const float c = __fsub_rn(__int2float_rn(Z[0]), __fmul_rn(g.fa, __int2float_rn(X[0])));
-    g.fc = __fsub_rn(c, __fmul_rn(g.fb, __int2float_rn(Y[0])));
-    g.ex0 = X[0];
-    g.ey0 = Y[0];
-    g.ex1 = det > 0 ? X[1] : X[2];
-    g.ey1 = det > 0 ? Y[1] : Y[2];
-    g.ex2 = det > 0 ? X[2] : X[1];
-    g.ey2 = det > 0 ? Y[2] : Y[1];
-    g.o0 = edge_owned(g.ex0, g.ey0, g.ex1, g.ey1);
-    g.o1 = edge_owned(g.ex1, g.ey1, g.ex2, g.ey2);
-    g.o2 = edge_owned(g.ex2, g.ey2, g.ex0, g.ey0);
-    g.xmin = max(0, min(X[0], min(X[1], X[2])));
-    g.xmax = min(w - 1, max(X[0], max(X[1], X[2])));
-    g.ymin = max(0, min(Y[0], min(Y[1], Y[2])));
-    g.ymax = min(h - 1, max(Y[0], max(Y[1], Y[2])));
-    if (g.xmax < g.xmin || g.ymax < g.ymin) g.empty = true;
-    return g;
-}
-
-// Writes the owned pixels of row y of a triangle, x from `first` in steps of
-// `stride` (lanes of a warp stride 32, a single thread strides 1).
-__device__ __forceinline__ void raster_row(const TriGeom &g, int y, int first, int stride, int w, int dmin, int dmax,
-                                           int16_t *__restrict__ dplane) {
-    int lo = g.xmin, hi = g.xmax;
-    edge_span(g.ex0, g.ey0, g.ex1, g.ey1, g.o0, y, lo, hi);
-    edge_span(g.ex1, g.ey1, g.ex2, g.ey2, g.o1, y, lo, hi);
-    edge_span(g.ex2, g.ey2, g.ex0, g.ey0, g.o2, y, lo, hi);
-    lo = max(g.xmin, lo - 1);
-    hi = min(g.xmax, hi + 1);
-    for (int x = lo + first; x <= hi; x += stride) {
-        const int e0 = (g.ex1 - g.ex0) * (y - g.ey0) - (g.ey1 - g.ey0) * (x - g.ex0);
-        const int e1 = (g.ex2 - g.ex1) * (y - g.ey1) - (g.ey2 - g.ey1) * (x - g.ex1);
-        const int e2 = (g.ex0 - g.ex2) * (y - g.ey2) - (g.ey0 - g.ey2) * (x - g.ex2);
-        if (!((e0 > 0 || (e0 == 0 && g.o0)) && (e1 > 0 || (e1 == 0 && g.o1)) && (e2 > 0 || (e2 == 0 && g.o2))))
-            continue;
-        const float t1 = __fmul_rn(g.fa, __int2float_rn(x));
-        const float t2 = __fmul_rn(g.fb, __int2float_rn(y));
-        const float mu = __fadd_rn(__fadd_rn(t1, t2), g.fc);
-        const int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
-        dplane[(size_t)y * w + x] = (int16_t)min(max(dp, dmin), dmax);
+    r.fa = __fdiv_rn(__int2float_rn(na), fdet);
+    r.fb = __fdiv_rn(__int2float_rn(nb), fdet);
+    const float c = __fsub_rn(__int2float_rn(Z[0]), __fmul_rn(r.fa, __int2float_rn(X[0])));
+    r.fc = __fsub_rn(c, __fmul_rn(r.fb, __int2float_rn(Y[0])));
+    // positively oriented vertex cycle (v0, v1, v2)
+    const int ex[3] = {X[0], det > 0 ? X[1] : X[2], det > 0 ? X[2] : X[1]};
+    const int ey[3] = {Y[0], det > 0 ? Y[1] : Y[2], det > 0 ? Y[2] : Y[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1;
+        // E(x, y) = (x1 - x0)(y - y0) - (y1 - y0)(x - x0) = A x + B y + C
+        const int A = ey[k] - ey[k1], B = ex[k1] - ex[k];
+        const int own = edge_owned(ex[k], ey[k], ex[k1], ey[k1]) ? 1 : 0;
+        r.A[k] = det == 0 ? 0 : A;
+        r.B[k] = det == 0 ? 0 : B;
+        r.C[k] = det == 0 ? 0 : own - A * ex[k] - B * ey[k];
     }
+    box.xmin = max(0, min(X[0], min(X[1], X[2])));
+    box.xmax = min(w - 1, max(X[0], max(X[1], X[2])));
+    box.ymin = max(0, min(Y[0], min(Y[1], Y[2])));
+    box.ymax = min(h - 1, max(Y[0], max(Y[1], Y[2])));
+    if (det == 0) box.xmax = box.xmin - 1;
+    return r;
 }
 
-// Writes the owned pixels of a small triangle: the group's G lanes tile the
-// bounding box as LX x LY (LX the least power of two >= its width, at most
-// G), consecutive x on consecutive lanes (their stores are contiguous), and
-// every pixel is confirmed with the three edge functions as in raster_row.
-template <int G>
-__device__ __forceinline__ void raster_box(const TriGeom &g, int gl, int w, int dmin, int dmax,
-                                           int16_t *__restrict__ dplane) {
-    const int bw = g.xmax - g.xmin + 1;
-    const int LX = bw >= G ? G : (bw > G / 2 ? G : (bw > G / 4 ? G / 2 : (bw > 1 ? 2 : 1)));
-    const int LY = G / LX, lx = gl % LX, ly = gl / LX;
-    for (int y = g.ymin + ly; y <= g.ymax; y += LY) {
-        for (int x = g.xmin + lx; x <= g.xmax; x += LX) {
-            const int e0 = (g.ex1 - g.ex0) * (y - g.ey0) - (g.ey1 - g.ey0) * (x - g.ex0);
-            const int e1 = (g.ex2 - g.ex1) * (y - g.ey1) - (g.ey2 - g.ey1) * (x - g.ex1);
-            const int e2 = (g.ex0 - g.ex2) * (y - g.ey2) - (g.ey0 - g.ey2) * (x - g.ex2);
-            if (!((e0 > 0 || (e0 == 0 && g.o0)) && (e1 > 0 || (e1 == 0 && g.o1)) && (e2 > 0 || (e2 == 0 && g.o2))))
-                continue;
-            const float t1 = __fmul_rn(g.fa, __int2float_rn(x));
-            const float t2 = __fmul_rn(g.fb, __int2float_rn(y));
-            const float mu = __fadd_rn(__fadd_rn(t1, t2), g.fc);
-            const int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
-            dplane[(size_t)y * w + x] = (int16_t)min(max(dp, dmin), dmax);
-        }
-    }
+__device__ __forceinline__ void store_rec(int4 *__restrict__ rec, int t, const TriRec &r, const TriBox &b) {
+    int4 *o = rec + kRecWords * (size_t)t;
+    o[0] = make_int4(r.A[0], r.A[1], r.A[2], r.B[0]);
+    o[1] = make_int4(r.B[1], r.B[2], r.C[0], r.C[1]);
+    o[2] = make_int4(r.C[2], __float_as_int(r.fa), __float_as_int(r.fb), __float_as_int(r.fc));
+    o[3] = make_int4(b.xmin, b.xmax, b.ymin, b.ymax);
 }
 
-constexpr int kRasterGroup = 8;       // lanes per small triangle (one pair: shorter chains)
-constexpr int kRasterGroupBatch = 4;  // lanes per small triangle in batches (more triangles in flight)
-constexpr int kBigSplit = 8;          // CTAs a big triangle is spread over, at most
+__device__ __forceinline__ TriRec load_rec(const int4 *__restrict__ rec, int t) {
+    const int4 p = rec[kRecWords * (size_t)t], q = rec[kRecWords * (size_t)t + 1], u = rec[kRecWords * (size_t)t + 2];
+    TriRec r;
+    r.A[0] = p.x, r.A[1] = p.y, r.A[2] = p.z, r.B[0] = p.w;
+    r.B[1] = q.x, r.B[2] = q.y, r.C[0] = q.z, r.C[1] = q.w;
+    r.C[2] = u.x, r.fa = __int_as_float(u.y), r.fb = __int_as_float(u.z), r.fc = __int_as_float(u.w);
+    return r;
+}
 
-template <int RG> __device__ __forceinline__ void plane_raster_body(const RasterArgs &a, const VB &vb, int big_area) {
-    const int side = vb.y;
-    const RasterSide S = side ? a.s[1] : a.s[0];
-    const int gl = threadIdx.x & (RG - 1);
-    const int gpb = blockDim.x / RG;  // triangles per CTA pass
+// Records, unit counts and the -1 fill of the maps (grid-stride; the maps
+// of the sides need not be contiguous).
+__device__ __forceinline__ void raster_setup_body(const RasterArgs &a, const VB &vb) {
+    const int tid = vb.x * blockDim.x + threadIdx.x, stride = vb.gx * blockDim.x;
+    const RasterSide &S = a.s[vb.y];
+    // -1 fill: 16-byte stores between an unaligned head and tail
+    const size_t npx = (size_t)a.w * a.h;
+    int16_t *d = S.dplane;
+    const size_t head = min(npx, (size_t)((16 - (reinterpret_cast<uintptr_t>(d) & 15)) & 15) / 2);
+    const size_t n8 = (npx - head) / 8;
+    uint4 *d8 = reinterpret_cast<uint4 *>(d + head);
+    for (size_t i = tid; i < n8; i += stride) d8[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    if ((size_t)tid < head) d[tid] = -1;
+    if ((size_t)tid < npx - head - 8 * n8) d[head + 8 * n8 + tid] = -1;
+    if (tid == 0) *S.nunits = 0;
     const int ntri = side_ntri(S);
-    for (int t = vb.x * gpb + (int)threadIdx.x / RG; t < ntri; t += vb.gx * gpb) {
-        const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
-        if (g.empty) continue;
-        const int rows = g.ymax - g.ymin + 1;
-        if ((g.xmax - g.xmin + 1) * rows > big_area) {
-            // drawn by plane_raster_big_kernel, split over up to kBigSplit CTAs
-            const int nsub = min(kBigSplit, (rows + 31) / 32);
-            if (gl == 0) {
-                const int k = atomicAdd(a.nbig, nsub);
-                for (int j = 0; j < nsub; ++j) a.big[k + j] = make_int2((side << 8) | (j << 4) | nsub, t);
-            }
-            continue;
-        }
-        raster_box<RG>(g, gl, a.w, a.dmin, a.dmax, S.dplane);
+    for (int t = tid; t < ntri; t += stride) {
+        TriBox b;
+        const TriRec r = tri_record(a.list, S.tri, t, S.right, a.w, a.h, b);
+        store_rec(S.rec, t, r, b);
+        const long long area = b.xmax >= b.xmin && b.ymax >= b.ymin
+                                   ? (long long)(b.xmax - b.xmin + 1) * (b.ymax - b.ymin + 1)
+                                   : 0;
+        S.ucnt[t] = (int)((area + kUnitPx - 1) / kUnitPx);
     }
 }
 
-__global__ void __launch_bounds__(256) plane_raster_kernel(RasterArgs a) {
-    plane_raster_body<kRasterGroup>(a, vb_single(), kBigAreaOne);
-}
-template <int RG>
-__global__ void __launch_bounds__(256) plane_raster_kernel_b(const RasterArgs *__restrict__ tab, VMap vm,
-                                                             int big_area) {
+__global__ void __launch_bounds__(256) raster_setup_kernel(RasterArgs a) { raster_setup_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) raster_setup_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    plane_raster_body<RG>(slot_entry(tab, vm.stride, vb.slot), vb, big_area);
+    raster_setup_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-// Big triangles: each list entry is one of the nsub parts of a triangle, one
-// CTA each (grid-stride over the list); part j takes the 8-row groups
-// j, j + nsub, j + 2 nsub, ... whose rows go to the CTA's warps, lanes
-// striding across x.
-__device__ __forceinline__ void plane_raster_big_body(const RasterArgs &a, const VB &vb) {
-    const int n = *a.nbig;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (int k = vb.x; k < n; k += vb.gx) {
-        const int2 e = a.big[k];
-        const int side = e.x >> 8, part = (e.x >> 4) & 15, nsub = e.x & 15, t = e.y;
-        const RasterSide S = side ? a.s[1] : a.s[0];
-        const TriGeom g = tri_geom(a.list, S.tri, t, S.right, a.w, a.h);
-        const int rows = g.ymax - g.ymin + 1;
-        for (int r0 = part * wpb; r0 < rows; r0 += nsub * wpb) {
-            const int r = r0 + warp;
-            if (r < rows) raster_row(g, g.ymin + r, lane, 32, a.w, a.dmin, a.dmax, S.dplane);
+// Extra units (chunks 1.. of each box) of the mesh: ulist[k] = (t, chunk);
+// *nunits counts them (64 bits: thin triangles' boxes can hold many), beyond
+// unit_cap the list is incomplete.
+__device__ __forceinline__ void raster_list_body(const RasterArgs &a, const VB &vb) {
+    const RasterSide &S = a.s[vb.y];
+    const int ntri = side_ntri(S);
+    for (int t = vb.x * blockDim.x + threadIdx.x; t < ntri; t += vb.gx * blockDim.x) {
+        const int n = S.ucnt[t] - 1;
+        if (n <= 0) continue;
+        const unsigned long long pos = atomicAdd(S.nunits, (unsigned long long)n);
+        for (int j = 0; j < n && pos + j < (unsigned long long)a.unit_cap; ++j) S.ulist[pos + j] = make_int2(t, j + 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) raster_list_kernel(RasterArgs a) { raster_list_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) raster_list_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    raster_list_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
+
+// Pixels [p0, p1) of the box of record r (row-major in the box), 32 at a
+// time across the warp.
+__device__ __forceinline__ void raster_span(const RasterArgs &a, const RasterSide &S, const TriRec &r, const int4 &b,
+                                            int p0, int p1, int lane) {
+    const int bw = b.y - b.x + 1;
+    int p = p0 + lane;
+    int y = b.z + p / bw, x = b.x + (p - (p / bw) * bw);
+    const int dy = 32 / bw, dx = 32 - dy * bw;
+    for (; p < p1; p += 32) {
+        if (r.A[0] * x + r.B[0] * y + r.C[0] > 0 && r.A[1] * x + r.B[1] * y + r.C[1] > 0 &&
+            r.A[2] * x + r.B[2] * y + r.C[2] > 0) {
+            const float t1 = __fmul_rn(r.fa, __int2float_rn(x));
+            const float t2 = __fmul_rn(r.fb, __int2float_rn(y));
+            const float mu = __fadd_rn(__fadd_rn(t1, t2), r.fc);
+            const int dp = __float2int_rz(floorf(__fadd_rn(mu, 0.5f)));
+            S.dplane[(size_t)y * a.w + x] = (int16_t)min(max(dp, a.dmin), a.dmax);
+        }
+        x += dx;
+        y += dy;
+        if (x > b.y) {
+            x -= bw;
+            ++y;
         }
     }
 }
 
-__global__ void __launch_bounds__(256) plane_raster_big_kernel(RasterArgs a) { plane_raster_big_body(a, vb_single()); }
-__global__ void __launch_bounds__(256) plane_raster_big_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
-    const VB vb = vb_batch(vm);
-    plane_raster_big_body(slot_entry(tab, vm.stride, vb.slot), vb);
+__device__ __forceinline__ void raster_draw_body(const RasterArgs &a, const VB &vb) {
+    const RasterSide &S = a.s[vb.y];
+    const int lane = threadIdx.x & 31;
+    const int wid = vb.x * (blockDim.x >> 5) + (threadIdx.x >> 5), nwarps = vb.gx * (blockDim.x >> 5);
+    const int ntri = side_ntri(S);
+    const unsigned long long nextra = *S.nunits;
+    const bool whole = nextra > (unsigned long long)a.unit_cap;  // the list is incomplete
+    const int nunits = ntri + (whole ? 0 : (int)nextra);
+    for (int u = wid; u < nunits; u += nwarps) {
+        int t = u, c = 0;
+        if (u >= ntri) {
+            const int2 e = S.ulist[u - ntri];
+            t = e.x;
+            c = e.y;
+        }
+        const int4 b = S.rec[kRecWords * (size_t)t + 3];
+        if (b.y < b.x || b.w < b.z) continue;
+        const int area = (b.y - b.x + 1) * (b.w - b.z + 1);
+        raster_span(a, S, load_rec(S.rec, t), b, c * kUnitPx, whole ? area : min(area, (c + 1) * kUnitPx), lane);
+    }
 }
 
-
+__global__ void __launch_bounds__(256) raster_draw_kernel(RasterArgs a) { raster_draw_body(a, vb_single()); }
+__global__ void __launch_bounds__(256) raster_draw_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    raster_draw_body(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 
 constexpr int kListPad = 16;  // padding entries (2047) after the candidate list
 
-// TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
-// every TPP-th candidate of its list and of its plane window and merge their
-// keys with shuffles (min is order free, so every TPP gives the same result).
 // Dense matching cost of two 16-byte descriptors added to acc: the SAD of
 // Sobel descriptors, or the Hamming distance of dense census records
 // (Sec. VI.A).  acc carries the key bias and, in the plane neighbourhood, the
@@ -260,6 +254,9 @@ template <bool CENSUS> __device__ __forceinline__ int dense_cost(const uint4 &a,
 // the packing stays one integer multiply-add.
 constexpr int kKeyMul = 2047;
 
+// TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
+// every TPP-th candidate of its list and of its plane window and merge their
+// keys with shuffles (min is order free, so every TPP gives the same result).
 template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + kListPad];
     __shared__ int s_P[kMaxSradius + 1];
@@ -424,45 +421,44 @@ static elas_status fill_prior_table(const elas_params *p, int *P) {
     return ELAS_OK;
 }
 
-// Scratch of the rasteriser: the big-triangle list (up to kBigSplit parts
-// per triangle) and its counter.
-size_t raster_scratch_bytes(int ntri_total) {
-    return align_up(sizeof(int32_t) * 4, 256) +
-           align_up(sizeof(int2) * kBigSplit * (size_t)(ntri_total > 0 ? ntri_total : 1), 256);
+// Entries of a mesh's list of extra units for at most tri_cap triangles:
+// most boxes are one unit; very thin triangles near the hull have many.
+static int raster_unit_cap(int tri_cap) { return 8 * (tri_cap > 0 ? tri_cap : 1) + 4096; }
+
+// Scratch of one mesh: records, unit counts, list of extra units, its count.
+static size_t raster_side_bytes(int tri_cap) {
+    const size_t cap = (size_t)(tri_cap > 0 ? tri_cap : 1);
+    return align_up(sizeof(int4) * kRecWords * cap, 256) + align_up(sizeof(int32_t) * cap, 256) +
+           align_up(sizeof(int2) * (size_t)raster_unit_cap(tri_cap), 256) + 256;
 }
 
-// Batched launches keep no memsets: this kernel fills the prior maps of a
-// pair (both sides, contiguous) with -1 and clears its big-triangle count.
-__device__ __forceinline__ void raster_init_body(const RasterArgs &a, const VB &vb) {
-    const size_t n = (size_t)a.nsides * a.w * a.h;  // int16 entries
-    int16_t *d = a.s[0].dplane;
-    const size_t n8 = n / 8;
-    uint4 *d8 = reinterpret_cast<uint4 *>(d);
-    const size_t stride = (size_t)vb.gx * blockDim.x;
-    const size_t t = (size_t)vb.x * blockDim.x + threadIdx.x;
-    for (size_t i = t; i < n8; i += stride) d8[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-    if (t < n - 8 * n8) d[8 * n8 + t] = -1;
-    if (t == 0) *a.nbig = 0;
-}
+size_t raster_scratch_bytes(int tri_cap, int nsides) { return (size_t)nsides * raster_side_bytes(tri_cap); }
 
-__global__ void __launch_bounds__(256) raster_init_kernel(RasterArgs a) { raster_init_body(a, vb_single()); }
-__global__ void __launch_bounds__(256) raster_init_kernel_b(const RasterArgs *__restrict__ tab, VMap vm) {
-    const VB vb = vb_batch(vm);
-    raster_init_body(slot_entry(tab, vm.stride, vb.slot), vb);
-}
-
+// Argument block for nsides meshes of at most tri_cap triangles each, their
+// scratch carved from `scratch` (raster_scratch_bytes bytes, 256-aligned).
 static RasterArgs raster_args(const int16_t *list, const RasterSide *sides, int nsides, int w, int h,
-                              const elas_params *p, void *scratch) {
+                              const elas_params *p, void *scratch, int tri_cap) {
     RasterArgs a{};
+    const size_t cap = (size_t)(tri_cap > 0 ? tri_cap : 1);
     a.list = list;
     a.nsides = nsides;
-    a.nbig = reinterpret_cast<int32_t *>(scratch);
-    a.big = reinterpret_cast<int2 *>(reinterpret_cast<char *>(scratch) + align_up(sizeof(int32_t) * 4, 256));
     a.w = w;
     a.h = h;
     a.dmin = p->disp_min;
     a.dmax = p->disp_max;
-    for (int i = 0; i < nsides; ++i) a.s[i] = sides[i];
+    a.unit_cap = raster_unit_cap(tri_cap);
+    char *q = reinterpret_cast<char *>(scratch);
+    for (int i = 0; i < nsides; ++i) {
+        a.s[i] = sides[i];
+        a.s[i].rec = reinterpret_cast<int4 *>(q);
+        q += align_up(sizeof(int4) * kRecWords * cap, 256);
+        a.s[i].ucnt = reinterpret_cast<int32_t *>(q);
+        q += align_up(sizeof(int32_t) * cap, 256);
+        a.s[i].ulist = reinterpret_cast<int2 *>(q);
+        q += align_up(sizeof(int2) * (size_t)a.unit_cap, 256);
+        a.s[i].nunits = reinterpret_cast<unsigned long long *>(q);
+        q += 256;
+    }
     return a;
 }
 
@@ -472,31 +468,19 @@ static int raster_max_ntri(const RasterArgs &a) {
     return maxt;
 }
 
-// Prior maps of one or two meshes.  With two, the maps must be contiguous
-// (dplane1 == dplane0 + w*h) so that one pass clears both: raster_init_kernel
-// (16-byte stores) when the maps are 16-byte aligned, else two memsets.
+// Grid of the setup kernel (per side: the larger of the pixel fill and the
+// triangles, grid-stride) and of the draw kernel (warps over units).
+static int raster_setup_blocks(const RasterArgs &a, int cap_blocks) {
+    const long long n = max((long long)a.w * a.h, (long long)raster_max_ntri(a));
+    return (int)max(1LL, min((n + 255) / 256, (long long)cap_blocks));
+}
+
+// Prior maps of one or two meshes.
 static elas_status raster_meshes(const RasterArgs &a, cudaStream_t st) {
-    const size_t n = (size_t)a.w * a.h * a.nsides;  // int16 entries
-    if (aligned(a.s[0].dplane, 16)) {
-        const size_t blocks = (n / 8 + 255) / 256;
-        const size_t cap_blocks = (size_t)sm_count() * 8;
-        raster_init_kernel<<<(unsigned)(blocks < cap_blocks ? (blocks > 0 ? blocks : 1) : cap_blocks), 256, 0, st>>>(a);
-        elas_status s0 = launch_status("raster_init_kernel");
-        if (s0 != ELAS_OK) return s0;
-    } else if (cudaMemsetAsync(a.s[0].dplane, 0xFF, n * sizeof(int16_t), st) != cudaSuccess ||
-               cudaMemsetAsync(a.nbig, 0, sizeof(int32_t), st) != cudaSuccess) {
-        return launch_status("memset d_plane");
-    }
-    const int maxt = raster_max_ntri(a);
-    if (maxt == 0) return ELAS_OK;
-    const int wpb = 256 / kRasterGroup;  // triangles per CTA pass
-    int blocks = (maxt + wpb - 1) / wpb;
-    if (blocks > sm_count() * 4) blocks = sm_count() * 4;
-    plane_raster_kernel<<<dim3(blocks, a.nsides), 256, 0, st>>>(a);
-    elas_status s = launch_status("plane_raster_kernel");
-    if (s != ELAS_OK) return s;
-    plane_raster_big_kernel<<<2 * sm_count(), 256, 0, st>>>(a);
-    return launch_status("plane_raster_big_kernel");
+    raster_setup_kernel<<<dim3(raster_setup_blocks(a, sm_count() * 4), a.nsides), 256, 0, st>>>(a);
+    raster_list_kernel<<<dim3(raster_setup_blocks(a, sm_count() * 4), a.nsides), 256, 0, st>>>(a);
+    raster_draw_kernel<<<dim3(sm_count() * 4, a.nsides), 256, 0, st>>>(a);
+    return launch_status("plane prior kernels");
 }
 
 static CellArgs cell_args(int w, int h, const elas_params *p, const int *P) {
@@ -539,8 +523,12 @@ static elas_status launch_cells(const CellArgs &a, int nsides, cudaStream_t st) 
 
 elas_status launch_plane_prior(const int16_t *list, const int32_t *tri, int ntri, int right, int w, int h,
                                const elas_params *p, int16_t *dplane, void *scratch, cudaStream_t st) {
-    RasterSide side{tri, ntri, right ? 1 : 0, dplane, nullptr};
-    return raster_meshes(raster_args(list, &side, 1, w, h, p, scratch), st);
+    RasterSide side{};
+    side.tri = tri;
+    side.ntri = ntri;
+    side.right = right ? 1 : 0;
+    side.dplane = dplane;
+    return raster_meshes(raster_args(list, &side, 1, w, h, p, scratch, ntri), st);
 }
 
 elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
@@ -560,7 +548,7 @@ elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int 
 }
 
 size_t dense_workspace(int w, int h, const elas_params *p) {
-    return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(2 * max_triangles(w, h, p));
+    return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(max_triangles(w, h, p), 2);
 }
 
 elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
@@ -569,10 +557,18 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
                        const int32_t *ntri_dev, DenseStage *o) {
     int16_t *dpL = reinterpret_cast<int16_t *>(ws);
     int16_t *dpR = dpL + (size_t)w * h;
-    const RasterSide sides[2] = {{triL, ntriL, 0, dpL, ntri_dev ? ntri_dev : nullptr},
-                                 {triR, ntriR, 1, dpR, ntri_dev ? ntri_dev + 1 : nullptr}};
+    RasterSide sides[2] = {};
+    sides[0].tri = triL;
+    sides[0].ntri = ntriL;
+    sides[0].dplane = dpL;
+    sides[0].ntri_dev = ntri_dev;
+    sides[1].tri = triR;
+    sides[1].ntri = ntriR;
+    sides[1].right = 1;
+    sides[1].dplane = dpR;
+    sides[1].ntri_dev = ntri_dev ? ntri_dev + 1 : nullptr;
     void *scratch = reinterpret_cast<char *>(ws) + align_up(2 * (size_t)w * h * sizeof(int16_t), 256);
-    o->raster = raster_args(list, sides, 2, w, h, p, scratch);
+    o->raster = raster_args(list, sides, 2, w, h, p, scratch, max_triangles(w, h, p));
     int P[kMaxSradius + 1];
     elas_status s = fill_prior_table(p, P);
     if (s != ELAS_OK) return s;
@@ -610,35 +606,28 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
     if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8 && ppt != 16)
         return fail(ELAS_ERR_INVALID_ARG, "dense pixels per thread %d", ppt);
-    VMap m_init, m_tri, m_big, m_cell[2];
-    vmap_clear(m_init, pairs.stride);
-    vmap_clear(m_tri, pairs.stride);
-    vmap_clear(m_big, pairs.stride);
+    VMap m_setup, m_list, m_draw, m_cell[2];
+    vmap_clear(m_setup, pairs.stride);
+    vmap_clear(m_list, pairs.stride);
+    vmap_clear(m_draw, pairs.stride);
     vmap_clear(m_cell[0], pairs.stride);
     vmap_clear(m_cell[1], pairs.stride);
+    // per pair: the one-pair grids shared out among the pairs, at least 16 CTAs
+    const int per_pair = max(16, sm_count() * 4 / pairs.n);
     int threads = 32;
     for (int i = 0; i < pairs.n; ++i) {
         const int slot = pairs.slot[i];
         const DenseStage &d = slot_entry(host, pairs.stride, slot);
-        const size_t n8 = ((size_t)d.raster.nsides * d.raster.w * d.raster.h + 7) / 8;
-        vmap_add(m_init, slot, dim3((unsigned)min((n8 + 255) / 256, (size_t)sm_count() * 4)));
-        const int maxt = raster_max_ntri(d.raster);
-        const int wpb = 256 / (pairs.n == 1 ? kRasterGroup : kRasterGroupBatch);
-        int blocks = (maxt + wpb - 1) / wpb;
-        if (pairs.n > 1) blocks = (blocks + 2) / 3;
-        blocks = max(1, min(blocks, sm_count() * 16));
-        vmap_add(m_tri, slot, dim3(blocks, d.raster.nsides));
-        // big triangles: the one-pair launch's 2 CTAs per SM, shared by the pairs
-        vmap_add(m_big, slot, dim3(max(32, 2 * sm_count() / pairs.n)));
+        const RasterArgs &r = d.raster;
+        vmap_add(m_setup, slot, dim3(raster_setup_blocks(r, per_pair), r.nsides));
+        vmap_add(m_list, slot, dim3(raster_setup_blocks(r, per_pair), r.nsides));
+        vmap_add(m_draw, slot, dim3(per_pair, r.nsides));
         vmap_add(m_cell[d.cell.census ? 1 : 0], slot, cell_grid(d.cell, 2));
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
     }
-    raster_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(t.raster, m_init);
-    if (pairs.n == 1)
-        plane_raster_kernel_b<kRasterGroup><<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri, kBigAreaOne);
-    else
-        plane_raster_kernel_b<kRasterGroupBatch><<<vmap_total(m_tri), 256, 0, st>>>(t.raster, m_tri, kBigAreaBatch);
-    plane_raster_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(t.raster, m_big);
+    raster_setup_kernel_b<<<vmap_total(m_setup), 256, 0, st>>>(t.raster, m_setup);
+    raster_list_kernel_b<<<vmap_total(m_list), 256, 0, st>>>(t.raster, m_list);
+    raster_draw_kernel_b<<<vmap_total(m_draw), 256, 0, st>>>(t.raster, m_draw);
     elas_status s = launch_status("batched plane prior");
     if (s != ELAS_OK) return s;
     if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");
@@ -649,8 +638,9 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
 
 }  // namespace elas
 
-extern "C" size_t elas_plane_prior_workspace_bytes(int32_t ntri) {
-    return ntri < 0 ? 0 : elas::raster_scratch_bytes(ntri);
+extern "C" size_t elas_plane_prior_workspace_bytes(int32_t w, int32_t h, int32_t ntri) {
+    if (w < 1 || h < 1 || w > 16383 || h > 16383 || ntri < 0) return 0;
+    return elas::raster_scratch_bytes(ntri, 1);
 }
 
 extern "C" elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,
@@ -664,8 +654,8 @@ extern "C" elas_status elas_plane_prior(const int16_t *list, int32_t n, const in
     if (n < 0 || ntri < 0) return fail(ELAS_ERR_INVALID_ARG, "negative count");
     if (ntri >= (1 << 30)) return fail(ELAS_ERR_INVALID_ARG, "too many triangles");
     if (!aligned(workspace, 256)) return fail(ELAS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
-    if (workspace_bytes < raster_scratch_bytes(ntri))
-        return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, raster_scratch_bytes(ntri));
+    if (workspace_bytes < raster_scratch_bytes(ntri, 1))
+        return fail(ELAS_ERR_CAPACITY, "workspace %zu < %zu bytes", workspace_bytes, raster_scratch_bytes(ntri, 1));
     return launch_plane_prior(list, tri, ntri, right, w, h, p, d_plane, workspace, to_stream(stream));
 }
 

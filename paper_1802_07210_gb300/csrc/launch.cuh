@@ -20,7 +20,7 @@ elas_status launch_support(const uint8_t *descL, const uint8_t *descR, int w, in
                            int16_t *d_can, int16_t *list, int32_t *count, uint32_t *grid_L, uint32_t *grid_R,
                            void *ws, cudaStream_t st);
 int max_triangles(int w, int h, const elas_params *p);
-size_t raster_scratch_bytes(int ntri_total);
+size_t raster_scratch_bytes(int tri_cap, int nsides);
 elas_status launch_plane_prior(const int16_t *list, const int32_t *tri, int ntri, int right, int w, int h,
                                const elas_params *p, int16_t *dplane, void *scratch, cudaStream_t st);
 elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,

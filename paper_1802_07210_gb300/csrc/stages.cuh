@@ -131,19 +131,21 @@ struct DtArgs {
 // ---- plane prior and dense matching ------------------------------------------
 struct RasterSide {
     const int32_t *tri;
-    int ntri, right;          // ntri: used when ntri_dev is NULL
+    int ntri, right;          // ntri: used when ntri_dev is NULL (else the capacity)
     int16_t *dplane;
     const int32_t *ntri_dev;  // device triangle count (negative = none)
+    int4 *rec;                // [cap][4] rasteriser records (edge functions, plane, box)
+    int32_t *ucnt;            // [cap] work units (box chunks) of each triangle
+    int2 *ulist;              // [unit_cap] extra units: (triangle, chunk >= 1)
+    unsigned long long *nunits;  // extra units of the mesh (the list is complete up to unit_cap)
 };
 
 struct RasterArgs {
     const int16_t *list;
     RasterSide s[2];
     int nsides;
-    int2 *big;      // parts of the triangles left to plane_raster_big_kernel:
-                    // x = (side << 8) | (part << 4) | parts, y = triangle
-    int32_t *nbig;  // count of big (zeroed before the launch)
     int w, h, dmin, dmax;
+    int unit_cap;  // entries of each mesh's list of extra units
 };
 
 struct CellSide {
