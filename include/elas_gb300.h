@@ -296,12 +296,11 @@ elas_status elas_triangulate_device(const int16_t *list, const int32_t *count, i
  * d_plane = clamp(floor((a*u + b*v) + c + 0.5), disp_min, disp_max); all
  * other pixels get -1.  right = 1: vertices at (u - d, v).
  * list/tri/d_plane: device; d_plane int16 [h][w].  workspace: device,
- * 256-byte aligned, >= elas_plane_prior_workspace_bytes(w, h, ntri) (the
- * triangles' plane and edge records and their 32x8-pixel tile lists; the
- * bytes grow with the image size and the triangle count; 0 for an invalid
- * size or a negative count).
+ * 256-byte aligned, >= elas_plane_prior_workspace_bytes(ntri) (a 64-byte
+ * plane and edge record per triangle and the list of the work units of
+ * large triangles; 0 for a negative count).
  */
-size_t elas_plane_prior_workspace_bytes(int32_t w, int32_t h, int32_t ntri);
+size_t elas_plane_prior_workspace_bytes(int32_t ntri);
 elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,
                              int32_t right, int32_t w, int32_t h, const elas_params *p,
                              int16_t *d_plane, void *workspace, size_t workspace_bytes,

@@ -90,7 +90,7 @@ SIGNATURES = {
     "elas_triangulate": (C.c_int, [_P, _I, _I, _P, _I, _P]),
     "elas_triangulate_device_workspace_bytes": (_Z, [_I, _I, _I]),
     "elas_triangulate_device": (C.c_int, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _Z, _P]),
-    "elas_plane_prior_workspace_bytes": (_Z, [_I, _I, _I]),
+    "elas_plane_prior_workspace_bytes": (_Z, [_I]),
     "elas_plane_prior": (C.c_int, [_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _Z, _P]),
     "elas_dense_argmin": (C.c_int, [_P, _P, _I, _I, _P, _P, _P, _I, _P, _P]),
     "elas_dense_workspace_bytes": (_Z, [_I, _I, _P]),

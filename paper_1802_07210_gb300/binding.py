@@ -133,7 +133,7 @@ def elas_plane_prior(lst, tri, w, h, prm=None, right=False, stream=None):
     out = torch.empty((h, w), dtype=torch.int16, device=dev)
     n = lst.shape[0]
     ntri = tri.shape[0]
-    nb = lib().elas_plane_prior_workspace_bytes(w, h, ntri)
+    nb = lib().elas_plane_prior_workspace_bytes(ntri)
     ws = _workspace(nb, dev)
     check(lib().elas_plane_prior(_dev(lst, torch.int16, "list"), n, _dev(tri, torch.int32, "tri"), ntri,
                                  int(bool(right)), w, h, C.byref(prm), C.c_void_p(out.data_ptr()),

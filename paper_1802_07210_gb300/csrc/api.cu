@@ -98,7 +98,7 @@ size_t elas_workspace_bytes(int32_t w, int32_t h, const elas_params *p) {
     const int32_t cap = (w / step) * (h / step);
     size_t m = elas_support_workspace_bytes(w, h, p);
     m = std::max(m, elas_triangulate_device_workspace_bytes(cap > 0 ? cap : 1, w, h));
-    m = std::max(m, elas_plane_prior_workspace_bytes(w, h, 2 * cap + 8));
+    m = std::max(m, elas_plane_prior_workspace_bytes(2 * cap + 8));
     m = std::max(m, elas_dense_workspace_bytes(w, h, p));
     m = std::max(m, elas_postprocess_workspace_bytes(w, h));
     m = std::max(m, elas_speckle_workspace_bytes(w, h));

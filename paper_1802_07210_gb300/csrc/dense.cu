@@ -638,9 +638,8 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
 
 }  // namespace elas
 
-extern "C" size_t elas_plane_prior_workspace_bytes(int32_t w, int32_t h, int32_t ntri) {
-    if (w < 1 || h < 1 || w > 16383 || h > 16383 || ntri < 0) return 0;
-    return elas::raster_scratch_bytes(ntri, 1);
+extern "C" size_t elas_plane_prior_workspace_bytes(int32_t ntri) {
+    return ntri < 0 ? 0 : elas::raster_scratch_bytes(ntri, 1);
 }
 
 extern "C" elas_status elas_plane_prior(const int16_t *list, int32_t n, const int32_t *tri, int32_t ntri,

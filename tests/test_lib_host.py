@@ -172,7 +172,7 @@ def test_one_workspace_for_every_call():
         assert total > 0
         assert total >= L.elas_support_workspace_bytes(w, h, C.byref(p))
         assert total >= L.elas_triangulate_device_workspace_bytes(cap, w, h)
-        assert total >= L.elas_plane_prior_workspace_bytes(w, h, 2 * cap + 8)
+        assert total >= L.elas_plane_prior_workspace_bytes(2 * cap + 8)
         assert total >= L.elas_dense_workspace_bytes(w, h, C.byref(p))
         assert total >= L.elas_postprocess_workspace_bytes(w, h)
         assert total >= L.elas_speckle_workspace_bytes(w, h)
