@@ -63,7 +63,7 @@ int cell_threads(int G, int tpp, int ppt);
 int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, PostArgs *passes);
 bool post_fusable(const elas_params *p);
 FusedPostArgs fused_post_args(const int16_t *d, int w, int h, const elas_params *p, float *out);
-dim3 fused_post_grid(int w, int h, int tile);
+dim3 fused_post_grid(int w, int h, int tile_y);
 
 // ---- many pairs per launch --------------------------------------------------
 // Tables are arrays of per-slot records `pairs.stride` bytes apart: `tab`

@@ -116,6 +116,10 @@ struct elas_pipeline {
     static constexpr size_t kGraphCache = 8;
     int use_graph = 1;
     cudaStream_t work = nullptr;
+    // the counts' read-back runs on a branch of its own, joined at the end
+    // of the step, so the LR check does not wait for the copy
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
     // last run
@@ -136,7 +140,11 @@ void release(elas_pipeline *pl) {
     if (pl->work) cudaStreamSynchronize(pl->work);
     for (auto &g : pl->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (pl->side) cudaStreamSynchronize(pl->side);
     if (pl->work) cudaStreamDestroy(pl->work);
+    if (pl->side) cudaStreamDestroy(pl->side);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     for (cudaEvent_t &e : pl->marks)
         if (e) cudaEventDestroy(e);
     void *dev[] = {pl->img, pl->descL, pl->descR, pl->sdescL, pl->sdescR, pl->dcan, pl->countlist, pl->gridL, pl->gridR, pl->tri,
@@ -218,10 +226,13 @@ extern "C" elas_status elas_pipeline_create(int32_t w, int32_t h, const elas_par
         release(pl);
         return fail(ELAS_ERR_NO_MEMORY, "helper thread");
     }
-    if (cudaStreamCreateWithFlags(&pl->work, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&pl->work, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         release(pl);
-        return fail(ELAS_ERR_NO_MEMORY, "pipeline capture stream");
+        return fail(ELAS_ERR_NO_MEMORY, "pipeline streams");
     }
     *out = pl;
     return ELAS_OK;
@@ -274,7 +285,9 @@ static elas_status run_step(elas_pipeline *pl, const uint8_t *imgL, const uint8_
                                    prof ? pl->marks[4] : nullptr)) != ELAS_OK)
             return s;
         mark(5);
-        if (cudaMemcpyAsync(pl->h_countlist, pl->countlist, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(pl->side, pl->ev_fork, 0) != cudaSuccess ||
+            cudaMemcpyAsync(pl->h_countlist, pl->countlist, 16, cudaMemcpyDeviceToHost, pl->side) != cudaSuccess ||
+            cudaEventRecord(pl->ev_join, pl->side) != cudaSuccess)
             return launch_status("stats to host");
         pl->stats.triangulate_ms = 0.0;
     } else {
@@ -303,6 +316,7 @@ static elas_status run_step(elas_pipeline *pl, const uint8_t *imgL, const uint8_
     }
     if ((s = launch_lr_check(dL, outR, w, h, p->lr_threshold, nullptr, nullptr, st)) != ELAS_OK) return s;
     if (post && (s = launch_post(dL, w, h, p, post, pl->ws_post, st)) != ELAS_OK) return s;
+    if (pl->gpu_tri && cudaStreamWaitEvent(st, pl->ev_join, 0) != cudaSuccess) return launch_status("stats join");
     mark(6);
     return ELAS_OK;
 }

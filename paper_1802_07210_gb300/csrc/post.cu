@@ -52,20 +52,21 @@ __global__ void __launch_bounds__(256) lr_check_kernel_b(const LrArgs *__restric
 }
 
 // Gap interpolation along a row or a column at element k of a line of
-// length len (stride es from base); In is LineIn (global maps) or SmemIn.
-template <class In>
-__device__ __forceinline__ float gap_at(const In &in, size_t base, size_t es, int k, int len, int gap) {
-    const float x = in.at(base + (size_t)k * es);
+// length len (stride es from base); In is LineIn (global maps, size_t
+// indices) or SmemIn (a shared tile, int indices).
+template <class In, class I>
+__device__ __forceinline__ float gap_at(const In &in, I base, I es, int k, int len, int gap) {
+    const float x = in.at(base + (I)k * es);
     float res = x;
     if (x < 0.0f) {
         // nearest valid element on each side within gap steps
         int l = -1, r = -1;
         for (int s = 1; s <= gap && k - s >= 0; ++s)
-            if (in.at(base + (size_t)(k - s) * es) >= 0.0f) { l = k - s; break; }
+            if (in.at(base + (I)(k - s) * es) >= 0.0f) { l = k - s; break; }
         for (int s = 1; s <= gap && k + s < len; ++s)
-            if (in.at(base + (size_t)(k + s) * es) >= 0.0f) { r = k + s; break; }
+            if (in.at(base + (I)(k + s) * es) >= 0.0f) { r = k + s; break; }
         if (l >= 0 && r >= 0 && r - l - 1 <= gap) {
-            const float d1 = in.at(base + (size_t)l * es), d2 = in.at(base + (size_t)r * es);
+            const float d1 = in.at(base + (I)l * es), d2 = in.at(base + (I)r * es);
             res = fabsf(__fsub_rn(d1, d2)) < 3.0f ? __fmul_rn(__fadd_rn(d1, d2), 0.5f) : fminf(d1, d2);
         }
     }
@@ -76,9 +77,9 @@ constexpr int kMeanRadius = 3;
 
 // Adaptive mean along a line: taps in ascending offset order, FP32 without
 // contraction.
-template <class In>
-__device__ __forceinline__ float mean_at(const In &in, size_t base, size_t es, int k, int len) {
-    const float d0 = in.at(base + (size_t)k * es);
+template <class In, class I>
+__device__ __forceinline__ float mean_at(const In &in, I base, I es, int k, int len) {
+    const float d0 = in.at(base + (I)k * es);
     float res = d0;
     if (d0 >= 0.0f) {
         float sw = 0.0f, swd = 0.0f;
@@ -86,7 +87,7 @@ __device__ __forceinline__ float mean_at(const In &in, size_t base, size_t es, i
         for (int o = -kMeanRadius; o <= kMeanRadius; ++o) {
             const int m = k + o;
             if (m < 0 || m >= len) continue;
-            const float di = in.at(base + (size_t)m * es);
+            const float di = in.at(base + (I)m * es);
             if (di < 0.0f) continue;
             const float wgt = __fsub_rn(4.0f, fabsf(__fsub_rn(di, d0)));
             if (wgt > 0.0f) {
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Fused post-processing: the four passes on one TxT tile in shared memory
-// (T = 16 for one map, 32 in batched launches).
+// Fused post-processing: the four passes on one TX x TY tile in shared memory
+// (32 x 16 for one map, 32 x 32 in batched launches).
 //
 // The output tile needs the vertical mean over rows +-3 (r), which needs the
 // horizontal mean over columns +-3, which needs the column gap pass over
@@ -138,74 +139,93 @@ __global__ void __launch_bounds__(256) post_pass_kernel_b(const PostArgs *__rest
 // read -1.  That is the same as the per-pass kernels, whose searches stop at
 // the image border, because a -1 is never taken as a valid neighbour or a
 // tap.  Each pass runs over exactly the region the next one reads, with the
-// same per-element functions as the per-pass kernels.
+// same per-element functions as the per-pass kernels.  Each region is walked
+// as one linear index split into row and column by a multiply-high.
 // ---------------------------------------------------------------------------
-constexpr int kFusedTile = 32;     // batched launches (many tiles in any case)
-constexpr int kFusedTileOne = 16;  // one-map launches: more CTAs for one map
+constexpr int kFusedTX = 32;       // tile width (one warp across)
+constexpr int kFusedTY = 32;       // batched launches (many tiles in any case)
+constexpr int kFusedTYOne = 16;    // one-map launches: more CTAs for one map
 constexpr int kFusedMaxGap = 16;
-template <int T> __host__ __device__ constexpr int fused_pitch() { return T + 2 * (kFusedMaxGap + kMeanRadius); }
+constexpr int kFusedHalo = kFusedMaxGap + kMeanRadius;
 
 struct SmemIn {
     const float *s;
-    __device__ __forceinline__ float at(size_t idx) const { return s[idx]; }
+    __device__ __forceinline__ float at(int idx) const { return s[idx]; }
 };
 
-template <int T>
+// Row of element i of a region w wide: floor(i / w) = umulhi(i, m) with
+// m = floor((2^32 - 1) / w) + 1, exact for i < 2^32 / w (here i < 2^13).
+struct RowSplit {
+    unsigned w, m;
+    __device__ __forceinline__ explicit RowSplit(int width) : w((unsigned)width), m(0xFFFFFFFFu / (unsigned)width + 1u) {}
+    __device__ __forceinline__ void at(int i, int &row, int &col) const {
+        const unsigned q = w == 1u ? (unsigned)i : __umulhi((unsigned)i, m);
+        row = (int)q;
+        col = i - (int)(q * w);
+    }
+};
+
+template <int TY>
 __device__ __forceinline__ void fused_post_body(const FusedPostArgs &a, const VB &vb) {
-    __shared__ float s_a[fused_pitch<T>() * fused_pitch<T>()];
-    __shared__ float s_b[fused_pitch<T>() * fused_pitch<T>()];
+    constexpr int TX = kFusedTX;
+    __shared__ float s_a[(TY + 2 * kFusedHalo) * (TX + 2 * kFusedHalo)];
+    __shared__ float s_b[(TY + 2 * kFusedHalo) * (TX + 2 * kFusedHalo)];
     const int w = a.w, h = a.h;
     const int g = a.gap, r = a.mean ? kMeanRadius : 0, H = g + r;
-    const int P = T + 2 * H;  // tile pitch
-    const int x0 = vb.x * T - H, y0 = vb.y * T - H;
+    const int PX = TX + 2 * H, PY = TY + 2 * H;  // tile pitch and rows
+    const int x0 = vb.x * TX - H, y0 = vb.y * TY - H;
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < P * P; i += nth) {
-        const int gx = x0 + i % P, gy = y0 + i / P;
+    const RowSplit full(PX), inner(PX - 2 * g);
+    for (int i = tid; i < PX * PY; i += nth) {
+        int yy, xx;
+        full.at(i, yy, xx);
+        const int gx = x0 + xx, gy = y0 + yy;
         s_a[i] = (gx >= 0 && gx < w && gy >= 0 && gy < h) ? (float)a.d[(size_t)gy * w + gx] : -1.0f;
     }
     __syncthreads();
     float *cur = s_a, *nxt = s_b;
     if (g > 0) {
+        const int cw = PX - 2 * g;
         // rows: every row, the columns the later passes read
-        const int cw = P - 2 * g;
-        for (int i = tid; i < cw * P; i += nth) {
-            const int c = g + i % cw, rr = i / cw;
-            nxt[rr * P + c] = gap_at(SmemIn{cur}, (size_t)rr * P, 1, c, P, g);
+        for (int i = tid; i < cw * PY; i += nth) {
+            int yy, c;
+            inner.at(i, yy, c);
+            nxt[yy * PX + g + c] = gap_at(SmemIn{cur}, yy * PX, 1, g + c, PX, g);
         }
         __syncthreads();
         // columns: those columns, the rows the means read
-        for (int i = tid; i < cw * cw; i += nth) {
-            const int c = g + i % cw, rr = g + i / cw;
-            cur[rr * P + c] = gap_at(SmemIn{nxt}, (size_t)c, (size_t)P, rr, P, g);
+        for (int i = tid; i < cw * (PY - 2 * g); i += nth) {
+            int rr, c;
+            inner.at(i, rr, c);
+            cur[(g + rr) * PX + g + c] = gap_at(SmemIn{nxt}, g + c, PX, g + rr, PY, g);
         }
         __syncthreads();
     }
     if (r > 0) {
-        // horizontal mean: the output columns, rows +-r
-        const int nr = T + 2 * r;
-        for (int i = tid; i < T * nr; i += nth) {
-            const int c = H + i % T, rr = g + i / T;
-            nxt[rr * P + c] = mean_at(SmemIn{cur}, (size_t)rr * P, 1, c, P);
+        // horizontal mean: the output columns, rows +-r (TX = 32: lane = column)
+        for (int i = tid; i < TX * (TY + 2 * r); i += nth) {
+            const int yy = g + i / TX, xx = H + i % TX;
+            nxt[yy * PX + xx] = mean_at(SmemIn{cur}, yy * PX, 1, xx, PX);
         }
         __syncthreads();
     }
     // vertical mean (or, without the means, the gap passes' result) to the output
     const float *src = r > 0 ? nxt : cur;
-    for (int i = tid; i < T * T; i += nth) {
-        const int c = H + i % T, rr = H + i / T;
-        const int gx = x0 + c, gy = y0 + rr;
+    for (int i = tid; i < TX * TY; i += nth) {
+        const int yy = H + i / TX, xx = H + i % TX;
+        const int gx = x0 + xx, gy = y0 + yy;
         if (gx >= w || gy >= h) continue;
-        a.out[(size_t)gy * w + gx] = r > 0 ? mean_at(SmemIn{src}, (size_t)c, (size_t)P, rr, P) : src[rr * P + c];
+        a.out[(size_t)gy * w + gx] = r > 0 ? mean_at(SmemIn{src}, xx, PX, yy, PY) : src[yy * PX + xx];
     }
 }
 
 __global__ void __launch_bounds__(256) fused_post_kernel(FusedPostArgs a) {
-    fused_post_body<kFusedTileOne>(a, vb_single());
+    fused_post_body<kFusedTYOne>(a, vb_single());
 }
-template <int T>
+template <int TY>
 __global__ void __launch_bounds__(256) fused_post_kernel_b(const FusedPostArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    fused_post_body<T>(slot_entry(tab, vm.stride, vb.slot), vb);
+    fused_post_body<TY>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 bool post_fusable(const elas_params *p) { return p->ipol_gap_width <= kFusedMaxGap; }
@@ -215,7 +235,7 @@ FusedPostArgs fused_post_args(const int16_t *d, int w, int h, const elas_params 
                          p->filter_adaptive_mean ? 1 : 0};
 }
 
-dim3 fused_post_grid(int w, int h, int tile) { return dim3((w + tile - 1) / tile, (h + tile - 1) / tile); }
+dim3 fused_post_grid(int w, int h, int tile_y) { return dim3((w + kFusedTX - 1) / kFusedTX, (h + tile_y - 1) / tile_y); }
 
 size_t post_workspace(int w, int h) { return 2 * align_up((size_t)w * h * sizeof(float), 256); }
 
@@ -267,7 +287,7 @@ dim3 post_grid(int w, int h) { return dim3((w + 31) / 32, (h + 7) / 8); }
 
 elas_status launch_post(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, cudaStream_t st) {
     if (post_fusable(p)) {
-        fused_post_kernel<<<fused_post_grid(w, h, kFusedTileOne), 256, 0, st>>>(fused_post_args(d, w, h, p, out));
+        fused_post_kernel<<<fused_post_grid(w, h, kFusedTYOne), 256, 0, st>>>(fused_post_args(d, w, h, p, out));
         return launch_status("fused_post_kernel");
     }
     PostArgs passes[4];
@@ -303,16 +323,16 @@ elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const 
     if ((s = launch_status("lr_check_kernel_b")) != ELAS_OK) return s;
     VMap m_f;
     vmap_clear(m_f, pairs.stride);
-    const int tile = pairs.n == 1 ? kFusedTileOne : kFusedTile;  // one map: the one-map tiles
+    const int tile = pairs.n == 1 ? kFusedTYOne : kFusedTY;  // one map: the one-map tiles
     for (int i = 0; i < pairs.n; ++i) {
         const LrArgs &l = slot_entry(host_lr, pairs.stride, pairs.slot[i]);
         vmap_add(m_f, pairs.slot[i], fused[i] ? fused_post_grid(l.w, l.h, tile) : dim3(0));
     }
     if (vmap_total(m_f) > 0) {
-        if (tile == kFusedTileOne)
-            fused_post_kernel_b<kFusedTileOne><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
+        if (tile == kFusedTYOne)
+            fused_post_kernel_b<kFusedTYOne><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
         else
-            fused_post_kernel_b<kFusedTile><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
+            fused_post_kernel_b<kFusedTY><<<vmap_total(m_f), 256, 0, st>>>(fused_tab, m_f);
         if ((s = launch_status("fused_post_kernel_b")) != ELAS_OK) return s;
     }
     for (int k = 0; k < maxp && k < 4; ++k) {
