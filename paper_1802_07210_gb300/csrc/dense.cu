@@ -161,9 +161,40 @@ __global__ void __launch_bounds__(256) raster_setup_kernel_b(const RasterArgs *_
     raster_setup_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
+constexpr int kListPad = 16;  // padding entries (2047) after a candidate list
+
+// The candidate list of one grid-vector cell (Sec. III.A: the disparities
+// of its mask within [dmin, dmax]), ascending, then kListPad entries of 2047
+// (above every dmax); returns the count.  Warp collective.  The words are
+// taken one at a time: lane l places bit l of the word after the set bits
+// below it, so the list comes out sorted with no per-lane bit loop.
+__device__ __forceinline__ int expand_cell_list(const uint32_t *__restrict__ g, int nw, int dmin, int dmax,
+                                                uint16_t *out, int lane) {
+    const uint32_t below = (1u << lane) - 1u;
+    int base = 0;
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int wi = w0 + lane;
+        uint32_t m = wi < nw ? __ldg(g + wi) : 0u;
+        // keep the bits inside [dmin, dmax]
+        const int lo = dmin - 32 * wi, hi = dmax - 32 * wi;
+        if (lo > 0) m &= lo >= 32 ? 0u : (0xFFFFFFFFu << lo);
+        if (hi < 31) m &= hi < 0 ? 0u : (0xFFFFFFFFu >> (31 - hi));
+        const int nk = min(32, nw - w0);
+        for (int k = 0; k < nk; ++k) {
+            const uint32_t mk = __shfl_sync(0xFFFFFFFFu, m, k);
+            if ((mk >> lane) & 1u) out[base + __popc(mk & below)] = (uint16_t)(32 * (w0 + k) + lane);
+            base += __popc(mk);
+        }
+    }
+    if (lane < kListPad) out[base + lane] = (uint16_t)2047;
+    return base;
+}
+
 // Extra units (chunks 1.. of each box) of the mesh: ulist[k] = (t, chunk);
 // *nunits counts them (64 bits: thin triangles' boxes can hold many), beyond
-// unit_cap the list is incomplete.
+// unit_cap the list is incomplete.  With lstride > 0 it also expands the
+// grid-vector masks of the mesh's side into the dense step's candidate
+// lists.
 __device__ __forceinline__ void raster_list_body(const RasterArgs &a, const VB &vb) {
     const RasterSide &S = a.s[vb.y];
     const int ntri = side_ntri(S);
@@ -172,6 +203,16 @@ __device__ __forceinline__ void raster_list_body(const RasterArgs &a, const VB &
         if (n <= 0) continue;
         const unsigned long long pos = atomicAdd(S.nunits, (unsigned long long)n);
         for (int j = 0; j < n && pos + j < (unsigned long long)a.unit_cap; ++j) S.ulist[pos + j] = make_int2(t, j + 1);
+    }
+    // the dense step's candidate lists: one warp per cell
+    if (a.lstride > 0) {
+        const int lane = threadIdx.x & 31;
+        const int ncell = a.gw * a.gh;
+        for (int c = vb.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell; c += vb.gx * (blockDim.x >> 5)) {
+            const int n = expand_cell_list(S.grid + (size_t)c * a.nw, a.nw, a.dmin, a.dmax,
+                                           S.clist + (size_t)c * a.lstride, lane);
+            if (lane == 0) S.ccount[c] = n;
+        }
     }
 }
 
@@ -235,7 +276,6 @@ __global__ void __launch_bounds__(256) raster_draw_kernel_b(const RasterArgs *__
     raster_draw_body(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
-constexpr int kListPad = 16;  // padding entries (2047) after the candidate list
 
 // Dense matching cost of two 16-byte descriptors added to acc: the SAD of
 // Sobel descriptors, or the Hamming distance of dense census records
@@ -257,8 +297,12 @@ constexpr int kKeyMul = 2047;
 // TPP = threads per pixel (1, 2 or 4): the TPP adjacent lanes of a pixel take
 // every TPP-th candidate of its list and of its plane window and merge their
 // keys with shuffles (min is order free, so every TPP gives the same result).
-template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
-    __shared__ __align__(16) uint16_t s_list[kMaxDisp + 1 + kListPad];
+// GLIST: the cell's candidate list was expanded into global memory by the
+// prior's list kernel (the CTA only waits for the prior table, at its
+// start); else warp 0 expands the mask into shared memory first.
+template <int TPP, bool CENSUS, bool GLIST>
+__device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
+    __shared__ __align__(16) uint16_t s_list[GLIST ? 1 : kMaxDisp + 1 + kListPad];
     __shared__ int s_P[kMaxSradius + 1];
     __shared__ int s_nlist;
 
@@ -278,35 +322,15 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
     // the key bias with the prior term (none with the prior switched off)
     if (tid <= kMaxSradius) s_P[tid] = kKeyBias + (a.prior_off ? 0 : a.P[tid]);
     // ---- candidate list of the cell, ascending ---------------------------------
-    if (!full && warp == 0) {
-        const int nw = a.nw;
-        const uint32_t *g = S.grid + (size_t)cell * nw;
-        // the words are taken one at a time: lane l places bit l of the word
-        // after the set bits below it, so the list comes out sorted with no
-        // per-lane bit loop
-        const uint32_t below = (1u << lane) - 1u;
-        int base = 0;
-        for (int w0 = 0; w0 < nw; w0 += 32) {
-            const int wi = w0 + lane;
-            uint32_t m = wi < nw ? __ldg(g + wi) : 0u;
-            // keep the bits inside [dmin, dmax]
-            const int lo = dmin - 32 * wi, hi = dmax - 32 * wi;
-            if (lo > 0) m &= lo >= 32 ? 0u : (0xFFFFFFFFu << lo);
-            if (hi < 31) m &= hi < 0 ? 0u : (0xFFFFFFFFu >> (31 - hi));
-            const int nk = min(32, nw - w0);
-            for (int k = 0; k < nk; ++k) {
-                const uint32_t mk = __shfl_sync(0xFFFFFFFFu, m, k);
-                if ((mk >> lane) & 1u) s_list[base + __popc(mk & below)] = (uint16_t)(32 * (w0 + k) + lane);
-                base += __popc(mk);
-            }
-        }
-        // pad with a disparity above every dmax
-        if (lane < kListPad) s_list[base + lane] = (uint16_t)2047;
-        if (lane == 0) s_nlist = base;
+    const uint16_t *__restrict__ glist = GLIST ? S.clist + (size_t)cell * a.lstride : nullptr;
+    if (!GLIST && !full && warp == 0) {
+        const int n = expand_cell_list(S.grid + (size_t)cell * a.nw, a.nw, dmin, dmax, s_list, lane);
+        if (lane == 0) s_nlist = n;
     }
     __syncthreads();
-    const int nlist = full ? 0 : s_nlist;
-    const int dlast = nlist > 0 ? (int)s_list[nlist - 1] : -1;  // largest entry
+    auto list_at = [&](int k) -> int { return GLIST ? (int)__ldg(glist + k) : (int)s_list[k]; };
+    const int nlist = full ? 0 : (GLIST ? __ldg(S.ccount + cell) : s_nlist);
+    const int dlast = nlist > 0 ? list_at(nlist - 1) : -1;  // largest entry
     const int sub = TPP > 1 ? (tid & (TPP - 1)) : 0;
 
     // ---- per-pixel argmin -------------------------------------------------------
@@ -347,7 +371,7 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
                             int lo = 0, hi = nlist;  // first entry above dlim
                             while (lo < hi) {
                                 const int mid = (lo + hi) >> 1;
-                                if ((int)s_list[mid] <= dlim)
+                                if (list_at(mid) <= dlim)
                                     lo = mid + 1;
                                 else
                                     hi = mid;
@@ -356,7 +380,7 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
                         }
 #pragma unroll 8
                         for (int k = sub; k < cnt; k += TPP) {
-                            const int d = s_list[k];
+                            const int d = list_at(k);
                             best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                         }
                         // the plane neighbourhood, the prior term in the accumulator
@@ -382,15 +406,15 @@ template <int TPP, bool CENSUS> __device__ __forceinline__ void cell_body(const 
     }
 }
 
-template <bool CENSUS> __global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) {
-    cell_body<1, CENSUS>(a, vb_single());
+template <bool CENSUS, bool GLIST> __global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) {
+    cell_body<1, CENSUS, GLIST>(a, vb_single());
 }
 
 // Batched launches: one launch per cost kind among the pairs.
 template <int TPP, bool CENSUS>
 __global__ void __launch_bounds__(1024) cell_kernel_b(const CellArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    cell_body<TPP, CENSUS>(slot_entry(tab, vm.stride, vb.slot), vb);
+    cell_body<TPP, CENSUS, false>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 template <bool CENSUS>
@@ -514,10 +538,18 @@ dim3 cell_grid(const CellArgs &a, int nsides) {
 }
 
 static elas_status launch_cells(const CellArgs &a, int nsides, cudaStream_t st) {
-    if (a.census)
-        cell_kernel<true><<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
-    else
-        cell_kernel<false><<<cell_grid(a, nsides), cell_threads(a.G, 1, 1), 0, st>>>(a);
+    const dim3 grid = cell_grid(a, nsides);
+    const int threads = cell_threads(a.G, 1, 1);
+    if (a.lstride > 0) {
+        if (a.census)
+            cell_kernel<true, true><<<grid, threads, 0, st>>>(a);
+        else
+            cell_kernel<false, true><<<grid, threads, 0, st>>>(a);
+    } else if (a.census) {
+        cell_kernel<true, false><<<grid, threads, 0, st>>>(a);
+    } else {
+        cell_kernel<false, false><<<grid, threads, 0, st>>>(a);
+    }
     return launch_status("cell_kernel");
 }
 
@@ -547,14 +579,26 @@ elas_status launch_dense(const uint8_t *descL, const uint8_t *descR, int w, int 
     return launch_cells(a, 1, st);
 }
 
+// Stride of a cell's candidate list: every disparity of the mask and the padding.
+static int cell_list_stride(const GridGeom &g) { return 32 * g.nw + kListPad; }
+
+// The cells' candidate lists of both sides, then their counts.
+static size_t cell_lists_bytes(int w, int h, const elas_params *p) {
+    const GridGeom g = grid_geom(w, h, p);
+    const size_t ncell = (size_t)g.gw * g.gh;
+    return 2 * align_up(sizeof(uint16_t) * ncell * cell_list_stride(g), 256) +
+           2 * align_up(sizeof(int32_t) * ncell, 256);
+}
+
 size_t dense_workspace(int w, int h, const elas_params *p) {
-    return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(max_triangles(w, h, p), 2);
+    return align_up(2 * (size_t)w * h * sizeof(int16_t), 256) + raster_scratch_bytes(max_triangles(w, h, p), 2) +
+           cell_lists_bytes(w, h, p);
 }
 
 elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                        const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
                        const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
-                       const int32_t *ntri_dev, DenseStage *o) {
+                       const int32_t *ntri_dev, DenseStage *o, bool cell_lists) {
     int16_t *dpL = reinterpret_cast<int16_t *>(ws);
     int16_t *dpR = dpL + (size_t)w * h;
     RasterSide sides[2] = {};
@@ -567,12 +611,40 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
     sides[1].right = 1;
     sides[1].dplane = dpR;
     sides[1].ntri_dev = ntri_dev ? ntri_dev + 1 : nullptr;
-    void *scratch = reinterpret_cast<char *>(ws) + align_up(2 * (size_t)w * h * sizeof(int16_t), 256);
+    char *scratch = reinterpret_cast<char *>(ws) + align_up(2 * (size_t)w * h * sizeof(int16_t), 256);
+    // the cells' candidate lists after the rasteriser's scratch: with
+    // cell_lists the prior's list kernel expands them and the argmin reads
+    // them (one pair: no CTA waits for its list); batches keep the
+    // expansion in each cell's CTA (one warp per cell there, so no wait)
+    const GridGeom gg = grid_geom(w, h, p);
+    const size_t ncell = (size_t)gg.gw * gg.gh;
+    const int lstride = cell_list_stride(gg);
+    char *lists = scratch + raster_scratch_bytes(max_triangles(w, h, p), 2);
+    uint16_t *clist[2];
+    int32_t *ccount[2];
+    for (int i = 0; i < 2; ++i) {
+        clist[i] = reinterpret_cast<uint16_t *>(lists);
+        lists += align_up(sizeof(uint16_t) * ncell * lstride, 256);
+    }
+    for (int i = 0; i < 2; ++i) {
+        ccount[i] = reinterpret_cast<int32_t *>(lists);
+        lists += align_up(sizeof(int32_t) * ncell, 256);
+    }
+    for (int i = 0; i < 2; ++i) {
+        sides[i].grid = i ? gridR : gridL;
+        sides[i].clist = clist[i];
+        sides[i].ccount = ccount[i];
+    }
     o->raster = raster_args(list, sides, 2, w, h, p, scratch, max_triangles(w, h, p));
+    o->raster.gw = gg.gw;
+    o->raster.gh = gg.gh;
+    o->raster.nw = gg.nw;
+    o->raster.lstride = cell_lists ? lstride : 0;
     int P[kMaxSradius + 1];
     elas_status s = fill_prior_table(p, P);
     if (s != ELAS_OK) return s;
     o->cell = cell_args(w, h, p, P);
+    o->cell.lstride = cell_lists ? lstride : 0;
     for (int i = 0; i < 2; ++i) {
         CellSide &cs = o->cell.s[i];
         cs.ref = reinterpret_cast<const uint4 *>(i ? descR : descL);
@@ -581,6 +653,8 @@ elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h,
         cs.dplane = i ? dpR : dpL;
         cs.out = i ? dR : dL;
         cs.dir = i ? +1 : -1;
+        cs.clist = clist[i];
+        cs.ccount = ccount[i];
     }
     return ELAS_OK;
 }
@@ -591,7 +665,7 @@ elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w,
                               cudaStream_t st, const int32_t *ntri_dev, cudaEvent_t after_prior) {
     DenseStage d;
     elas_status s = dense_args(descL, descR, w, h, p, list, triL, ntriL, triR, ntriR, gridL, gridR, dL, dR, ws,
-                               ntri_dev, &d);
+                               ntri_dev, &d, true);
     if (s != ELAS_OK) return s;
     if ((s = raster_meshes(d.raster, st)) != ELAS_OK) return s;
     if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");

@@ -58,7 +58,8 @@ DtArgs triangulate_args(const int16_t *list, const int32_t *count, int cap, int 
 elas_status dense_args(const uint8_t *descL, const uint8_t *descR, int w, int h, const elas_params *p,
                        const int16_t *list, const int32_t *triL, int ntriL, const int32_t *triR, int ntriR,
                        const uint32_t *gridL, const uint32_t *gridR, int16_t *dL, int16_t *dR, void *ws,
-                       const int32_t *ntri_dev, DenseStage *o);
+                       const int32_t *ntri_dev, DenseStage *o,
+                       bool cell_lists);
 int cell_threads(int G, int tpp, int ppt);
 int post_passes(const int16_t *d, int w, int h, const elas_params *p, float *out, void *ws, PostArgs *passes);
 bool post_fusable(const elas_params *p);

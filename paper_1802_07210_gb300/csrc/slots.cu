@@ -228,7 +228,7 @@ elas_status SlotPool::write_records(int id) {
     int32_t *nts[2] = {sl.counters + 1, sl.counters + 2};
     t.dt = triangulate_args(sl.list, sl.counters, sl.nc, w, h, tris, nts, sl.tri_cap, sl.ws_dt);
     elas_status s = dense_args(sl.descL, sl.descR, w, h, p, sl.list, tris[0], sl.tri_cap, tris[1], sl.tri_cap,
-                               sl.gridL, sl.gridR, sl.io_dL, sl.io_dR, sl.ws_dense, sl.counters + 1, &t.dense);
+                               sl.gridL, sl.gridR, sl.io_dL, sl.io_dR, sl.ws_dense, sl.counters + 1, &t.dense, false);
     if (s != ELAS_OK) return s;
     t.lr = LrArgs{sl.io_dL, sl.io_dR, w, h, p->lr_threshold, nullptr, nullptr};
     sl.fused = sl.post_on && post_fusable(p) ? 1 : 0;

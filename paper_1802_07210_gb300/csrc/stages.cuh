@@ -138,6 +138,11 @@ struct RasterSide {
     int32_t *ucnt;            // [cap] work units (box chunks) of each triangle
     int2 *ulist;              // [unit_cap] extra units: (triangle, chunk >= 1)
     unsigned long long *nunits;  // extra units of the mesh (the list is complete up to unit_cap)
+    // the dense step's candidate lists, expanded here from the grid vectors
+    // when lstride > 0 (the argmin runs after the prior)
+    const uint32_t *grid;  // [gh][gw][nw] grid-vector masks
+    uint16_t *clist;       // [gh * gw][lstride] ascending candidates, then 2047
+    int32_t *ccount;       // [gh * gw] candidates per cell
 };
 
 struct RasterArgs {
@@ -146,6 +151,7 @@ struct RasterArgs {
     int nsides;
     int w, h, dmin, dmax;
     int unit_cap;  // entries of each mesh's list of extra units
+    int gw, gh, nw, lstride;  // grid-vector cells and the candidate lists' stride (0: none)
 };
 
 struct CellSide {
@@ -154,12 +160,15 @@ struct CellSide {
     const int16_t *dplane;  // prior map (may be NULL with full range)
     int16_t *out;
     int dir;
+    const uint16_t *clist;  // the cells' candidate lists (CellArgs::lstride > 0)
+    const int32_t *ccount;
 };
 
 struct CellArgs {
     CellSide s[2];
     int w, h, G, gw, nw, dmin, dmax, sradius, match_texture, full, prior_off;
     int census;  // descriptors are 16-byte dense census records, Hamming cost (Sec. VI.A)
+    int lstride;  // > 0: candidate lists ready in clist (else each CTA expands its cell's mask)
     int P[kMaxSradius + 1];
 };
 
