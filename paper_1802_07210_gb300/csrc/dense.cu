@@ -300,7 +300,10 @@ constexpr int kKeyMul = 2047;
 // GLIST: the cell's candidate list was expanded into global memory by the
 // prior's list kernel (the CTA only waits for the prior table, at its
 // start); else warp 0 expands the mask into shared memory first.
-template <int TPP, bool CENSUS, bool GLIST>
+// PF: the reference descriptor and prior of a thread's next pixel are
+// loaded while the current one is matched (batches, where a thread walks
+// many pixels; one pair has one pixel per thread).
+template <int TPP, bool CENSUS, bool GLIST, bool PF>
 __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     __shared__ __align__(16) uint16_t s_list[GLIST ? 1 : kMaxDisp + 1 + kListPad];
     __shared__ int s_P[kMaxSradius + 1];
@@ -339,57 +342,74 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     const int ppb = blockDim.x / TPP;  // pixels per pass of the CTA
     const int sdy = ppb / cw, sdx = ppb - sdy * cw;
     int px = (tid / TPP) % cw, py = (tid / TPP) / cw;
+    auto inner = [&](int qx, int qy) { return qx >= 2 && qx <= W - 3 && qy >= 2 && qy <= H - 3; };
+    uint4 r_nx = make_uint4(0u, 0u, 0u, 0u);
+    int dp_nx = -1;
+    if (PF && tid / TPP < npx && inner(x0 + px, y0 + py)) {
+        const size_t i0 = (size_t)(y0 + py) * W + x0 + px;
+        r_nx = __ldg(ref + i0);
+        if (!full) dp_nx = (int)__ldg(S.dplane + i0);
+    }
     for (int pb = 0; pb < npx; pb += ppb) {
         const int p = pb + tid / TPP;
+        const bool live = p < npx;
+        const int x = x0 + px, y = y0 + py;
+        const size_t row = (size_t)y * W;
+        const bool in = live && inner(x, y);
+        uint4 r = r_nx;
+        int dp = full ? -1 : dp_nx;
+        if (!PF && in) {
+            r = __ldg(ref + row + x);
+            if (!full) dp = (int)__ldg(S.dplane + row + x);
+        }
+        // the next pixel's position and loads
+        px += sdx;
+        py += sdy;
+        if (px >= cw) {
+            px -= cw;
+            ++py;
+        }
+        if (PF && p + ppb < npx && inner(x0 + px, y0 + py)) {
+            const size_t i1 = (size_t)(y0 + py) * W + x0 + px;
+            r_nx = __ldg(ref + i1);
+            if (!full) dp_nx = (int)__ldg(S.dplane + i1);
+        }
         int best = 0x7FFFFFFF;
-        bool live = false;
-        size_t row = 0;
-        int x = 0;
-        if (p < npx) {
-            x = x0 + px;
-            const int y = y0 + py;
-            row = (size_t)y * W;
-            live = true;
-            if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
-                const uint4 r = __ldg(ref + row + x);
-                const int dp = full ? -1 : (int)__ldg(S.dplane + row + x);
-                // census records have no texture measure: no texture test
-                if ((CENSUS || (int)texture16(r) >= a.match_texture) && (full || dp >= 0)) {
-                    // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
-                    // (the lower bound of the first condition is <= 0; the list's
-                    // padding value 2047 exceeds every dmax)
-                    const int dlim = min(dmax, dir < 0 ? x - 2 : W - 3 - x);
-                    const uint4 *orow = oth + row + x;
-                    if (full) {
-                        for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
-                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
-                        }
-                    } else {
-                        // the admissible entries are a prefix of the ascending list
-                        int cnt = nlist;
-                        if (dlim < dlast) {
-                            int lo = 0, hi = nlist;  // first entry above dlim
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (list_at(mid) <= dlim)
-                                    lo = mid + 1;
-                                else
-                                    hi = mid;
-                            }
-                            cnt = lo;
-                        }
-#pragma unroll 8
-                        for (int k = sub; k < cnt; k += TPP) {
-                            const int d = list_at(k);
-                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
-                        }
-                        // the plane neighbourhood, the prior term in the accumulator
-                        const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
-#pragma unroll 5
-                        for (int d = lo + sub; d <= hi; d += TPP)
-                            best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), s_P[abs(d - dp)]) * kKeyMul + d);
-                    }
+        // census records have no texture measure: no texture test
+        if (in && (CENSUS || (int)texture16(r) >= a.match_texture) && (full || dp >= 0)) {
+            // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
+            // (the lower bound of the first condition is <= 0; the list's
+            // padding value 2047 exceeds every dmax)
+            const int dlim = min(dmax, dir < 0 ? x - 2 : W - 3 - x);
+            const uint4 *orow = oth + row + x;
+            if (full) {
+                for (int d = dmin + sub; d <= dlim; d += TPP) {  // no plane, so no prior term
+                    best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                 }
+            } else {
+                // the admissible entries are a prefix of the ascending list
+                int cnt = nlist;
+                if (dlim < dlast) {
+                    int lo = 0, hi = nlist;  // first entry above dlim
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (list_at(mid) <= dlim)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    cnt = lo;
+                }
+#pragma unroll 8
+                for (int k = sub; k < cnt; k += TPP) {
+                    const int d = list_at(k);
+                    best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
+                }
+                // the plane neighbourhood, the prior term in the accumulator
+                const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
+#pragma unroll 5
+                for (int d = lo + sub; d <= hi; d += TPP)
+                    best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), s_P[abs(d - dp)]) * kKeyMul + d);
             }
         }
         if (TPP > 1) {
@@ -397,24 +417,18 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
             for (int o = TPP / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
         }
         if (live && sub == 0) S.out[row + x] = (int16_t)(best != 0x7FFFFFFF ? (best % kKeyMul) : -1);
-        px += sdx;
-        py += sdy;
-        if (px >= cw) {
-            px -= cw;
-            ++py;
-        }
     }
 }
 
-template <bool CENSUS, bool GLIST> __global__ void __launch_bounds__(1024) cell_kernel(CellArgs a) {
-    cell_body<1, CENSUS, GLIST>(a, vb_single());
+template <bool CENSUS, bool GLIST> __global__ void __launch_bounds__(1024, 2) cell_kernel(CellArgs a) {
+    cell_body<1, CENSUS, GLIST, false>(a, vb_single());
 }
 
 // Batched launches: one launch per cost kind among the pairs.
 template <int TPP, bool CENSUS>
 __global__ void __launch_bounds__(1024) cell_kernel_b(const CellArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    cell_body<TPP, CENSUS, false>(slot_entry(tab, vm.stride, vb.slot), vb);
+    cell_body<TPP, CENSUS, false, true>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 template <bool CENSUS>
