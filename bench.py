@@ -969,7 +969,7 @@ def dense_work(work, prm, w, h):
 # DRAM bytes (read + write) of one cell_kernel launch, from one ncu capture of
 # the kernel as it is now (dram__bytes_read.sum + dram__bytes_write.sum);
 # to be taken again whenever the kernel changes.
-DENSE_TRAFFIC_BYTES = {"640x480_D256": 11034368}
+DENSE_TRAFFIC_BYTES = {"640x480_D256": 11162112}
 DENSE_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                         "--clock-control none -k regex:cell_kernel -s 2 -c 1 on python bench.py --steps 3 --warmup 3 "
                         "--no-cpu-baseline --skip-extra (L2 flushed before each step; reads only, below the minimum "
