@@ -489,6 +489,9 @@ typedef struct {
     int32_t dense_threads_per_pixel; /* dense argmin threads per pixel: 1, 2, 4 */
     int32_t use_graph;               /* capture and replay a CUDA graph       */
     int32_t dense_pixels_per_thread; /* dense argmin pixels per thread: 1, 2, 4, 8, 16 */
+    int32_t dense_fused;             /* 1: plane prior and dense argmin as one persistent
+                                        cooperative launch (one warp per cell); 0: one
+                                        launch per kernel */
 } elas_batch_config;
 
 elas_status elas_batch_create(int32_t n, const int32_t *w, const int32_t *h, const elas_params *params,

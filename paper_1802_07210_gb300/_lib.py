@@ -55,7 +55,7 @@ class PipelineStats(C.Structure):
 class BatchConfig(C.Structure):
     _fields_ = [("desc_tile_rows", C.c_int32), ("support_warps", C.c_int32),
                 ("dense_threads_per_pixel", C.c_int32), ("use_graph", C.c_int32),
-                ("dense_pixels_per_thread", C.c_int32)]
+                ("dense_pixels_per_thread", C.c_int32), ("dense_fused", C.c_int32)]
 
 
 class ServerConfig(C.Structure):

@@ -317,7 +317,7 @@ class Batch:
         cur = self.config()
         cur.update(kw)
         cfg = BatchConfig(cur["desc_tile_rows"], cur["support_warps"], cur["dense_threads_per_pixel"],
-                          cur["use_graph"], cur["dense_pixels_per_thread"])
+                          cur["use_graph"], cur["dense_pixels_per_thread"], cur.get("dense_fused", 0))
         check(lib().elas_batch_set_config(self._h, C.byref(cfg)))
 
     def _dev_arrays(self, imgL, imgR, dL, dR, post):

@@ -64,7 +64,8 @@ void release(elas_batch *b) {
 }
 
 std::vector<int> signature(const elas_batch *b) {
-    std::vector<int> sig{b->knobs.desc_rows, b->knobs.support_warps, b->knobs.dense_tpp, b->knobs.dense_ppt};
+    std::vector<int> sig{b->knobs.desc_rows, b->knobs.support_warps, b->knobs.dense_tpp, b->knobs.dense_ppt,
+                         b->knobs.dense_fused};
     for (int id : b->ids) sig.push_back(b->pool[id].npass * 2 + b->pool[id].fused);
     return sig;
 }
@@ -140,7 +141,8 @@ bool knob_ok(const Knobs &k) {
     return (k.desc_rows == 12 || k.desc_rows == 24 || k.desc_rows == 36) &&
            (k.support_warps == 4 || k.support_warps == 8 || k.support_warps == 16) &&
            (k.dense_tpp == 1 || k.dense_tpp == 2 || k.dense_tpp == 4) &&
-           (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8 || k.dense_ppt == 16);
+           (k.dense_ppt == 1 || k.dense_ppt == 2 || k.dense_ppt == 4 || k.dense_ppt == 8 || k.dense_ppt == 16) &&
+           (k.dense_fused == 0 || k.dense_fused == 1);
 }
 
 }  // namespace
@@ -190,6 +192,7 @@ extern "C" elas_status elas_batch_get_config(const elas_batch *b, elas_batch_con
     cfg->support_warps = b->knobs.support_warps;
     cfg->dense_threads_per_pixel = b->knobs.dense_tpp;
     cfg->dense_pixels_per_thread = b->knobs.dense_ppt;
+    cfg->dense_fused = b->knobs.dense_fused;
     cfg->use_graph = b->use_graph;
     return ELAS_OK;
 }
@@ -201,9 +204,11 @@ extern "C" elas_status elas_batch_set_config(elas_batch *b, const elas_batch_con
     k.support_warps = cfg->support_warps;
     k.dense_tpp = cfg->dense_threads_per_pixel;
     k.dense_ppt = cfg->dense_pixels_per_thread;
+    k.dense_fused = cfg->dense_fused;
     if (!knob_ok(k))
-        return fail(ELAS_ERR_INVALID_ARG, "config %d/%d/%d/%d outside {4,8,16}/{4,8,16}/{1,2,4}/{1,2,4,8}",
-                    k.desc_rows, k.support_warps, k.dense_tpp, k.dense_ppt);
+        return fail(ELAS_ERR_INVALID_ARG,
+                    "config %d/%d/%d/%d/%d outside {12,24,36}/{4,8,16}/{1,2,4}/{1,2,4,8,16}/{0,1}", k.desc_rows,
+                    k.support_warps, k.dense_tpp, k.dense_ppt, k.dense_fused);
     b->knobs = k;
     b->use_graph = cfg->use_graph ? 1 : 0;
     return ELAS_OK;
@@ -278,22 +283,28 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
             for (int j = 0; j < i; ++j) cudaEventDestroy(mk.ev[j]);
             return launch_status("tune events");
         }
-    // stage index of each knob (time between marks stage and stage + 1)
+    // the stages each knob is timed over (between marks first and last); the
+    // persistent prior + argmin launch is weighed against the separate
+    // launches over both stages, with the shapes found for the latter
     struct Axis {
         int *field;
-        int stage;
+        int first, last;
+        int nv;
         int values[3];
     };
     Knobs k = b->knobs;
-    Axis axes[4] = {{&k.desc_rows, 0, {12, 24, 36}},
-                    {&k.support_warps, 1, {4, 8, 16}},
-                    {&k.dense_tpp, 4, {1, 2, 4}},
-                    {&k.dense_ppt, 4, {4, 8, 16}}};
+    k.dense_fused = 0;
+    Axis axes[5] = {{&k.desc_rows, 0, 1, 3, {12, 24, 36}},
+                    {&k.support_warps, 1, 2, 3, {4, 8, 16}},
+                    {&k.dense_tpp, 4, 5, 3, {1, 2, 4}},
+                    {&k.dense_ppt, 4, 5, 3, {4, 8, 16}},
+                    {&k.dense_fused, 3, 5, 2, {0, 1, 0}}};
     const int reps = 3;
     for (Axis &ax : axes) {
         float best_ms = 1e30f;
         int best_v = *ax.field;
-        for (int v : ax.values) {
+        for (int vi = 0; vi < ax.nv; ++vi) {
+            const int v = ax.values[vi];
             *ax.field = v;
             float tot = 0.0f;
             for (int r = 0; r <= reps && s == ELAS_OK; ++r) {  // r = 0 warms up
@@ -304,7 +315,7 @@ extern "C" elas_status elas_batch_tune(elas_batch *b, const uint8_t *const *imgL
                     break;
                 }
                 float ms = 0.0f;
-                cudaEventElapsedTime(&ms, mk.ev[ax.stage], mk.ev[ax.stage + 1]);
+                cudaEventElapsedTime(&ms, mk.ev[ax.first], mk.ev[ax.last]);
                 if (r > 0) tot += ms;
             }
             if (s != ELAS_OK) break;

@@ -46,8 +46,8 @@ __device__ __forceinline__ VB vb_single() {
     return v;
 }
 
-__device__ __forceinline__ VB vb_batch(const VMap &m) {
-    const int b = blockIdx.x;
+// Pair and local block of block b of a batched grid.
+__device__ __forceinline__ VB vb_at(const VMap &m, int b) {
     // last pair whose first block is <= b (pairs with no blocks are skipped
     // because a later pair starts at the same offset)
     int lo = 0, hi = m.n - 1;
@@ -71,6 +71,8 @@ __device__ __forceinline__ VB vb_batch(const VMap &m) {
     v.x = r - v.y * v.gx;
     return v;
 }
+
+__device__ __forceinline__ VB vb_batch(const VMap &m) { return vb_at(m, blockIdx.x); }
 
 // Entry of `slot` in a table whose entries are `stride` bytes apart (the
 // tables are arrays of per-slot records; tab points at slot 0's entry).
@@ -96,6 +98,6 @@ inline bool vmap_add(VMap &m, int slot, dim3 g) {
     ++m.n;
     return true;
 }
-inline int vmap_total(const VMap &m) { return m.off[m.n]; }
+__host__ __device__ inline int vmap_total(const VMap &m) { return m.off[m.n]; }
 
 }  // namespace elas

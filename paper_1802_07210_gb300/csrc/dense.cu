@@ -31,6 +31,8 @@
 //                      result is the argmin over the union.  The list is
 //                      uniform across the CTA: no divergence, broadcast
 //                      shared loads.
+#include <cooperative_groups.h>
+
 #include "launch.cuh"
 
 namespace elas {
@@ -303,11 +305,22 @@ constexpr int kKeyMul = 2047;
 // PF: the reference descriptor and prior of a thread's next pixel are
 // loaded while the current one is matched (batches, where a thread walks
 // many pixels; one pair has one pixel per thread).
-template <int TPP, bool CENSUS, bool GLIST, bool PF>
+// WARPC: the cell belongs to one warp of the CTA (the persistent prior and
+// argmin kernel runs kFusedCellWarps cells per CTA): the warp keeps its own
+// list and prior table in shared memory and synchronises alone.
+constexpr int kFusedThreads = 256;
+constexpr int kFusedCellWarps = kFusedThreads / 32;
+
+template <int TPP, bool CENSUS, bool GLIST, bool PF, bool WARPC = false>
 __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
-    __shared__ __align__(16) uint16_t s_list[GLIST ? 1 : kMaxDisp + 1 + kListPad];
-    __shared__ int s_P[kMaxSradius + 1];
-    __shared__ int s_nlist;
+    constexpr int NG = WARPC ? kFusedCellWarps : 1;  // cell groups of the CTA
+    __shared__ __align__(16) uint16_t s_list_g[NG][GLIST ? 1 : kMaxDisp + 1 + kListPad];
+    __shared__ int s_P_g[NG][kMaxSradius + 1];
+    __shared__ int s_nlist_g[NG];
+    const int grp_of = WARPC ? (int)(threadIdx.x >> 5) : 0;
+    uint16_t *s_list = s_list_g[grp_of];
+    int *s_P = s_P_g[grp_of];
+    int &s_nlist = s_nlist_g[grp_of];
 
     const CellSide &S = a.s[vb.z];
     const int W = a.w, H = a.h, G = a.G;
@@ -316,7 +329,10 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     const int x0 = cx * G, y0 = cy * G;
     const int cw = min(G, W - x0), ch = min(G, H - y0);
     const int npx = cw * ch;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // threads of the cell: the CTA, or one warp
+    const int tid = WARPC ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int nthreads = WARPC ? 32 : (int)blockDim.x;
+    const int lane = threadIdx.x & 31, warp = WARPC ? 0 : (int)(threadIdx.x >> 5);
     const int cell = cy * a.gw + cx;
     const uint4 *__restrict__ ref = S.ref;
     const uint4 *__restrict__ oth = S.oth;
@@ -330,7 +346,10 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
         const int n = expand_cell_list(S.grid + (size_t)cell * a.nw, a.nw, dmin, dmax, s_list, lane);
         if (lane == 0) s_nlist = n;
     }
-    __syncthreads();
+    if (WARPC)
+        __syncwarp();
+    else
+        __syncthreads();
     auto list_at = [&](int k) -> int { return GLIST ? (int)__ldg(glist + k) : (int)s_list[k]; };
     const int nlist = full ? 0 : (GLIST ? __ldg(S.ccount + cell) : s_nlist);
     const int dlast = nlist > 0 ? list_at(nlist - 1) : -1;  // largest entry
@@ -339,7 +358,7 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     // ---- per-pixel argmin -------------------------------------------------------
     // pixel p of the cell is (x0 + p % cw, y0 + p / cw); a thread's pixels
     // advance by ppb, so after one division the position steps incrementally
-    const int ppb = blockDim.x / TPP;  // pixels per pass of the CTA
+    const int ppb = nthreads / TPP;  // pixels per pass of the cell's threads
     const int sdy = ppb / cw, sdx = ppb - sdy * cw;
     int px = (tid / TPP) % cw, py = (tid / TPP) / cw;
     auto inner = [&](int qx, int qy) { return qx >= 2 && qx <= W - 3 && qy >= 2 && qy <= H - 3; };
@@ -348,7 +367,7 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     if (PF && tid / TPP < npx && inner(x0 + px, y0 + py)) {
         const size_t i0 = (size_t)(y0 + py) * W + x0 + px;
         r_nx = __ldg(ref + i0);
-        if (!full) dp_nx = (int)__ldg(S.dplane + i0);
+        if (!full) dp_nx = (int)__ldcg(S.dplane + i0);
     }
     for (int pb = 0; pb < npx; pb += ppb) {
         const int p = pb + tid / TPP;
@@ -360,7 +379,7 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
         int dp = full ? -1 : dp_nx;
         if (!PF && in) {
             r = __ldg(ref + row + x);
-            if (!full) dp = (int)__ldg(S.dplane + row + x);
+            if (!full) dp = (int)__ldcg(S.dplane + row + x);
         }
         // the next pixel's position and loads
         px += sdx;
@@ -372,7 +391,7 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
         if (PF && p + ppb < npx && inner(x0 + px, y0 + py)) {
             const size_t i1 = (size_t)(y0 + py) * W + x0 + px;
             r_nx = __ldg(ref + i1);
-            if (!full) dp_nx = (int)__ldg(S.dplane + i1);
+            if (!full) dp_nx = (int)__ldcg(S.dplane + i1);
         }
         int best = 0x7FFFFFFF;
         // census records have no texture measure: no texture test
@@ -440,6 +459,66 @@ static void cell_launch_b(const CellArgs *tab, const VMap &m, int tpp, int threa
         cell_kernel_b<2, CENSUS><<<total, threads, 0, st>>>(tab, m);
     else
         cell_kernel_b<4, CENSUS><<<total, threads, 0, st>>>(tab, m);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent prior + argmin for a batch (one cooperative launch): the CTAs
+// walk the setup blocks of every pair, meet at a grid barrier, the list
+// blocks, a barrier, the draw blocks, a barrier, then the cells, one warp
+// per cell (kFusedCellWarps cells per item).  The bodies are those of the
+// separate launches, so the maps are the same; every value one stage writes
+// and a later one reads is read through L2 or with plain loads after the
+// barrier.
+// ---------------------------------------------------------------------------
+struct DenseFusedArgs {
+    const RasterArgs *rtab;
+    const CellArgs *ctab;
+    VMap setup, list, draw;
+    VMap cells[2];  // Sobel/SAD and census pairs: items of kFusedCellWarps cells
+};
+
+// Cells of item b of `m`: warp k takes cell kFusedCellWarps * item + k of
+// the pair's cells (both reference images, left first).
+template <int TPP, bool CENSUS>
+__device__ __forceinline__ void fused_cells(const DenseFusedArgs &f, const VMap &m, int b) {
+    const VB vb = vb_at(m, b);
+    const CellArgs &a = slot_entry(f.ctab, m.stride, vb.slot);
+    const int gh = (a.h + a.G - 1) / a.G, per_side = a.gw * gh;
+    const int c = vb.x * kFusedCellWarps + (int)(threadIdx.x >> 5);
+    if (c >= 2 * per_side) return;
+    VB w;
+    w.slot = vb.slot;
+    w.z = c / per_side;
+    const int r = c - w.z * per_side;
+    w.y = r / a.gw;
+    w.x = r - w.y * a.gw;
+    w.gx = a.gw;
+    w.gy = gh;
+    w.gz = 2;
+    cell_body<TPP, CENSUS, false, true, true>(a, w);
+}
+
+template <int TPP> __global__ void __launch_bounds__(kFusedThreads, 4) dense_fused_kernel_b(DenseFusedArgs f) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int nb = gridDim.x;
+    for (int b = blockIdx.x; b < vmap_total(f.setup); b += nb) {
+        const VB vb = vb_at(f.setup, b);
+        raster_setup_body(slot_entry(f.rtab, f.setup.stride, vb.slot), vb);
+    }
+    grid.sync();
+    for (int b = blockIdx.x; b < vmap_total(f.list); b += nb) {
+        const VB vb = vb_at(f.list, b);
+        raster_list_body(slot_entry(f.rtab, f.list.stride, vb.slot), vb);
+    }
+    grid.sync();
+    for (int b = blockIdx.x; b < vmap_total(f.draw); b += nb) {
+        const VB vb = vb_at(f.draw, b);
+        raster_draw_body(slot_entry(f.rtab, f.draw.stride, vb.slot), vb);
+    }
+    grid.sync();
+    for (int b = blockIdx.x; b < vmap_total(f.cells[0]); b += nb) fused_cells<TPP, false>(f, f.cells[0], b);
+    for (int b = blockIdx.x; b < vmap_total(f.cells[1]); b += nb) fused_cells<TPP, true>(f, f.cells[1], b);
 }
 
 // ---------------------------------------------------------------------------
@@ -688,8 +767,41 @@ elas_status launch_dense_both(const uint8_t *descL, const uint8_t *descR, int w,
 
 // Batched plane prior and dense matching over the pairs of `pairs`; host
 // is the host copy of the table.
+// The persistent kernel for threads-per-pixel tpp: CTAs resident at once
+// (every CTA of a cooperative launch must be), queried once per device.
+template <int TPP> static int fused_blocks() {
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && per_sm[dev] == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dense_fused_kernel_b<TPP>, kFusedThreads, 0) !=
+            cudaSuccess)
+            n = 0;
+        per_sm[dev] = n;
+    }
+    return (dev >= 0 && dev < 64 ? per_sm[dev] : 0) * sm_count();
+}
+
+template <int TPP> static elas_status launch_fused(DenseFusedArgs &f, cudaStream_t st) {
+    const int blocks = fused_blocks<TPP>();
+    if (blocks <= 0) return fail(ELAS_ERR_CUDA, "no resident CTA for the persistent dense kernel");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, dense_fused_kernel_b<TPP>, f) != cudaSuccess) return launch_status("dense_fused_kernel_b");
+    return launch_status("dense_fused_kernel_b");
+}
+
 elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp, int ppt,
-                           cudaStream_t st, cudaEvent_t after_prior) {
+                           cudaStream_t st, cudaEvent_t after_prior, bool fused) {
     if (pairs.n == 0) return ELAS_OK;
     if (tpp != 1 && tpp != 2 && tpp != 4) return fail(ELAS_ERR_INVALID_ARG, "dense threads per pixel %d", tpp);
     if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8 && ppt != 16)
@@ -712,6 +824,28 @@ elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const V
         vmap_add(m_draw, slot, dim3(per_pair, r.nsides));
         vmap_add(m_cell[d.cell.census ? 1 : 0], slot, cell_grid(d.cell, 2));
         threads = max(threads, cell_threads(d.cell.G, tpp, ppt));
+    }
+    if (fused) {
+        // one persistent launch: the prior and the argmin, one warp per cell
+        DenseFusedArgs f;
+        f.rtab = t.raster;
+        f.ctab = t.cell;
+        f.setup = m_setup;
+        f.list = m_list;
+        f.draw = m_draw;
+        vmap_clear(f.cells[0], pairs.stride);
+        vmap_clear(f.cells[1], pairs.stride);
+        for (int i = 0; i < pairs.n; ++i) {
+            const DenseStage &d = slot_entry(host, pairs.stride, pairs.slot[i]);
+            const dim3 g = cell_grid(d.cell, 2);
+            vmap_add(f.cells[d.cell.census ? 1 : 0], pairs.slot[i],
+                     dim3((g.x * g.y * g.z + kFusedCellWarps - 1) / kFusedCellWarps));
+        }
+        elas_status s = tpp == 1 ? launch_fused<1>(f, st) : (tpp == 2 ? launch_fused<2>(f, st) : launch_fused<4>(f, st));
+        if (s != ELAS_OK) return s;
+        // the prior and the argmin share the launch: the mark follows it
+        if (after_prior && record_mark(after_prior, st) != cudaSuccess) return launch_status("prior mark");
+        return ELAS_OK;
     }
     raster_setup_kernel_b<<<vmap_total(m_setup), 256, 0, st>>>(t.raster, m_setup);
     raster_list_kernel_b<<<vmap_total(m_list), 256, 0, st>>>(t.raster, m_list);

@@ -82,8 +82,9 @@ elas_status launch_support_b(const SupportTables &t, const SupportStage *host, c
 elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VMap &pairs, int nsides,
                                  int32_t *counter, cudaStream_t st);
 // after_prior (may be NULL) is recorded between the prior and the argmin.
+// fused: the prior and the argmin as one persistent cooperative launch.
 elas_status launch_dense_b(const DenseTables &t, const DenseStage *host, const VMap &pairs, int tpp, int ppt,
-                           cudaStream_t st, cudaEvent_t after_prior = nullptr);
+                           cudaStream_t st, cudaEvent_t after_prior = nullptr, bool fused = false);
 // post_tab[k]: table of post-processing pass k (k < 4); npass[i]: passes of
 // pair i of `pairs`; fused[i]: pair i uses the fused kernel (table fused_tab).
 elas_status launch_lr_post_b(const LrArgs *lr_tab, const LrArgs *host_lr, const PostArgs *const *post_tab,

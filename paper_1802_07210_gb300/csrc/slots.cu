@@ -317,7 +317,8 @@ elas_status SlotPool::launch(const int *ids, int n, const Knobs &k, cudaStream_t
     if ((s = launch_triangulate_b(&D->dt, &H->dt, pairs, 2, counter, st)) != ELAS_OK) return s;
     mark(3);
     const DenseTables dn{&D->dense.raster, &D->dense.cell};
-    if ((s = launch_dense_b(dn, &H->dense, pairs, k.dense_tpp, k.dense_ppt, st, marks ? marks->ev[4] : nullptr)) != ELAS_OK)
+    if ((s = launch_dense_b(dn, &H->dense, pairs, k.dense_tpp, k.dense_ppt, st, marks ? marks->ev[4] : nullptr,
+                            k.dense_fused != 0)) != ELAS_OK)
         return s;
     mark(5);
     const PostArgs *post_tabs[4] = {&D->post[0], &D->post[1], &D->post[2], &D->post[3]};

@@ -21,6 +21,7 @@ struct Knobs {
     int support_warps = 8;  // lattice candidates (warps) per support CTA: 4, 8, 16
     int dense_tpp = 1;      // threads per pixel in the dense argmin: 1, 2, 4
     int dense_ppt = 4;      // pixels per thread (per pixel group) in the dense argmin: 1, 2, 4, 8
+    int dense_fused = 0;    // 1: prior and argmin in one persistent cooperative launch
 };
 
 // The stage arguments of one slot, one record per slot in the tables.

@@ -138,16 +138,20 @@ def test_mixed_batch_equals_per_pair_path(mix):
 
 
 KNOBS = [
-    dict(desc_tile_rows=36, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=1),
-    dict(desc_tile_rows=24, support_warps=16, dense_threads_per_pixel=2, dense_pixels_per_thread=2),
-    dict(desc_tile_rows=12, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=1),
-    dict(desc_tile_rows=24, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=4),
-    dict(desc_tile_rows=36, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=4),
-    dict(desc_tile_rows=12, support_warps=16, dense_threads_per_pixel=1, dense_pixels_per_thread=8),
+    dict(desc_tile_rows=36, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=1, dense_fused=0),
+    dict(desc_tile_rows=24, support_warps=16, dense_threads_per_pixel=2, dense_pixels_per_thread=2, dense_fused=0),
+    dict(desc_tile_rows=12, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=1, dense_fused=0),
+    dict(desc_tile_rows=24, support_warps=4, dense_threads_per_pixel=1, dense_pixels_per_thread=4, dense_fused=0),
+    dict(desc_tile_rows=36, support_warps=8, dense_threads_per_pixel=4, dense_pixels_per_thread=4, dense_fused=0),
+    dict(desc_tile_rows=12, support_warps=16, dense_threads_per_pixel=1, dense_pixels_per_thread=8, dense_fused=0),
+    # the prior and the argmin as one persistent cooperative launch
+    dict(desc_tile_rows=24, support_warps=8, dense_threads_per_pixel=1, dense_pixels_per_thread=16, dense_fused=1),
+    dict(desc_tile_rows=24, support_warps=8, dense_threads_per_pixel=2, dense_pixels_per_thread=16, dense_fused=1),
+    dict(desc_tile_rows=12, support_warps=4, dense_threads_per_pixel=4, dense_pixels_per_thread=4, dense_fused=1),
 ]
 
 
-@pytest.mark.parametrize("knobs", KNOBS, ids=lambda k: "%d-%d-%d-%d" % tuple(k.values()))
+@pytest.mark.parametrize("knobs", KNOBS, ids=lambda k: "%d-%d-%d-%d-%d" % tuple(k.values()))
 @pytest.mark.parametrize("graph", [0, 1])
 def test_knob_settings_give_identical_results(mix, knobs, graph):
     b = _batch(mix)
@@ -170,6 +174,7 @@ def test_tuner_picks_valid_knobs(mix):
     assert cfg["support_warps"] in (4, 8, 16)
     assert cfg["dense_threads_per_pixel"] in (1, 2, 4)
     assert cfg["dense_pixels_per_thread"] in (1, 2, 4, 8, 16)
+    assert cfg["dense_fused"] in (0, 1)
     assert b.config()["desc_tile_rows"] == cfg["desc_tile_rows"]
     b.run(imgL, imgR, dL, dR, post)
     _check(mix, dL, dR, post, "tuned")

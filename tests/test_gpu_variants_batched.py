@@ -70,9 +70,13 @@ def _check(it, dL, dR, post, what):
         assert np.abs(post - ref["post"]).max() <= 1e-4, (what, it["name"])
 
 
-def test_variant_mix_in_one_batch(mix):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_variant_mix_in_one_batch(mix, fused):
+    """fused: the plane prior and the dense argmin (Sobel/SAD and census
+    pairs alike) in one persistent cooperative launch."""
     B = _B()
     b = B.Batch([(it["L"].shape[1], it["L"].shape[0]) for it in mix], [it["prm"] for it in mix])
+    b.set_config(dense_fused=fused)
     dL = [torch.empty(it["L"].shape, dtype=torch.int16, device="cuda") for it in mix]
     dR = [torch.empty_like(t) for t in dL]
     post = [torch.empty(it["L"].shape, dtype=torch.float32, device="cuda") if it["post"] else None for it in mix]
