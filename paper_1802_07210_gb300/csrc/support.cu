@@ -63,16 +63,13 @@ __device__ __forceinline__ Win load_win(const uint4 *__restrict__ d, int w, int 
     return r;
 }
 
-// Window cost: the SAD of the four descriptors (VACC: the vabsdiff4 form,
-// else the dp4a form; the sums are equal), or the Hamming distance of the
-// census bits.  Both stay below 2^15.
-template <bool CENSUS, bool VACC>
-__device__ __forceinline__ uint32_t win_cost(const Win &a, const Win &b) {
+// Window cost: the SAD of the four descriptors (accumulating byte-SIMD
+// absolute differences), or the Hamming distance of the census bits.  Both
+// stay below 2^15.
+template <bool CENSUS> __device__ __forceinline__ uint32_t win_cost(const Win &a, const Win &b) {
     if (CENSUS) return ham16(a.q[0], b.q[0]) + ham16(a.q[1], b.q[1]);
-    if (VACC)
-        return sad16_vacc(a.q[0], b.q[0]) + sad16_vacc(a.q[1], b.q[1]) + sad16_vacc(a.q[2], b.q[2]) +
-               sad16_vacc(a.q[3], b.q[3]);
-    return sad16(a.q[0], b.q[0]) + sad16(a.q[1], b.q[1]) + sad16(a.q[2], b.q[2]) + sad16(a.q[3], b.q[3]);
+    return sad16_vacc(a.q[0], b.q[0]) + sad16_vacc(a.q[1], b.q[1]) + sad16_vacc(a.q[2], b.q[2]) +
+           sad16_vacc(a.q[3], b.q[3]);
 }
 
 // The texture test of a window: Sobel windows need texture >= support_texture;
@@ -100,8 +97,9 @@ __device__ __forceinline__ int warp_best_disparity(const uint4 *__restrict__ oth
     if (hi - lo + 1 < 2) return -1;
     uint32_t m1 = 0xFFFFFFFFu, m2 = 0xFFFFFFFFu;
     int d1 = -1;
+#pragma unroll 2
     for (int d = lo + lane; d <= hi; d += 32) {
-        const uint32_t c = win_cost<CENSUS, false>(a, load_win<CENSUS>(oth, w, u + dir * d, v));
+        const uint32_t c = win_cost<CENSUS>(a, load_win<CENSUS>(oth, w, u + dir * d, v));
         if (c < m1) {
             m2 = m1;
             m1 = c;
@@ -243,7 +241,7 @@ template <bool CENSUS> __device__ __forceinline__ void support_match_row_body(co
             Win lw;
 #pragma unroll
             for (int i = 0; i < 4; ++i) lw.q[i] = s_desc[4 * k + i];
-            const uint32_t c = win_cost<CENSUS, true>(lw, r);
+            const uint32_t c = win_cost<CENSUS>(lw, r);
             const uint32_t key = in ? ((c << 16) | (uint32_t)d) : 0xFFFFFFFFu;
             const uint32_t kmin = __reduce_min_sync(0xFFFFFFFFu, key);
             const uint32_t other = (in && key != kmin) ? c : 0xFFFFFFFFu;
