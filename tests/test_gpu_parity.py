@@ -180,12 +180,36 @@ def test_pipeline_end_to_end(pairs, name):
     st = pl.stats()
     assert st["n_support"] == len(ref["list"])
     assert st["n_tri_left"] == len(ref["triL"]) and st["n_tri_right"] == len(ref["triR"])
-    # host-buffer path
+    # host-buffer path: repeated calls on the same pinned buffers (the step
+    # replayed from its graph), new contents of those buffers, and pageable
+    # buffers
     hL = torch.empty((h, w), dtype=torch.int16).pin_memory()
+    hR = torch.empty((h, w), dtype=torch.int16).pin_memory()
     hpost = torch.empty((h, w), dtype=torch.float32).pin_memory()
-    pl.run_host(torch.from_numpy(L).pin_memory(), torch.from_numpy(R).pin_memory(), hL, None, hpost)
-    np.testing.assert_array_equal(hL.numpy(), ref["lrL"])
-    assert np.abs(hpost.numpy() - ref["post"]).max() <= POST_TOL
+    iL, iR = torch.from_numpy(L).pin_memory(), torch.from_numpy(R).pin_memory()
+    for run in range(4):
+        for t in (hL, hR):
+            t.fill_(-7)
+        hpost.fill_(-7.0)
+        pl.run_host(iL, iR, hL, hR, hpost)
+        np.testing.assert_array_equal(hL.numpy(), ref["lrL"], err_msg="host run %d" % run)
+        np.testing.assert_array_equal(hR.numpy(), ref["lrR"], err_msg="host run %d" % run)
+        assert np.abs(hpost.numpy() - ref["post"]).max() <= POST_TOL
+    # the same buffers, the images swapped for a fronto-parallel pair
+    L2, R2 = synth.fronto_parallel_pair(w, h, 7, seed=11, noise_sigma=1.0)
+    ref2 = oracle.pipeline(L2, R2, wl.params, postprocess_on=True)
+    iL.copy_(torch.from_numpy(L2))
+    iR.copy_(torch.from_numpy(R2))
+    pl.run_host(iL, iR, hL, hR, hpost)
+    np.testing.assert_array_equal(hL.numpy(), ref2["lrL"])
+    np.testing.assert_array_equal(hR.numpy(), ref2["lrR"])
+    assert np.abs(hpost.numpy() - ref2["post"]).max() <= POST_TOL
+    pL = torch.empty((h, w), dtype=torch.int16)
+    ppost = torch.empty((h, w), dtype=torch.float32)
+    for run in range(2):
+        pl.run_host(torch.from_numpy(L), torch.from_numpy(R), pL, None, ppost)
+        np.testing.assert_array_equal(pL.numpy(), ref["lrL"], err_msg="pageable run %d" % run)
+        assert np.abs(ppost.numpy() - ref["post"]).max() <= POST_TOL
     pl.close()
 
 
