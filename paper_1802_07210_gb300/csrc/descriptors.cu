@@ -305,55 +305,98 @@ elas_status launch_descriptors_b(const DescArgs *tab, const DescArgs *host, cons
 // Census transform (Sec. VI.A).  Bit k = (dy + R) * W + (dx + R) of a pixel
 // is set iff its neighbour at (dx, dy) is darker than the pixel (R = W/2);
 // neighbours outside the image repeat the nearest border pixel, so every
-// pixel has a full W x W census.  One CTA per 32x8 tile of one image: the
-// tile and its R-pixel halo are staged in shared memory with clamped
-// coordinates, then each thread compares its W*W neighbours (the loops are
-// unrolled, so the bit positions are constants) and stores its NW 32-bit
-// words as 16-byte vectors: NW = 8 for the 32-byte support record, 4 for the
-// 16-byte dense record.
+// pixel has a full W x W census.  One CTA per 128x8 tile of one image: the
+// tile and its halo are staged in shared memory with clamped coordinates
+// (rows as 32-bit words, R4 = R rounded up to 4 bytes each side).  A thread
+// takes four adjacent pixels of a row: for every offset the four neighbour
+// bytes are one funnel shift of the row's words, the four comparisons one
+// byte-wise "less than" (bytes_lt), and the four bits go to byte lanes of an
+// accumulator (bit k & 7 of lane j for pixel j); four accumulators
+// (k >> 3 & 3) make one 32-bit word of every pixel after a byte transpose.
+// The loops are unrolled, so every position is a constant.  NW = 8 words
+// for the 32-byte support record, 4 for the 16-byte dense record.
 // ---------------------------------------------------------------------------
-constexpr int kCensusTW = 32, kCensusTH = 8;
+constexpr int kCensusPX = 4;                             // adjacent pixels of a thread
+constexpr int kCensusTW = 32 * kCensusPX, kCensusTH = 8;  // tile: one warp per row
+
+// Bit 7 of byte j is [n_j < c_j] for unsigned bytes (the other bits carry
+// nothing).  (n_j | 0x80) - (c_j & 0x7F) lies in [1, 255], so it borrows
+// nothing from the next byte, and its bit 7 is [n_j & 0x7F >= c_j & 0x7F];
+// n < c iff the top bits are 0 < 1, or equal with the low bits n < c.
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t n, uint32_t c, uint32_t c_low) {
+    const uint32_t d = (n | 0x80808080u) - c_low;
+    return (~n & c) | (~(n ^ c) & ~d);
+}
 
 template <int W, int NW> __device__ __forceinline__ void census_body(const CensusArgs &a, const VB &vb) {
-    constexpr int R = W / 2, SW = kCensusTW + 2 * R, SH = kCensusTH + 2 * R;
+    constexpr int R = W / 2, R4 = (R + 3) & ~3;
+    constexpr int SWB = kCensusTW + 2 * R4, SWW = SWB / 4, SH = kCensusTH + 2 * R;
+    constexpr int RW0 = (R4 - R) / 4, NRW = (R4 + R + 3) / 4 - RW0 + 1;  // row words a thread reads
     static_assert(W * W <= 32 * NW, "census window does not fit the record");
-    __shared__ uint8_t s[SH][SW];
+    static_assert((R4 + R + 3) / 4 <= R4 / 2, "a thread's row words stay inside the staged row");
+    __shared__ uint32_t s[SH][SWW];
     const uint8_t *img = vb.z ? a.imgR : a.imgL;
     uint4 *out = vb.z ? a.outR : a.outL;
     const int w = a.w, h = a.h;
     const int x0 = vb.x * kCensusTW, y0 = vb.y * kCensusTH;
-    const int tid = threadIdx.y * kCensusTW + threadIdx.x;
-    for (int i = tid; i < SW * SH; i += kCensusTW * kCensusTH) {
-        const int sx = i % SW, sy = i / SW;
-        const int x = min(max(x0 - R + sx, 0), w - 1), y = min(max(y0 - R + sy, 0), h - 1);
-        s[sy][sx] = img[(size_t)y * a.pitch + x];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    uint8_t *sb = reinterpret_cast<uint8_t *>(&s[0][0]);
+    for (int i = tid; i < SH * SWB; i += blockDim.x * blockDim.y) {
+        const int sy = i / SWB, sx = i - sy * SWB;
+        const int x = min(max(x0 - R4 + sx, 0), w - 1), y = min(max(y0 - R + sy, 0), h - 1);
+        sb[i] = img[(size_t)y * a.pitch + x];
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + kCensusPX * tx, y = y0 + ty;
     if (x >= w || y >= h) return;
-    const int cx = threadIdx.x + R, cy = threadIdx.y + R;
-    const uint32_t c = s[cy][cx];
-    uint32_t word[NW];
+    const uint32_t c = s[ty + R][R4 / 4 + tx];  // the four pixels
+    const uint32_t c_low = c & 0x7F7F7F7Fu;
+    uint32_t word[kCensusPX][NW];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) word[j] = 0u;
+    for (int j = 0; j < kCensusPX; ++j)
+#pragma unroll
+        for (int q = 0; q < NW; ++q) word[j][q] = 0u;
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
+        uint32_t rw[NRW];
+#pragma unroll
+        for (int q = 0; q < NRW; ++q) rw[q] = s[ty + R + dy][tx + RW0 + q];
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
             const int k = (dy + R) * W + (dx + R);
-            word[k >> 5] |= (uint32_t)((uint32_t)s[cy + dy][cx + dx] < c) << (k & 31);
+            const int off = R4 + dx, lo = off / 4 - RW0, sh = 8 * (off % 4);
+            const uint32_t n = sh == 0 ? rw[lo] : __funnelshift_r(rw[lo], rw[lo + 1], sh);
+            const int bit = k & 7;
+            acc[(k >> 3) & 3] |= (bytes_lt(n, c, c_low) >> (7 - bit)) & (0x01010101u << bit);
+            if ((k & 31) == 31 || k == W * W - 1) {
+                // bytes 0..3 of word k >> 5 of the four pixels, transposed
+                const uint32_t lo01 = __byte_perm(acc[0], acc[1], 0x5140), hi01 = __byte_perm(acc[0], acc[1], 0x7362);
+                const uint32_t lo23 = __byte_perm(acc[2], acc[3], 0x5140), hi23 = __byte_perm(acc[2], acc[3], 0x7362);
+                word[0][k >> 5] = __byte_perm(lo01, lo23, 0x5410);
+                word[1][k >> 5] = __byte_perm(lo01, lo23, 0x7632);
+                word[2][k >> 5] = __byte_perm(hi01, hi23, 0x5410);
+                word[3][k >> 5] = __byte_perm(hi01, hi23, 0x7632);
+                acc[0] = acc[1] = acc[2] = acc[3] = 0u;
+            }
         }
     }
-    uint4 *o = out + ((size_t)y * w + x) * (NW / 4);
 #pragma unroll
-    for (int j = 0; j < NW / 4; ++j) o[j] = make_uint4(word[4 * j], word[4 * j + 1], word[4 * j + 2], word[4 * j + 3]);
+    for (int j = 0; j < kCensusPX; ++j) {
+        if (x + j >= w) break;
+        uint4 *o = out + ((size_t)y * w + x + j) * (NW / 4);
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q)
+            o[q] = make_uint4(word[j][4 * q], word[j][4 * q + 1], word[j][4 * q + 2], word[j][4 * q + 3]);
+    }
 }
 
-template <int W, int NW> __global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel(CensusArgs a) {
+template <int W, int NW> __global__ void __launch_bounds__(32 * kCensusTH) census_kernel(CensusArgs a) {
     census_body<W, NW>(a, vb_single());
 }
 template <int W, int NW>
-__global__ void __launch_bounds__(kCensusTW *kCensusTH) census_kernel_b(const CensusArgs *__restrict__ tab, VMap vm) {
+__global__ void __launch_bounds__(32 * kCensusTH) census_kernel_b(const CensusArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
     census_body<W, NW>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
@@ -364,12 +407,12 @@ static dim3 census_grid(int w, int h, int two) {
 
 template <int W, int NW>
 static elas_status census_launch(const CensusArgs &a, int two, cudaStream_t st) {
-    census_kernel<W, NW><<<census_grid(a.w, a.h, two), dim3(kCensusTW, kCensusTH), 0, st>>>(a);
+    census_kernel<W, NW><<<census_grid(a.w, a.h, two), dim3(32, kCensusTH), 0, st>>>(a);
     return launch_status("census_kernel");
 }
 
 template <int W, int NW> static void census_launch_b(const CensusArgs *tab, const VMap &m, cudaStream_t st) {
-    census_kernel_b<W, NW><<<vmap_total(m), dim3(kCensusTW, kCensusTH), 0, st>>>(tab, m);
+    census_kernel_b<W, NW><<<vmap_total(m), dim3(32, kCensusTH), 0, st>>>(tab, m);
 }
 
 bool census_shape_ok(int window, int nbytes) {
