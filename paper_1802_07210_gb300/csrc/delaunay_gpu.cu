@@ -584,8 +584,12 @@ constexpr int kDtRadius1 = 96;     // first cache radius of the CTA pass
 constexpr int kDtRadius2 = 192;    // its second, when a step's circle does not fit the first
 constexpr int kDtCandCap2 = 3072;  // candidates cached per CTA (48 KB)
 constexpr int kDtMaxRows = 64;     // cell rows a radius-192 disc spans, with margin
-constexpr int kDtBlockThreads = 256;  // threads of a CTA-pass CTA
+constexpr int kDtBlockThreads = 256;  // threads of a CTA-pass CTA (one pair: its longest star sets the pass)
 constexpr int kDtBlocksPerSM = 3;     // CTA-pass CTAs resident per SM (85 registers a thread)
+// batches of two or more pairs: smaller CTAs, one more per SM (more stars at
+// once across the pairs; a step's selection takes a little longer)
+constexpr int kDtBlockThreadsB = 192;
+constexpr int kDtBlocksPerSMB = 4;
 static_assert(2 * kDtRadius2 / kDtCell + 2 <= kDtMaxRows, "the CTA pass's disc must fit the row table");
 
 // CTA reduction of the threads' (best, key) under the pencil order: each
@@ -1062,7 +1066,8 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block
 // stars of one pair overlap the work of all the others.  queue_id 1: the
 // warp pass's queues; 0: the group pass's (a batch of one pair, which skips
 // the warp pass).
-__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM)
+template <int THREADS, int PER_SM>
+__global__ void __launch_bounds__(THREADS, PER_SM)
     dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides, int32_t *counter, int queue_id) {
     extern __shared__ int4 s_cand[];
     __shared__ DtBlockShared sh;
@@ -1392,7 +1397,10 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
     }
     const int smem3 = kDtCandCap2 * (int)sizeof(int4) + (2 * max_gh + 1) * (int)sizeof(int);
     if (smem3 > 200 * 1024) return fail(ELAS_ERR_INVALID_ARG, "image too tall for the triangulation grid");
-    if (cudaFuncSetAttribute(dt_pass_block_kernel_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
+    if (cudaFuncSetAttribute(dt_pass_block_kernel_b<kDtBlockThreads, kDtBlocksPerSM>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess ||
+        cudaFuncSetAttribute(dt_pass_block_kernel_b<kDtBlockThreadsB, kDtBlocksPerSMB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel_b shared memory attribute");
     dt_init_kernel_b<<<vmap_total(m_init), 256, 0, st>>>(tab, m_init, counter);
     dt_points_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
@@ -1410,8 +1418,12 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
     }
     const int nsm = sm_count();
-    dt_pass_block_kernel_b<<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter,
-                                                                                 one ? 0 : 1);
+    if (one)
+        dt_pass_block_kernel_b<kDtBlockThreads, kDtBlocksPerSM>
+            <<<nsm * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(tab, pairs, nsides, counter, 0);
+    else
+        dt_pass_block_kernel_b<kDtBlockThreadsB, kDtBlocksPerSMB>
+            <<<nsm * kDtBlocksPerSMB, kDtBlockThreadsB, smem3, st>>>(tab, pairs, nsides, counter, 1);
     dt_tri_scan_kernel_b<<<vmap_total(m_scan), 1024, 0, st>>>(tab, m_scan);
     dt_emit_kernel_b<<<vmap_total(m_pts), 256, 0, st>>>(tab, m_pts);
     dt_emit_big_kernel_b<<<vmap_total(m_big), 256, 0, st>>>(tab, m_big);
