@@ -383,11 +383,19 @@ __device__ __forceinline__ int4 dt_group_best(unsigned m, int4 best, DtKey<int> 
     return best;
 }
 
-// G lanes per star, candidates within R (list capacity CAP).  QUEUE: the
-// stars of the first queue (left by the R = 32 pass), failures go to the
-// second queue; else every point, failures to the first queue.
-template <int G, int R, int CAP, bool QUEUE>
+// Star queues of a side: 1 = (pending, npending), 2 = (pending2,
+// npending2), 3 = (pending, npending3) (batches: the third pass's output,
+// written after the second pass has read `pending`).
+__device__ __forceinline__ const int32_t *dt_queue(const DtSide &S, int q) { return q == 2 ? S.pending2 : S.pending; }
+__device__ __forceinline__ int32_t *dt_queue_len(const DtSide &S, int q) {
+    return q == 2 ? S.npending2 : (q == 3 ? S.npending3 : S.npending);
+}
+
+// G lanes per star, candidates within R (list capacity CAP).  QIN: 0 =
+// every point, else the stars of that queue; failures go to queue QOUT.
+template <int G, int R, int CAP, int QIN, int QOUT>
 __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb) {
+    constexpr bool QUEUE = QIN != 0;
     static_assert(2 * R / kDtCell + 2 <= G, "the group's lanes fetch the cell rows of the disc");
     static_assert(R <= 64, "32-bit pencil keys are exact for coordinates within 64 of p");
     __shared__ int s_list[kDtGroupThreads / G][CAP];
@@ -397,9 +405,10 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
     const unsigned gm = G == 32 ? 0xFFFFFFFFu : ((1u << (G & 31)) - 1u) << gbase;
     int *list = s_list[threadIdx.x / G];
     const int groups = vb.gx * (kDtGroupThreads / G);
-    const int njobs = QUEUE ? *S.npending : n;
+    const int njobs = QUEUE ? *dt_queue_len(S, QIN) : n;
+    const int32_t *qin = dt_queue(S, QIN);
     for (int j = vb.x * (kDtGroupThreads / G) + threadIdx.x / G; j < njobs; j += groups) {
-        const int4 p = QUEUE ? S.pts[S.slot[S.pending[j]]] : S.pts[j];
+        const int4 p = QUEUE ? S.pts[S.slot[qin[j]]] : S.pts[j];
         if (!p.w || (!QUEUE && S.status[p.z] != 0)) continue;
         // candidates: lanes fetch the cell rows' ranges, then stride over them
         const int cx0 = max(0, p.x - R) / kDtCell, cx1 = min(a.gw - 1, max(0, p.x + R) / kDtCell);
@@ -535,10 +544,8 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
                 S.status[p.z] = 1;
                 S.owned[p.z] = written;
                 if (written > kDtSlots) atomicOr(S.err, 4);
-            } else if (QUEUE) {
-                S.pending2[atomicAdd(S.npending2, 1)] = p.z;
             } else {
-                S.pending[atomicAdd(S.npending, 1)] = p.z;
+                const_cast<int32_t *>(dt_queue(S, QOUT))[atomicAdd(dt_queue_len(S, QOUT), 1)] = p.z;
             }
         }
         __syncwarp(gm);
@@ -547,16 +554,23 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
 
 
 template <int G, int R> __device__ __forceinline__ void dt_pass1_body(const DtArgs &a, const VB &vb) {
-    dt_group_pass_body<G, R, kDtListCap, false>(a, vb);
-}
-__device__ __forceinline__ void dt_pass1b_body(const DtArgs &a, const VB &vb) {
-    dt_group_pass_body<32, kDtRadiusB, kDtListCapB, true>(a, vb);
+    dt_group_pass_body<G, R, kDtListCap, 0, 1>(a, vb);
 }
 
-__global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel(DtArgs a) { dt_pass1b_body(a, vb_single()); }
+// Batches: the stars left by the first pass go through a middle pass (eight
+// lanes, the 32-pixel disc) and those left again through the warp pass
+// (the 64-pixel disc); the CTA pass takes the third queue.
+constexpr int kDtRadiusM = 32;
+constexpr int kDtListCapM = 192;  // the radius-32 disc holds at most ~130 lattice points
+constexpr int kDtGroupM = 8;
+
+__global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1m_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
+    const VB vb = vb_batch(vm);
+    dt_group_pass_body<kDtGroupM, kDtRadiusM, kDtListCapM, 1, 2>(slot_entry(tab, vm.stride, vb.slot), vb);
+}
 __global__ void __launch_bounds__(kDtGroupThreads, 3) dt_pass1b_kernel_b(const DtArgs *__restrict__ tab, VMap vm) {
     const VB vb = vb_batch(vm);
-    dt_pass1b_body(slot_entry(tab, vm.stride, vb.slot), vb);
+    dt_group_pass_body<32, kDtRadiusB, kDtListCapB, 2, 3>(slot_entry(tab, vm.stride, vb.slot), vb);
 }
 
 __global__ void __launch_bounds__(kDtGroupThreads, 4) dt_pass1_kernel(DtArgs a) {
@@ -1085,7 +1099,7 @@ __global__ void __launch_bounds__(THREADS, PER_SM)
             v[j] = 0;
             if (q < nq_all) {
                 const DtSide &Q = slot_entry(tab, vm.stride, vm.slot[q / nsides]).s[q % nsides];
-                v[j] = max(0, queue_id ? *Q.npending2 : *Q.npending);
+                v[j] = max(0, *dt_queue_len(Q, queue_id ? 3 : 1));
             }
             sum += v[j];
         }
@@ -1124,7 +1138,7 @@ __global__ void __launch_bounds__(THREADS, PER_SM)
         const DtArgs &a = slot_entry(tab, vm.stride, vm.slot[lo / nsides]);
         const DtSide &S = a.s[lo % nsides];
         const int n = min(max(*a.count, 0), a.cap);
-        dt_block_item(a, S, (queue_id ? S.pending2 : S.pending)[item - s_pre[lo]], n, s_cand, sh, r_start,
+        dt_block_item(a, S, dt_queue(S, queue_id ? 3 : 1)[item - s_pre[lo]], n, s_cand, sh, r_start,
                       r_start + a.gh);
     }
 }
@@ -1284,6 +1298,7 @@ static DtSide dt_carve(void *ws, int cap, int w, int h) {
     s.err = small;
     s.npending = small + 1;
     s.npending2 = small + 2;
+    s.npending3 = small + 3;
     return s;
 }
 
@@ -1350,7 +1365,7 @@ __device__ __forceinline__ void dt_init_body(const DtArgs &a, const VB &vb, int3
         else if (k < ncell1 + 2 * a.h)
             S.rowmax[k - ncell1 - a.h] = (int32_t)0x80808080u;
         else
-            S.err[k - ncell1 - 2 * a.h] = 0;  // err, npending, npending2 and one spare word
+            S.err[k - ncell1 - 2 * a.h] = 0;  // err, npending, npending2, npending3
     }
 }
 
@@ -1415,6 +1430,7 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         dt_pass1_kernel_b1<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
     } else {
         dt_pass1_kernel_b<<<vmap_total(m_grp), kDtGroupThreads, 0, st>>>(tab, m_grp);
+        dt_pass1m_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
         dt_pass1b_kernel_b<<<vmap_total(m_grp2), kDtGroupThreads, 0, st>>>(tab, m_grp2);
     }
     const int nsm = sm_count();
