@@ -233,20 +233,30 @@ template <bool CENSUS> __device__ __forceinline__ void support_match_row_body(co
         // candidates u = s + d with d in [dmin, dmax] for some s of the window
         const int k0 = max(0, (s0 + dmin + step - 1) / step), k1 = min(wc - 1, (s0 + 31 + dmax) / step);
         const int slot = j % L.slots;
-        for (int k = k0; k <= k1; ++k) {
-            const int2 lh = s_lohi[k];
-            if (lh.x > lh.y) continue;  // uniform over the warp
-            const int d = k * step - sl;
-            const bool in = s_ok && d >= lh.x && d <= lh.y;
-            Win lw;
+        // two candidates per step: their chains (window load, cost, the two
+        // reductions) are independent, so they overlap
+        for (int k = k0; k <= k1; k += 2) {
+            const bool has1 = k + 1 <= k1;
+            const int2 lh0 = s_lohi[k], lh1 = has1 ? s_lohi[k + 1] : make_int2(1, 0);
+            const int d0 = k * step - sl, d1 = d0 + step;
+            const bool in0 = s_ok && d0 >= lh0.x && d0 <= lh0.y;
+            const bool in1 = s_ok && d1 >= lh1.x && d1 <= lh1.y;
+            Win lw0, lw1;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) lw.q[i] = s_desc[4 * k + i];
-            const uint32_t c = win_cost<CENSUS>(lw, r);
-            const uint32_t key = in ? ((c << 16) | (uint32_t)d) : 0xFFFFFFFFu;
-            const uint32_t kmin = __reduce_min_sync(0xFFFFFFFFu, key);
-            const uint32_t other = (in && key != kmin) ? c : 0xFFFFFFFFu;
-            const uint32_t m2 = __reduce_min_sync(0xFFFFFFFFu, other);
-            if (lane == 0 && kmin != 0xFFFFFFFFu) s_res[k * L.slots + slot] = make_uint2(kmin, m2);
+            for (int i = 0; i < 4; ++i) {
+                lw0.q[i] = s_desc[4 * k + i];
+                lw1.q[i] = has1 ? s_desc[4 * (k + 1) + i] : lw0.q[i];
+            }
+            const uint32_t c0 = win_cost<CENSUS>(lw0, r), c1 = win_cost<CENSUS>(lw1, r);
+            const uint32_t key0 = in0 ? ((c0 << 16) | (uint32_t)d0) : 0xFFFFFFFFu;
+            const uint32_t key1 = in1 ? ((c1 << 16) | (uint32_t)d1) : 0xFFFFFFFFu;
+            const uint32_t kmin0 = __reduce_min_sync(0xFFFFFFFFu, key0);
+            const uint32_t kmin1 = __reduce_min_sync(0xFFFFFFFFu, key1);
+            const uint32_t m20 = __reduce_min_sync(0xFFFFFFFFu, (in0 && key0 != kmin0) ? c0 : 0xFFFFFFFFu);
+            const uint32_t m21 = __reduce_min_sync(0xFFFFFFFFu, (in1 && key1 != kmin1) ? c1 : 0xFFFFFFFFu);
+            // a candidate with an empty range (lo > hi) has no lane in it
+            if (lane == 0 && kmin0 != 0xFFFFFFFFu) s_res[k * L.slots + slot] = make_uint2(kmin0, m20);
+            if (lane == 0 && kmin1 != 0xFFFFFFFFu) s_res[(k + 1) * L.slots + slot] = make_uint2(kmin1, m21);
         }
     }
     __syncthreads();
