@@ -79,6 +79,25 @@ def test_big_empty_circles_and_fans():
     _check(pts, 800, 310)
 
 
+def test_dense_sets_and_far_clusters():
+    rng = np.random.default_rng(5)
+    # a 2-pixel lattice with holes: every disc holds more points than the
+    # passes list, so the stars take the unlisted steps
+    pts = [(2 * i + 3, 2 * j + 3, int(rng.integers(0, 30))) for j in range(40) for i in range(60)
+           if rng.random() < 0.6]
+    _check(pts, 130, 90)
+    # clusters far apart: long edges between them and circles far wider than
+    # any listed disc (region steps clipped to the disc and the half-plane)
+    seen, pts = set(), []
+    for cx, cy in ((20, 20), (300, 40), (150, 200), (40, 280), (290, 290), (160, 30)):
+        for _ in range(30):
+            x, y = cx + int(rng.integers(0, 20)), cy + int(rng.integers(0, 20))
+            if (x, y) not in seen:
+                seen.add((x, y))
+                pts.append((x, y, int(rng.integers(0, 12))))
+    _check(pts, 320, 320)
+
+
 def test_right_coordinates_with_many_duplicates():
     # all points of a row collapse onto a few right-image positions
     pts = [(u, v, u % 20) for v in range(10, 60, 5) for u in range(20, 200, 5)]
