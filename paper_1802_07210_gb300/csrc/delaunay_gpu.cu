@@ -655,6 +655,7 @@ struct DtBlockShared {
     unsigned fmin[3];  // least float key of a selection (three buffers, used in turn)
     int nband[3];      // band members listed by a selection
     int4 win;          // winner of an exactly ordered band
+    int small;         // the first band member's circle fits the disc of radius R (selections with R > 0)
 };
 
 // Float filter of the pencil order (CTA pass).  With coordinates below 2^14
@@ -697,15 +698,20 @@ __device__ __forceinline__ bool dt_key_better_w(const DtKey<int> &k1, const DtKe
 // least is in the band too) and list it; a single listed candidate
 // is the winner, else warp 0 orders the list exactly (the whole CTA when it
 // overflows).  par: the caller's turn counter (the same on every thread).
+// With R > 0, small tells whether the winner's circumdisc lies inside the
+// disc of radius R about p (dt_small_circle): the thread that lists the
+// first band member tests it before the second barrier, which is the answer
+// when the band has one member, so the other threads skip the 64-bit test.
 // Thread 0 resets the next call's buffers before this call's first barrier:
 // their last readers (two calls back) have passed the previous call's first
 // barrier, and the next call writes them only after this call's.
 template <typename Each>
 __device__ int4 dt_block_select(Each each, const int4 &p, const int4 &e, int side, const int4 &seed,
-                                DtBlockShared &sh, int &par) {
+                                DtBlockShared &sh, int &par, int R, bool &small) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int b = par, nxt = par == 2 ? 0 : par + 1;
     par = nxt;
+    small = false;
     if (tid == 0) {
         sh.fmin[nxt] = 0xFFFFFFFFu;
         sh.nband[nxt] = 0;
@@ -759,33 +765,46 @@ __device__ int4 dt_block_select(Each each, const int4 &p, const int4 &e, int sid
             bk = dt_key<int>(p, e, q1, side);
         }
     }
+    auto fits = [&](const int4 &c) {
+        return c.w && (side > 0 ? dt_small_circle(p, e, c, R) : dt_small_circle(p, c, e, R));
+    };
     if (best.w) {
         const int pos = atomicAdd(&sh.nband[b], 1);
         if (pos < kDtBandCap) {
             sh.red[pos] = best;
             sh.rn[pos] = bk.N;
             sh.rd[pos] = bk.D;
+            if (pos == 0 && R > 0) sh.small = fits(best);
         }
     }
     __syncthreads();
     const int nb = sh.nband[b];
-    if (nb == 1) return sh.red[0];
-    if (nb > kDtBandCap)
-        return dt_block_best(best, DtKey<int64_t>{bk.N, bk.D}, p, e, side, sh.red, sh.rn, sh.rd);
-    if (tid < 32) {
-        int4 c = lane < nb ? sh.red[lane] : make_int4(0, 0, 0, 0);
-        DtKey<int64_t> k{lane < nb ? sh.rn[lane] : 0, lane < nb ? sh.rd[lane] : 1};
-        c = dt_warp_key_best(c, k, p, e, side);
-        if (lane == 0) sh.win = c;
+    if (nb == 1) {
+        small = R > 0 && sh.small;
+        return sh.red[0];
     }
-    __syncthreads();
-    return sh.win;
+    int4 w;
+    if (nb > kDtBandCap) {
+        w = dt_block_best(best, DtKey<int64_t>{bk.N, bk.D}, p, e, side, sh.red, sh.rn, sh.rd);
+    } else {
+        if (tid < 32) {
+            int4 c = lane < nb ? sh.red[lane] : make_int4(0, 0, 0, 0);
+            DtKey<int64_t> k{lane < nb ? sh.rn[lane] : 0, lane < nb ? sh.rd[lane] : 1};
+            c = dt_warp_key_best(c, k, p, e, side);
+            if (lane == 0) sh.win = c;
+        }
+        __syncthreads();
+        w = sh.win;
+    }
+    small = R > 0 && fits(w);
+    return w;
 }
 
 // Best third vertex for edge (p, cur) on `side`, over the cache (cand, k) or,
 // with cand == NULL, over every alive point.
 __device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, const int4 &cur, int side,
-                                              const int4 *cand, int k, int n, DtBlockShared &sh, int &par) {
+                                              const int4 *cand, int k, int n, DtBlockShared &sh, int &par, int R,
+                                              bool &small) {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int4 none = make_int4(0, 0, 0, 0);
     if (cand)
@@ -793,12 +812,12 @@ __device__ __forceinline__ int4 dt_block_step(const DtSide &S, const int4 &p, co
             [&](auto &&v) {
                 for (int j = tid; j < k; j += nth) v(cand[j]);
             },
-            p, cur, side, none, sh, par);
+            p, cur, side, none, sh, par, R, small);
     return dt_block_select(
         [&](auto &&v) {
             for (int j = tid; j < n; j += nth) v(S.pts[j]);
         },
-        p, cur, side, none, sh, par);
+        p, cur, side, none, sh, par, R, small);
 }
 
 // Exact step for edge (p, cur) on `side` without the radius limit.  Only
@@ -876,6 +895,7 @@ __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int
     // each warp takes cell rows in turn; its lanes stride over the row's
     // contiguous range of the grid-sorted points
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    bool unused;
     return dt_block_select(
         [&](auto &&v) {
             for (int cy = warp; cy < a.gh; cy += nwarps) {
@@ -892,7 +912,7 @@ __device__ int4 dt_block_region_step(const DtArgs &a, const DtSide &S, const int
                 for (; j < len; j += 32) v(S.pts[s0 + j]);
             }
         },
-        p, cur, side, bc, sh, par);
+        p, cur, side, bc, sh, par, 0, unused);
 }
 
 __device__ int dt_block_gather(const DtArgs &a, const DtSide &S, const int4 &p, int R, int4 *cand,
@@ -957,16 +977,16 @@ __device__ int dt_block_star(const DtArgs &a, const DtSide &S, int i, const int4
         int4 b = make_int4(0, 0, 0, 0);
         for (;;) {
             if (!cand || k > kDtCandCap2) break;
-            b = dt_block_step(S, p, cur, side, cand, k, n, sh, par);
-            const bool small =
-                b.w && (side > 0 ? dt_small_circle(p, cur, b, R) : dt_small_circle(p, b, cur, R));
+            bool small;
+            b = dt_block_step(S, p, cur, side, cand, k, n, sh, par, R, small);
             if (small) return b;
             if (R >= kDtRadius2) break;
             R = kDtRadius2;  // refill the cache once with the larger disc
             k = dt_block_gather(a, S, p, R, cand, sh);
         }
         if (r_start) return dt_block_region_step(a, S, p, cur, side, b, sh, r_start, r_len, par);
-        return dt_block_step(S, p, cur, side, nullptr, 0, n, sh, par);
+        bool unused;
+        return dt_block_step(S, p, cur, side, nullptr, 0, n, sh, par, 0, unused);
     };
     int4 cur = first;
     bool closed = false;
