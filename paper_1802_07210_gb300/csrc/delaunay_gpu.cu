@@ -283,6 +283,30 @@ __device__ __forceinline__ bool dt_small_circle(const int4 &p, const int4 &a, co
     return pa * pb * ab <= R2 * ar * ar;
 }
 
+// The same test in 32-bit integers for discs of radius R <= 24: once pa and
+// pb are at most R^2, pa * pb * ab <= 4 R^6 < 2^31 and R^2 * ar^2 <= R^6
+// (|ar| <= sqrt(pa pb)); coordinate differences below 2^15 keep pa and pb
+// themselves within 31 bits.
+template <int R>
+__device__ __forceinline__ bool dt_small_circle32(const int4 &p, const int4 &a, const int4 &b) {
+    static_assert(R <= 24, "4 R^6 must fit in 31 bits");
+    const int ax = a.x - p.x, ay = a.y - p.y, bx = b.x - p.x, by = b.y - p.y;
+    const int pa = ax * ax + ay * ay, pb = bx * bx + by * by;
+    if (pa > R * R || pb > R * R) return false;
+    const int dx = bx - ax, dy = by - ay;
+    const int ab = dx * dx + dy * dy;
+    const int ar = ax * by - ay * bx;
+    return pa * pb * ab <= R * R * ar * ar;
+}
+
+template <int R>
+__device__ __forceinline__ bool dt_small_circle_r(const int4 &p, const int4 &a, const int4 &b) {
+    if constexpr (R <= 24)
+        return dt_small_circle32<R>(p, a, b);
+    else
+        return dt_small_circle(p, a, b, R);
+}
+
 // Records triangle (p, a, b) if p owns it (lowest index).
 __device__ __forceinline__ void dt_record(const DtSide &S, int i, int &written, const int4 &p, const int4 &a,
                                           const int4 &b, bool leader) {
@@ -481,7 +505,7 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
                     e_l = cur;
                     break;
                 }
-                if (!dt_small_circle(p, cur, best, R)) {
+                if (!dt_small_circle_r<R>(p, cur, best)) {
                     certified = false;
                     break;
                 }
@@ -514,7 +538,7 @@ __device__ __forceinline__ void dt_group_pass_body(const DtArgs &a, const VB &vb
                         e_r = cur;
                         break;
                     }
-                    if (!dt_small_circle(p, best, cur, R)) {
+                    if (!dt_small_circle_r<R>(p, best, cur)) {
                         certified = false;
                         break;
                     }
