@@ -1104,18 +1104,34 @@ __device__ __forceinline__ void dt_block_item(const DtArgs &a, const DtSide &S, 
     __syncthreads();
 }
 
-// One pair: the CTAs of side blockIdx.y stride over that side's queue (the
-// group pass's, or with second_queue the warp pass's).
-__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block_kernel(DtArgs a, int second_queue) {
+// One pair, persistent (every CTA resident): the CTAs take the stars of
+// both sides' queues from one atomic counter, the two queues interleaved so
+// that both sides' stars start in the first wave (the pass lasts as long as
+// its longest star, so none should wait behind the other side's).  The
+// counter is side 0's npending2, which dt_init_kernel zeroes and the one-pair
+// passes leave unused.
+__global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block_kernel(DtArgs a, int nsides) {
     extern __shared__ int4 s_cand[];  // [kDtCandCap2], then the region rows
     __shared__ DtBlockShared sh;
+    __shared__ int s_item;
     int *r_start = reinterpret_cast<int *>(s_cand + kDtCandCap2);
     int *r_len = r_start + a.gh;
-    const DtSide S = blockIdx.y ? a.s[1] : a.s[0];
     const int n = min(max(*a.count, 0), a.cap);
-    const int nq = second_queue ? *S.npending2 : *S.npending;
-    const int32_t *queue = second_queue ? S.pending2 : S.pending;
-    for (int q0 = blockIdx.x; q0 < nq; q0 += gridDim.x) dt_block_item(a, S, queue[q0], n, s_cand, sh, r_start, r_len);
+    const int nq0 = *a.s[0].npending, nq1 = nsides > 1 ? *a.s[1].npending : 0;
+    const int m = min(nq0, nq1), total = nq0 + nq1;
+    int32_t *counter = a.s[0].npending2;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) break;
+        const bool two = item < 2 * m;
+        const int side = two ? (item & 1) : (nq0 > nq1 ? 0 : 1);
+        const int idx = two ? (item >> 1) : item - m;
+        const DtSide S = side ? a.s[1] : a.s[0];
+        dt_block_item(a, S, S.pending[idx], n, s_cand, sh, r_start, r_len);
+    }
 }
 
 // Many pairs, persistent: the queues of every (pair, side) of the launch are
@@ -1387,7 +1403,7 @@ elas_status launch_triangulate_device(const int16_t *list, const int32_t *count,
     if (cudaFuncSetAttribute(dt_pass_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) != cudaSuccess)
         return launch_status("dt_pass_block_kernel shared memory attribute");
     (void)smem2;
-    dt_pass_block_kernel<<<dim3(sm_count() * kDtBlocksPerSM, nsides), kDtBlockThreads, smem3, st>>>(a, 0);
+    dt_pass_block_kernel<<<sm_count() * kDtBlocksPerSM, kDtBlockThreads, smem3, st>>>(a, nsides);
     dt_tri_scan_kernel<<<dim3(1, nsides), 1024, 0, st>>>(a);
     dt_emit_kernel<<<dim3(pblocks, nsides), tb, 0, st>>>(a);
     dt_emit_big_kernel<<<dim3(sm_count(), nsides), 256, 0, st>>>(a);

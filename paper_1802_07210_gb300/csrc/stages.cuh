@@ -112,7 +112,7 @@ struct DtSide {
     int32_t *pending;          // [cap] points queued for the CTA pass
     int32_t *npending;         // queue length
     int32_t *pending2;         // [cap] points queued again
-    int32_t *npending2;
+    int32_t *npending2;        // its length (one pair: side 0's is the CTA pass's work counter)
     int32_t *npending3;        // batches: the third queue's length (its entries reuse `pending`)
     int32_t *rowmin, *rowmax;  // [h] extreme x of the points of each image row
     int32_t *tri;              // output [cap_tri][3]
