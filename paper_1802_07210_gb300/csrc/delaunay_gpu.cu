@@ -211,47 +211,9 @@ constexpr int kDtRadius = 24;     // pass-1 search radius (one pair)
 constexpr int kDtRadiusBatch = 18;  // pass-1 search radius in batched launches
 constexpr int kDtSlots = 32;      // owned triangles kept per point
 
-__device__ __forceinline__ int4 shfl4_from(const int4 &v, int src) {
-    return make_int4(__shfl_sync(0xFFFFFFFFu, v.x, src), __shfl_sync(0xFFFFFFFFu, v.y, src),
-                     __shfl_sync(0xFFFFFFFFu, v.z, src), __shfl_sync(0xFFFFFFFFu, v.w, src));
-}
-
 __device__ __forceinline__ int4 shfl4(const int4 &v, int src_xor) {
     return make_int4(__shfl_xor_sync(0xFFFFFFFFu, v.x, src_xor), __shfl_xor_sync(0xFFFFFFFFu, v.y, src_xor),
                      __shfl_xor_sync(0xFFFFFFFFu, v.z, src_xor), __shfl_xor_sync(0xFFFFFFFFu, v.w, src_xor));
-}
-
-// Better of two third-vertex candidates in the pencil order of edge (p, e):
-// ccw: triangles (p, e, c); else (p, c, e).  c2 beats c1 iff c2 lies inside
-// the circle of c1's triangle.  w = 0 marks "no candidate".
-template <typename T>
-__device__ __forceinline__ int4 dt_better(const int4 &c1, const int4 &c2, const int4 &p, const int4 &e, bool ccw) {
-    if (!c2.w) return c1;
-    if (!c1.w) return c2;
-    const int s = ccw ? dt_incircle<T>(p, e, c1, c2) : dt_incircle<T>(p, c1, e, c2);
-    return (s > 0 || (s == 0 && c2.z < c1.z)) ? c2 : c1;
-}
-
-template <typename T>
-__device__ __forceinline__ int4 dt_warp_best(int4 best, const int4 &p, const int4 &e, bool ccw) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = dt_better<T>(best, shfl4(best, o), p, e, ccw);
-    return best;
-}
-
-// True iff no point lies strictly left (left = true) or strictly right of the
-// line p->e.  Within one image row the orientation is affine in x, so the
-// row's two extreme points decide for the whole row.  Warp collective.
-__device__ __forceinline__ bool dt_open_edge_ok(const DtSide &S, int h, const int4 &p, const int4 &e, bool left,
-                                                int lane) {
-    bool bad = false;
-    for (int y = lane; y < h && !bad; y += 32) {
-        const int x0 = S.rowmin[y], x1 = S.rowmax[y];
-        if (x0 > x1) continue;
-        const int64_t o0 = dt_orient(p.x, p.y, e.x, e.y, x0, y), o1 = dt_orient(p.x, p.y, e.x, e.y, x1, y);
-        bad = left ? (o0 > 0 || o1 > 0) : (o0 < 0 || o1 < 0);
-    }
-    return !__any_sync(0xFFFFFFFFu, bad);
 }
 
 __device__ __forceinline__ unsigned long long dt_nn_key(const int4 &p, const int4 &q) {
@@ -366,11 +328,6 @@ constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (a radius-24 disc holds at most ~75 lattice points at step 5)
 constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
 constexpr int kDtListCapB = 640; // the radius-64 disc holds at most ~520 lattice points
-
-__device__ __forceinline__ int4 gshfl4(unsigned m, const int4 &v, int src) {
-    return make_int4(__shfl_sync(m, v.x, src), __shfl_sync(m, v.y, src), __shfl_sync(m, v.z, src),
-                     __shfl_sync(m, v.w, src));
-}
 
 // Group reduction of (best, key) under the pencil order of edge (p, e).
 template <int G>
