@@ -351,8 +351,6 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
     else
         __syncthreads();
     auto list_at = [&](int k) -> int { return GLIST ? (int)__ldg(glist + k) : (int)s_list[k]; };
-    const int nlist = full ? 0 : (GLIST ? __ldg(S.ccount + cell) : s_nlist);
-    const int dlast = nlist > 0 ? list_at(nlist - 1) : -1;  // largest entry
     const int sub = TPP > 1 ? (tid & (TPP - 1)) : 0;
 
     // ---- per-pixel argmin -------------------------------------------------------
@@ -394,6 +392,9 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
             if (!full) dp_nx = (int)__ldcg(S.dplane + i1);
         }
         int best = 0x7FFFFFFF;
+        // the list length, read after the pixel's own loads so that they are
+        // in flight together
+        const int nlist = full ? 0 : (GLIST ? __ldg(S.ccount + cell) : s_nlist);
         // census records have no texture measure: no texture test
         if (in && (CENSUS || (int)texture16(r) >= a.match_texture) && (full || dp >= 0)) {
             // admissible d: 2 <= x + dir*d <= w-3 and d <= dmax, i.e. d <= dlim
@@ -406,9 +407,14 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
                     best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                 }
             } else {
-                // the admissible entries are a prefix of the ascending list
+                // the admissible entries are a prefix of the ascending list:
+                // entries above dlim (only near the image border) are skipped
+                // by a predicate, so the load of an inadmissible d never
+                // issues; the batched census kernel finds the prefix's end by
+                // bisection instead (the predicate costs it registers)
+                constexpr bool kBisect = CENSUS && !GLIST;
                 int cnt = nlist;
-                if (dlim < dlast) {
+                if (kBisect && nlist > 0 && dlim < list_at(nlist - 1)) {
                     int lo = 0, hi = nlist;  // first entry above dlim
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -422,7 +428,8 @@ __device__ __forceinline__ void cell_body(const CellArgs &a, const VB &vb) {
 #pragma unroll 8
                 for (int k = sub; k < cnt; k += TPP) {
                     const int d = list_at(k);
-                    best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
+                    if (kBisect || d <= dlim)
+                        best = min(best, dense_cost<CENSUS>(r, __ldg(orow + dir * d), kKeyBias) * kKeyMul + d);
                 }
                 // the plane neighbourhood, the prior term in the accumulator
                 const int lo = max(dmin, dp - sradius), hi = min(dlim, dp + sradius);
