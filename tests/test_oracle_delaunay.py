@@ -114,6 +114,44 @@ def test_general_position_matches_brute_force(orc):
         done += 1
 
 
+def _incircle_all(P, T):
+    """Exact incircle determinants of every point against every triangle
+    (int64: coordinates below 2^14 keep each term below 2^58)."""
+    out = []
+    for t0 in range(0, len(T), 256):
+        A, B, C = (P[T[t0:t0 + 256, i]][:, None, :] for i in range(3))
+        m = [Q - P[None, :, :] for Q in (A, B, C)]
+        lift = [q[..., 0] * q[..., 0] + q[..., 1] * q[..., 1] for q in m]
+        det = (m[0][..., 0] * (m[1][..., 1] * lift[2] - lift[1] * m[2][..., 1])
+               - m[0][..., 1] * (m[1][..., 0] * lift[2] - lift[1] * m[2][..., 0])
+               + lift[0] * (m[1][..., 0] * m[2][..., 1] - m[1][..., 1] * m[2][..., 0]))
+        out.append(det)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_random_sets_match_qhull(orc, seed):
+    """Sets of 1,500 points, far beyond what brute force reaches, against
+    Qhull's Delaunay triangulation (a library routine), after checking
+    exactly that Qhull's triangles have empty circumcircles with no fourth
+    point on any of them: the triangulation is then the unique Delaunay one."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(300 + seed)
+    P = np.unique(rng.integers(0, 16000, (1600, 2)), axis=0)[:1500]
+    P = P[rng.permutation(len(P))].astype(np.int64)
+    T = spatial.Delaunay(P.astype(np.float64)).simplices.astype(np.int64)
+    # counter-clockwise, then every other point strictly outside each circle
+    o = (P[T[:, 1], 0] - P[T[:, 0], 0]) * (P[T[:, 2], 1] - P[T[:, 0], 1]) \
+        - (P[T[:, 1], 1] - P[T[:, 0], 1]) * (P[T[:, 2], 0] - P[T[:, 0], 0])
+    assert np.all(o != 0)
+    T[o < 0] = T[o < 0][:, [0, 2, 1]]
+    det = _incircle_all(P, T)
+    det[np.arange(len(T))[:, None], T] = -1  # a triangle's own vertices
+    assert np.all(det < 0), "Qhull's triangulation is not strictly Delaunay for this seed"
+    got = orc.delaunay([tuple(map(int, p)) for p in P])
+    assert _canon(got) == _canon(T)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_lattice_subsets_are_valid(orc, seed):
     rng = np.random.default_rng(seed)
