@@ -1,9 +1,11 @@
 """Pins of the oracle's descriptor step (Sec. III.A, Fig. 1(b-d); Sec. VI.A)
-against hand-derived values, closed forms and the mirror symmetry."""
+against hand-derived values, closed forms, the mirror symmetry and a library
+correlation."""
 import json
 import os
 
 import numpy as np
+import pytest
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -94,3 +96,18 @@ def test_transpose_swaps_gradients(orc):
     duT, dvT = orc.sobel(img.T.copy())
     np.testing.assert_array_equal(duT, dv.T)
     np.testing.assert_array_equal(dvT, du.T)
+
+
+def test_interior_gradients_match_a_library_correlation(orc):
+    """Inside the one-pixel frame, du and dv are the correlations of the image
+    with the 3x3 Sobel kernels (a library routine): a wrong weight, sign or a
+    transposed kernel fails here."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    K = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]], np.int64)
+    rng = np.random.default_rng(8)
+    for h, w in ((37, 53), (5, 5), (64, 200)):
+        img = rng.integers(0, 256, (h, w)).astype(np.uint8)
+        du, dv = orc.sobel(img)
+        inner = (slice(1, -1), slice(1, -1))
+        np.testing.assert_array_equal(du[inner], ndimage.correlate(img.astype(np.int64), K)[inner])
+        np.testing.assert_array_equal(dv[inner], ndimage.correlate(img.astype(np.int64), K.T)[inner])

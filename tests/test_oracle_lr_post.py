@@ -4,6 +4,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -139,3 +140,14 @@ def test_median_invariants(orc):
         win = d[max(0, v - 2):v + 3, max(0, u - 2):u + 3]
         if d[v, u] >= 0:
             assert out[v, u] in win[win >= 0]
+
+
+def test_median_interior_matches_a_library_filter(orc):
+    """With every disparity valid, a window at least r pixels from the border
+    holds (2r+1)^2 values and its median is the library's median filter."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(4)
+    d = rng.integers(0, 256, (41, 47)).astype(np.int16)
+    for r in (1, 2, 3):
+        inner = (slice(r, -r), slice(r, -r))
+        np.testing.assert_array_equal(orc.median(d, r)[inner], ndimage.median_filter(d, size=2 * r + 1)[inner])
