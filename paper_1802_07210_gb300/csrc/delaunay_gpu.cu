@@ -20,13 +20,13 @@
 // triangle's circumdisc lies inside that disc (4 r^2 <= R^2 in exact
 // arithmetic, so no farther point can matter) and,
 // where the star stays open (p on the hull), nothing lies beyond either open
-// edge (checked against the extreme points of every image row).  The other
-// stars go through the same group pass once more with one warp per star and
-// the points within 64 pixels (circles up to radius 32).  The rest are
-// rebuilt by one CTA (256 threads) per point: each step takes the best of
-// the points within 192 pixels when its circle fits that disc, else scans
-// the grid cells its circle (or, with no candidate, its half-plane) meets,
-// which is exact.  Each triangle
+// edge (checked against the extreme points of every image row).  In batches
+// of two or more pairs the other stars go through the same group pass twice
+// more: eight lanes and the points within 32 pixels, then one warp and the
+// points within 64.  The rest are rebuilt by one CTA per point: each step
+// takes the best of the points within 96 (then 192) pixels when its circle
+// fits that disc, else scans the grid cells its circle (or, with no
+// candidate, its half-plane) meets, which is exact.  Each triangle
 // is emitted once, by its lowest-index vertex, at an offset from an
 // exclusive scan of the per-point counts, so the output order is
 // deterministic.
