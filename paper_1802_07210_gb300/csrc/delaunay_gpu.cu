@@ -326,7 +326,7 @@ constexpr int kDtGroup = 4;       // lanes per star in batched launches (issue-b
 constexpr int kDtGroupOne = 16;   // lanes per star for one pair (latency-bound: shorter star chains)
 constexpr int kDtGroupThreads = 256;
 constexpr int kDtListCap = 128;  // candidates per point (a radius-24 disc holds at most ~75 lattice points at step 5)
-constexpr int kDtRadiusB = 64;   // second group pass: one warp per star left by the first
+constexpr int kDtRadiusB = 64;   // warp pass (batches): one warp per star left by the middle pass
 constexpr int kDtListCapB = 640; // the radius-64 disc holds at most ~520 lattice points
 
 // Group reduction of (best, key) under the pencil order of edge (p, e).
@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(kDtBlockThreads, kDtBlocksPerSM) dt_pass_block
 // time from one atomic counter (zeroed by dt_init_kernel_b), so the long
 // stars of one pair overlap the work of all the others.  queue_id 1: the
 // warp pass's queues; 0: the group pass's (a batch of one pair, which skips
-// the warp pass).
+// the middle and warp passes).
 template <int THREADS, int PER_SM>
 __global__ void __launch_bounds__(THREADS, PER_SM)
     dt_pass_block_kernel_b(const DtArgs *__restrict__ tab, VMap vm, int nsides, int32_t *counter, int queue_id) {
@@ -1421,8 +1421,8 @@ elas_status launch_triangulate_b(const DtArgs *tab, const DtArgs *host, const VM
         vmap_add(m_scan, slot, dim3(1, nsides));
         const int gthreads = kDtGroupThreads / (pairs.n == 1 ? kDtGroupOne : kDtGroup);
         vmap_add(m_grp, slot, dim3(dt_point_blocks(a.cap, gthreads, pairs.n), nsides));
-        // the second group pass gets a warp per star of a queue of a few
-        // percent of the points
+        // the middle and warp passes get their queues of a few percent of
+        // the points (grid-stride over the queue)
         vmap_add(m_grp2, slot, dim3(max(1, min(sm_count(), a.cap / 256)), nsides));
         vmap_add(m_big, slot, dim3(pairs.n == 1 ? sm_count() : 64, nsides));
         max_gh = max(max_gh, a.gh);
