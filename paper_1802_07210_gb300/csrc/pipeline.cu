@@ -3,11 +3,16 @@
 // Owns, for one image size: device buffers for every intermediate, the
 // workspaces, a pinned staging area for the support list (device -> host)
 // and the triangles (host -> device), and one helper thread so that the
-// left- and right-coordinate triangulations run concurrently.
+// left- and right-coordinate triangulations of the host route run
+// concurrently.
 //
-// Per pair: descriptors (or the two census records) -> support (GPU) | count+list to host | two
-// triangulations (host, in parallel) | triangles to device | plane prior ->
-// dense -> LR check -> post-processing (GPU).
+// Per pair, GPU triangulation (the default): descriptors (or the two census
+// records) -> support -> both triangulations -> plane prior -> dense -> LR
+// check -> post-processing, all on the device and replayed as one CUDA graph
+// per set of buffers; the support and triangle counts go to the host on a
+// side stream for the statistics.  Host route: support (GPU) | count + list
+// to host | two triangulations (host, in parallel) | triangles to device |
+// plane prior -> dense -> LR check -> post-processing (GPU).
 #include <chrono>
 #include <condition_variable>
 #include <functional>
